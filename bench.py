@@ -1,0 +1,328 @@
+#!/usr/bin/env python3
+"""Throughput of the factorized stochastic three-point hot path on one GB300.
+
+One step = one pass of the whole hot path over the meson workload on a 24^3 x 48
+lattice: for each sink separation t_f in {8, 10, 12} (source at the origin, its
+own 16 Z2xZ2 noises and Gaussian solutions), the insertion part on every slice
+0..t_f, the meson spectator on t_f (93 momenta with |k|^2 <= 8 at sink and
+insertion), and the combine for 16 Gamma structures on every insertion slice.
+
+Metric: site*noise*momentum contractions per second = sum over projected slices
+of V3 * N_r * Nq, divided by the wall time of the step (timed on the device).
+
+Run:  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp64]
+      python bench.py --impl reference      (the FP64 CPU oracle on a bounded sample)
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "site*noise*mom contractions/s"
+UNIT = "contractions/s"
+WORKLOAD = "meson 3pt 24^3x48, 1 source at origin, N_r=16, t_f in {8,10,12}, 93 momenta (|k|^2<=8), complex128 inputs"
+
+L, T_SLAB, N_R, TFS, N2MAX = 24, 13, 16, (8, 10, 12), 8
+SEED = 2000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lhc", choices=["lhc", "reference"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def units_per_step(nq):
+    V3 = L ** 3
+    slices = sum(tf + 1 for tf in TFS) + len(TFS)
+    return V3 * N_R * nq * slices
+
+
+# --------------------------------------------------------------------------- inputs
+
+def make_inputs():
+    """Seeded inputs of the workload (host, numpy): S on slices 0..12 (the slab the
+    step touches), and per t_f its own solutions (slices 0..t_f) and noise."""
+    from paper_1711_02384_gb300 import inputs
+    S = inputs.propagator(SEED, L, 48, slices=range(T_SLAB))              # [13][V3][12][12]
+    psis, etas = [], []
+    for j, tf in enumerate(TFS):
+        psi = np.zeros((N_R, T_SLAB, L ** 3, 12), dtype=np.complex128)
+        psi[:, :tf + 1] = inputs.solutions(SEED + 10 * (j + 1), L, 48, N_R, slices=range(tf + 1))
+        psis.append(psi)
+        etas.append(inputs.noise(SEED + 10 * (j + 1) + 3, L, N_R, tf))
+    return S, psis, etas
+
+
+def gamma_sets():
+    from oracle import gamma as OG          # the 16 Dirac structures (plain constants)
+    g16 = OG.gamma16(OG.chiral())
+    g4 = np.broadcast_to(OG.chiral()[3], (16, 4, 4)).copy()
+    return g16, g4, g16.copy()
+
+
+# --------------------------------------------------------------------------- clocks
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- reference arm / cpu baseline
+
+def oracle_sample(S, psis, etas, k):
+    """The FP64 oracle as it stands on a bounded sample of the workload: the
+    insertion on slice 5 and the spectator on the sink slice, for t_f = 10 (all
+    16 noises, all 93 momenta).  Returns (units, seconds)."""
+    from oracle import contractions as OC
+    g5 = np.diag([1.0, 1.0, -1.0, -1.0]).astype(complex)
+    r3 = np.zeros(3, dtype=int)
+    t0 = time.perf_counter()
+    OC.insertion(S[5:6], psis[1][:, 5:6], g5, r3, k, L)
+    OC.spectator_meson(S[TFS[1]], etas[1], g5, r3, k, L)
+    dt = time.perf_counter() - t0
+    return 2 * L ** 3 * N_R * len(k), dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle.momenta import momenta
+    k = momenta(N2MAX)
+    S, psis, etas = make_inputs()
+    for _ in range(args.warmup):
+        oracle_sample(S, psis, etas, k)
+    tot_u, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        u, t = oracle_sample(S, psis, etas, k)
+        tot_u += u
+        tot_t += t
+    v = tot_u / tot_t
+    cores = os.cpu_count()
+    sample = "insertion slice 5 + spectator slice 10 of the t_f=10 set, 16 noises, 93 momenta, per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Philox Gaussian propagators/solutions, Z2xZ2 noise)",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1711_02384_gb300 import lhc
+    k = lhc.momenta(N2MAX)
+    nq = len(k)
+    r = np.zeros(4, dtype=np.int32)
+    S_h, psis_h, etas_h = make_inputs()
+    g16, g4, gsrc = gamma_sets()
+    S = torch.from_numpy(S_h).to(dev)
+    psis = [torch.from_numpy(p).to(dev) for p in psis_h]
+    etas = [torch.from_numpy(e).to(dev) for e in etas_h]
+    G = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (g16, g4, gsrc)]
+    ctx = lhc.Context(local)
+    st = torch.cuda.current_stream(dev)
+
+    outs_ins = [torch.empty((tf + 1, nq, N_R, 192), dtype=torch.complex128, device=dev) for tf in TFS]
+    outs_spec = [torch.empty((nq, N_R, 192), dtype=torch.complex128, device=dev) for _ in TFS]
+    outs_c = [torch.empty((tf + 1, 16, nq, nq), dtype=torch.complex128, device=dev) for tf in TFS]
+
+    def step():
+        for j, tf in enumerate(TFS):
+            ctx.insertion(S, psis[j], 0, tf, r, k, prec=args.prec, out=outs_ins[j])
+            ctx.spectator(S, etas[j], tf, r, k, prec=args.prec, out=outs_spec[j])
+            for y in range(tf + 1):
+                ctx.combine(outs_spec[j], outs_ins[j][y], G[0], G[1], G[2], out=outs_c[j][y])
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    upstep = units_per_step(nq)
+    value = upstep * args.steps * world / (ms / 1e3)
+
+    # dominant kernel: timed with CUDA events on its own stream by the library
+    kern = lhc.KERNEL_FUSED if args.prec == "mixed" else lhc.KERNEL_PROJECT
+    ctx.profile(True)
+    step()
+    torch.cuda.synchronize(dev)
+    ctx.profile(False)
+    kms, kn, kwork = ctx.profile_read(kern)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    if args.prec == "mixed":
+        peak = peaks.get("bf16_tflops", 1900.0)
+        bound, punit, peak_src = "tensor", "TFLOP/s", "measured bf16 burst (fp16 same rate)"
+    else:
+        peak = 1.25     # FP64: 2 DFMA/clk/SM x 152 SMs x ~2.06 GHz (nominal GB300 FP64 rate)
+        bound, punit, peak_src = "alu", "TFLOP/s", "nominal FP64 1.25 TFLOP/s"
+    achieved = (kwork / (kms / 1e3)) / 1e12 if kms > 0 else None
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": punit,
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "kernel_ms_per_launch": kms / kn if kn else None, "launches_per_step": kn,
+                "peak_source": peak_src}
+    gpu_launches_step = None
+    try:
+        tot = 0
+        for kid in range(4):
+            tot += ctx.profile_read(kid)[1]
+        gpu_launches_step = tot
+    except Exception:
+        pass
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        S_p = torch.from_numpy(S_h).pin_memory()
+        psis_p = [torch.from_numpy(p).pin_memory() for p in psis_h]
+        etas_p = [torch.from_numpy(e).pin_memory() for e in etas_h]
+        G_p = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (g16, g4, gsrc)]
+        hi = [torch.empty((tf + 1, nq, N_R, 192), dtype=torch.complex128).pin_memory() for tf in TFS]
+        hs = [torch.empty((nq, N_R, 192), dtype=torch.complex128).pin_memory() for _ in TFS]
+        hc = [torch.empty((tf + 1, 16, nq, nq), dtype=torch.complex128).pin_memory() for tf in TFS]
+
+        def step_host():
+            for j, tf in enumerate(TFS):
+                ctx.insertion(S_p, psis_p[j], 0, tf, r, k, prec=args.prec, out=hi[j], stream=st.cuda_stream)
+                ctx.spectator(S_p, etas_p[j], tf, r, k, prec=args.prec, out=hs[j], stream=st.cuda_stream)
+                for y in range(tf + 1):
+                    ctx.combine(hs[j], hi[j][y], G_p[0], G_p[1], G_p[2], out=hc[j][y], stream=st.cuda_stream)
+
+        step_host()
+        torch.cuda.synchronize(dev)
+        ne = max(1, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            step_host()
+        torch.cuda.synchronize(dev)
+        dt = (time.perf_counter() - t0) / ne
+        V3 = L ** 3
+        h2d = 0
+        d2h = 0
+        for tf in TFS:
+            h2d += (tf + 1) * V3 * 144 * 16 + N_R * (tf + 1) * V3 * 12 * 16      # S + psi slices
+            h2d += V3 * 144 * 16 + N_R * V3 * 12 * 16                             # S + eta (spectator)
+            d2h += (tf + 1) * nq * N_R * 192 * 16 + nq * N_R * 192 * 16           # open-spin outputs
+            h2d += (tf + 1) * (2 * nq * N_R * 192 * 16 + 3 * 16 * 16 * 16)        # combine inputs
+            d2h += (tf + 1) * 16 * nq * nq * 16                                   # correlators
+        e2e = {"value": upstep / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": dt * 1e3}
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        from oracle.momenta import momenta
+        u, t = oracle_sample(S_h, psis_h, etas_h, momenta(N2MAX))
+        cpu = {"value": u / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "insertion slice 5 + spectator slice 10 of the t_f=10 set, 16 noises, 93 momenta"}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f16x2->f32 (mixed)" if args.prec == "mixed" else "f64",
+            "data": "synthetic (seeded Philox Gaussian propagators/solutions, Z2xZ2 noise)",
+            "config": {"workload": WORKLOAD, "precision": args.prec, "parallelism": f"replicas x{world}",
+                       "l2": "inputs (2.1 GB per step) larger than L2", "units_per_step": upstep},
+            "clocks": clk, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": gpu_launches_step,
+        }))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

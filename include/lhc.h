@@ -1,0 +1,176 @@
+/*
+ * liblhc -- factorized stochastic three-point contractions with open spin indices
+ * (Bali et al., "Baryonic and mesonic 3-point functions with open spin indices",
+ * Lattice 2017, arXiv:1711.02384), for one NVIDIA GB300 (sm_103a).
+ *
+ * The correlator of Eq. 1 is split (Eq. 8) into a spectator part (Eq. 9), living
+ * on the sink timeslice, and an insertion part (Eq. 10), living on every
+ * insertion timeslice.  Both keep every spin index and the source colour open and
+ * are Fourier-projected onto many momenta; the correlator for any Gamma structure
+ * and any momentum pair is then the cheap noise average of Eq. 5 (the combine).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * complex numbers   interleaved (re, im); LHC_C128 = 2 x double, LHC_C64 = 2 x float.
+ * timeslice         L^3 sites, site = (z*L + y)*L + x.
+ * propagator        S[T][L^3][12][12] = G(x, r): row = sink spin*3 + colour at x,
+ *                   column = source spin*3 + colour at r (a point-to-all propagator).
+ * solution psi      psi[n_r][T][L^3][12]: s_i of Eq. 5 (D s_i = eta_i).
+ * noise eta         eta[n_r][L^3][12] on the sink slice only (Eq. 5, time-partitioned).
+ * momenta k         host int[nq][3]; p = 2*pi*k/L (Sec. 3).  Any order, any values.
+ * source r          host int[4] = (x, y, z, t).  Spatial phases use x - r (the rule
+ *                   stated after Eq. 10), wrapped periodically; r[3] is not used
+ *                   (timeslices are passed as absolute indices, taken mod T).
+ * gamma5            diagonal, set per context (default chiral basis diag(1,1,-1,-1)).
+ * output            always complex128, in caller memory.
+ *
+ * Memory: every buffer argument may be device memory or host memory (pinned or
+ * pageable).  Host buffers are staged through the context's workspace; a call
+ * that touches any host buffer synchronizes its stream before it returns.  With
+ * only device buffers a call is asynchronous on `stream` (a cudaStream_t; NULL =
+ * legacy default stream).  The caller owns every buffer it passes; the library
+ * never frees them.  The library owns its workspace and its cached phase tables,
+ * both counted against the context's HBM budget.
+ *
+ * Errors: every call returns an lhc_status; nothing is thrown across the ABI.
+ * Invalid arguments return LHC_EINVAL before anything is launched.
+ * lhc_last_error() gives a human-readable description of the last failure on
+ * the calling thread.
+ */
+#ifndef LHC_H
+#define LHC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lhc_ctx_s *lhc_ctx;
+
+typedef enum {
+  LHC_OK = 0,
+  LHC_EINVAL = 1,     /* bad argument (shape, pointer, enum)                        */
+  LHC_ENOMEM = 2,     /* device allocation failed                                    */
+  LHC_EBUDGET = 3,    /* request does not fit the context's HBM budget               */
+  LHC_ETIMEOUT = 4,   /* a bounded wait ran out                                      */
+  LHC_ECUDA = 5,      /* a CUDA runtime call failed (see lhc_last_error)             */
+  LHC_EBUSY = 6,      /* job still running                                           */
+  LHC_ENOTFOUND = 7,  /* unknown handle or job id                                    */
+  LHC_ECANCELED = 8   /* job was cancelled                                           */
+} lhc_status;
+
+typedef enum {
+  LHC_FP64 = 0,   /* plain FP64 GPU path: FP64 site contraction and projection          */
+  LHC_MIXED = 1   /* FP32 site contraction, split-FP16 tensor-core projection with
+                     FP32 accumulation, FP64 cross-block reduction                       */
+} lhc_precision;
+
+typedef enum { LHC_C128 = 0, LHC_C64 = 1 } lhc_dtype;
+typedef enum { LHC_MESON = 0, LHC_BARYON = 1 } lhc_kind;
+
+typedef struct {
+  int L;       /* spatial extent (sites per direction), 1 <= L <= 128 */
+  int T;       /* temporal extent                                     */
+  int dtype;   /* lhc_dtype of the propagator, solution and noise     */
+} lhc_lattice;
+
+/* Status text (static string). */
+const char *lhc_strerror(int status);
+
+/* Description of the last failure on the calling thread (static per thread). */
+const char *lhc_last_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int lhc_version(void);
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the device
+ * memory the library itself allocates (workspace, phase tables); 0 = no bound. */
+int lhc_create(lhc_ctx *ctx, int device, size_t hbm_budget_bytes);
+
+/* Destroy a context: synchronizes the device, then frees everything it owns. */
+int lhc_destroy(lhc_ctx ctx);
+
+/* Diagonal of gamma5 (each entry +1 or -1) used by every later call on ctx. */
+int lhc_set_gamma5(lhc_ctx ctx, const int g5[4]);
+
+/* Momentum set of Sec. 3: every integer k with |k|^2 <= n2max and, if cmax >= 0,
+ * |k_j| <= cmax, ordered by (|k|^2, kx, ky, kz).  Writes min(count, cap) vectors
+ * to k (host int[cap][3], may be NULL when cap = 0) and the full count to *nq. */
+int lhc_momenta(int n2max, int cmax, int *k, int cap, int *nq);
+
+/* Insertion part, Eq. 10, on every slice t = t_lo .. t_hi (taken mod T):
+ *
+ *   out[t - t_lo][q][i][(at*4 + bt)*12 + b*3 + a]
+ *     = sum_y e^{+i p_q.(y - r)} sum_{a~} g5(at) conj(psi_i(y)[at*3 + a~])
+ *                                   S3(y)[(bt*3 + a~)*12 + b*3 + a]
+ *
+ * (at = alpha~, bt = beta~, b = beta, a = source colour).  S3: propagator
+ * G3(y, r); psi: solutions; out: complex128 [t_hi - t_lo + 1][nq][n_r][192].
+ * prec: lhc_precision.  Requires 1 <= n_r, 1 <= nq, 0 <= t_hi - t_lo < T. */
+int lhc_insertion(lhc_ctx ctx, const lhc_lattice *lat, const void *S3, const void *psi,
+                  int n_r, int t_lo, int t_hi, const int r[4], const int *k, int nq,
+                  int prec, void *out, void *stream);
+
+/* Spectator part on the sink slice t_sink.
+ *
+ * kind = LHC_MESON, Eq. 9 with G1(r, x') = gamma5 S1(x')^dagger gamma5:
+ *   out[q][i][(bp*4 + ap)*12 + al*3 + a]
+ *     = sum_x' e^{-i p_q.(x' - r)} sum_{a'} g5(bp) g5(ap) g5(al) eta_i(x')[bp*3 + a']
+ *                                      conj(S1(x')[(ap*3 + a')*12 + al*3 + a])
+ *   (bp = beta', ap = alpha', al = alpha); out: complex128 [nq][n_r][192].
+ *
+ * kind = LHC_BARYON (the paper states the baryon case without a formula; this is
+ * the eps-eps reading in which the third quark's sink end is the same stochastic
+ * (gamma5 eta_i) as the meson's, so the insertion part is shared):
+ *   out[q][i][((((a1p*4 + a1)*4 + a2p)*4 + a2)*4 + bp)*3 + c]
+ *     = sum_x' e^{-i p_q.(x' - r)} sum eps_{a' b' c'} eps_{a b c}
+ *         GA(x')[(a1p*3 + a')*12 + a1*3 + a] GB(x')[(a2p*3 + b')*12 + a2*3 + b]
+ *         g5(bp) eta_i(x')[bp*3 + c']
+ *   GA, GB: the two spectator propagators G(x', r); out: complex128 [nq][n_r][3072].
+ * GB must be NULL for LHC_MESON and non-NULL for LHC_BARYON. */
+int lhc_spectator(lhc_ctx ctx, const lhc_lattice *lat, int kind, const void *S1_or_GA,
+                  const void *GB, const void *eta, int n_r, int t_sink, const int r[4],
+                  const int *k, int nq, int prec, void *out, void *stream);
+
+/* Noise-averaged combine (Eqs. 5 and 8), FP64, for ng spin structures:
+ *
+ * LHC_MESON:  out[g][p][q] = (1/n_r) sum_i sum Gsnk[g][ap][bp] Gins[g][at][bt] Gsrc[g][b][al]
+ *                            spec[p][i][(bp, ap, al, a)] ins[q][i][(at, bt, b, a)]
+ *             snk, src: complex128 [ng][4][4]
+ * LHC_BARYON: out[g][p][q] = (1/n_r) sum_{i,c} sum Wsnk[g][a1p][a2p][bp] Wsrc[g][a1][a2][b]
+ *                            Gins[g][at][bt] spec[p][i][(a1p,a1,a2p,a2,bp,c)] ins[q][i][(at,bt,b,c)]
+ *             snk, src: complex128 [ng][4][4][4]
+ * ins_g: complex128 [ng][4][4]; spec: [np][n_r][192 | 3072]; ins: [nq][n_r][192]
+ * (one insertion slice); out: complex128 [ng][np][nq]. */
+int lhc_combine(lhc_ctx ctx, int kind, const void *spec, int np, const void *ins, int nq,
+                int n_r, const void *snk, const void *ins_g, const void *src, int ng,
+                void *out, void *stream);
+
+/* Kernel-level timing with CUDA events recorded on the launching stream, for
+ * roofline measurements.  lhc_profile(ctx, 1) clears the records and starts
+ * recording around every launch of the listed kernels; lhc_profile(ctx, 0) stops.
+ * lhc_profile_read waits for the recorded launches and returns, for one kernel
+ * class, the summed device time in ms, the number of launches, and the
+ * algorithmic work of those launches (flops for LHC_KERNEL_PROJECT and
+ * LHC_KERNEL_FUSED: 8 per complex multiply-add of the direct sum; bytes of input
+ * read plus output written for LHC_KERNEL_CONTRACT).  Timing adds two event
+ * records per launch; leave it off outside measurements. */
+typedef enum {
+  LHC_KERNEL_PROJECT = 0,    /* FP64 projection GEMM                                   */
+  LHC_KERNEL_CONTRACT = 1,   /* FP64 site contraction                                  */
+  LHC_KERNEL_FUSED = 2,      /* mixed path: fused contraction + tensor-core projection */
+  LHC_KERNEL_REDUCE = 3,     /* mixed path: FP64 cross-block reduction                 */
+  LHC_KERNEL_COUNT = 4
+} lhc_kernel_id;
+
+int lhc_profile(lhc_ctx ctx, int enable);
+int lhc_profile_read(lhc_ctx ctx, int kernel, double *total_ms, long long *launches,
+                     double *work);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LHC_H */

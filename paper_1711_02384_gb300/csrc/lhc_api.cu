@@ -1,0 +1,577 @@
+// C ABI of liblhc: argument checks, memory, host staging, phase-table cache and
+// dispatch to the kernels.  Every entry point returns an lhc_status.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+
+#include "lhc_internal.h"
+
+namespace lhc {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
+static int fail(int status, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return status;
+}
+
+bool PhaseKey::operator<(const PhaseKey &o) const {
+  if (L != o.L) return L < o.L;
+  if (nq != o.nq) return nq < o.nq;
+  if (sign != o.sign) return sign < o.sign;
+  if (fmt != o.fmt) return fmt < o.fmt;
+  if (rx != o.rx) return rx < o.rx;
+  if (ry != o.ry) return ry < o.ry;
+  if (rz != o.rz) return rz < o.rz;
+  return khash < o.khash;
+}
+
+uint64_t hash_k(const int *k, int nq) {
+  uint64_t h = 1469598103934665603ull;   // FNV-1a over the integers
+  for (int j = 0; j < 3 * nq; ++j) {
+    uint32_t v = (uint32_t)k[j];
+    for (int b = 0; b < 4; ++b) {
+      h ^= (v >> (8 * b)) & 0xffu;
+      h *= 1099511628211ull;
+    }
+  }
+  return h;
+}
+
+int g5mask_of(const lhc_ctx ctx) {
+  int m = 0;
+  for (int s = 0; s < 4; ++s)
+    if (ctx->g5[s] < 0) m |= 1 << s;
+  return m;
+}
+
+static void evict_one_phase(lhc_ctx ctx) {
+  if (ctx->phase_lru.empty()) return;
+  PhaseKey key = ctx->phase_lru.back();
+  ctx->phase_lru.pop_back();
+  auto it = ctx->phases.find(key);
+  if (it != ctx->phases.end()) {
+    cudaDeviceSynchronize();
+    dev_free(ctx, it->second.buf);
+    ctx->phases.erase(it);
+  }
+}
+
+int dev_alloc(lhc_ctx ctx, DevBuf &b, size_t bytes) {
+  b = DevBuf{};
+  if (bytes == 0) return LHC_OK;
+  while (ctx->budget && ctx->used + bytes > ctx->budget && !ctx->phase_lru.empty())
+    evict_one_phase(ctx);
+  if (ctx->budget && ctx->used + bytes > ctx->budget)
+    return fail(LHC_EBUDGET, "allocation of %zu bytes exceeds the HBM budget (%zu of %zu in use)",
+                bytes, ctx->used, ctx->budget);
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return fail(LHC_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  b.bytes = bytes;
+  ctx->used += bytes;
+  return LHC_OK;
+}
+
+void dev_free(lhc_ctx ctx, DevBuf &b) {
+  if (b.p) {
+    cudaFree(b.p);
+    ctx->used -= b.bytes;
+  }
+  b = DevBuf{};
+}
+
+int ensure(lhc_ctx ctx, DevBuf &b, size_t bytes) {
+  if (b.bytes >= bytes) return LHC_OK;
+  LHC_CHECK_CUDA(cudaDeviceSynchronize());   // nothing in flight may still use the old buffer
+  dev_free(ctx, b);
+  return dev_alloc(ctx, b, bytes + bytes / 4);
+}
+
+int get_phase_f64(lhc_ctx ctx, int L, const int *k, int nq, const int r[4], int sign,
+                  cudaStream_t st, const double2 **out) {
+  PhaseKey key{L, nq, sign, 0, ((r[0] % L) + L) % L, ((r[1] % L) + L) % L, ((r[2] % L) + L) % L,
+                hash_k(k, nq)};
+  auto it = ctx->phases.find(key);
+  if (it != ctx->phases.end()) {
+    ctx->phase_lru.remove(key);
+    ctx->phase_lru.push_front(key);
+    *out = static_cast<const double2 *>(it->second.buf.p);
+    return LHC_OK;
+  }
+  size_t V3 = (size_t)L * L * L;
+  size_t tbytes = (size_t)nq * V3 * sizeof(double2);
+  size_t kbytes = (size_t)3 * nq * sizeof(int);
+  size_t off_roots = (tbytes + kbytes + 255) & ~(size_t)255;
+  size_t off_k = tbytes;
+  PhaseEntry e;
+  LHC_TRY(dev_alloc(ctx, e.buf, off_roots + (size_t)L * sizeof(double2)));
+  std::vector<double2> roots(L);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int m = 0; m < L; ++m) roots[m] = make_double2(std::cos(two_pi * m / L), std::sin(two_pi * m / L));
+  char *base = static_cast<char *>(e.buf.p);
+  // synchronous copies: the host vectors go out of scope at return
+  LHC_CHECK_CUDA(cudaMemcpy(base + off_k, k, kbytes, cudaMemcpyHostToDevice));
+  LHC_CHECK_CUDA(cudaMemcpy(base + off_roots, roots.data(), (size_t)L * sizeof(double2),
+                            cudaMemcpyHostToDevice));
+  launch_phase_f64(reinterpret_cast<double2 *>(base), reinterpret_cast<const int *>(base + off_k), nq,
+                   L, key.rx, key.ry, key.rz, sign, reinterpret_cast<const double2 *>(base + off_roots),
+                   st);
+  LHC_CHECK_CUDA(cudaGetLastError());
+  ctx->phases[key] = e;
+  ctx->phase_lru.push_front(key);
+  *out = reinterpret_cast<const double2 *>(base);
+  return LHC_OK;
+}
+
+ProfScope::ProfScope(lhc_ctx c, cudaStream_t s, int k, double w) : ctx(c), st(s), kernel(k), work(w) {
+  if (!ctx->prof_on) return;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    cudaGetLastError();
+    a = b = nullptr;
+    return;
+  }
+  cudaEventRecord(a, st);
+}
+
+ProfScope::~ProfScope() {
+  if (!a) return;
+  cudaEventRecord(b, st);
+  ctx->prof.push_back(ProfRecord{kernel, a, b, work});
+}
+
+}  // namespace lhc
+
+using namespace lhc;
+
+namespace {
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+size_t esize(int dtype) { return dtype == LHC_C128 ? 16 : 8; }
+
+int check_lattice(const lhc_lattice *lat) {
+  if (!lat) return fail(LHC_EINVAL, "lattice is NULL");
+  if (lat->L < 1 || lat->L > 128 || lat->T < 1 || lat->T > 4096)
+    return fail(LHC_EINVAL, "lattice extent out of range (L=%d, T=%d)", lat->L, lat->T);
+  if (lat->dtype != LHC_C128 && lat->dtype != LHC_C64)
+    return fail(LHC_EINVAL, "unknown dtype %d", lat->dtype);
+  return LHC_OK;
+}
+
+}  // namespace
+
+// per-context event ordering the shared workspace between streams
+struct CtxSync {
+  cudaEvent_t ev = nullptr;
+  cudaStream_t last = nullptr;
+  bool used = false;
+};
+static std::map<lhc_ctx, CtxSync> g_sync;
+static std::mutex g_sync_mu;
+
+static int begin_call(lhc_ctx ctx, cudaStream_t st) {
+  LHC_CHECK_CUDA(cudaSetDevice(ctx->device));
+  std::lock_guard<std::mutex> g(g_sync_mu);
+  CtxSync &s = g_sync[ctx];
+  if (!s.ev) LHC_CHECK_CUDA(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
+  if (s.used && s.last != st) LHC_CHECK_CUDA(cudaStreamWaitEvent(st, s.ev, 0));
+  return LHC_OK;
+}
+
+static int end_call(lhc_ctx ctx, cudaStream_t st) {
+  std::lock_guard<std::mutex> g(g_sync_mu);
+  CtxSync &s = g_sync[ctx];
+  LHC_CHECK_CUDA(cudaEventRecord(s.ev, st));
+  s.last = st;
+  s.used = true;
+  return LHC_OK;
+}
+
+extern "C" {
+
+const char *lhc_strerror(int status) {
+  switch (status) {
+    case LHC_OK: return "success";
+    case LHC_EINVAL: return "invalid argument";
+    case LHC_ENOMEM: return "out of device memory";
+    case LHC_EBUDGET: return "request exceeds the HBM budget";
+    case LHC_ETIMEOUT: return "timed out";
+    case LHC_ECUDA: return "CUDA error";
+    case LHC_EBUSY: return "busy";
+    case LHC_ENOTFOUND: return "not found";
+    case LHC_ECANCELED: return "canceled";
+    default: return "unknown status";
+  }
+}
+
+const char *lhc_last_error(void) { return g_err; }
+
+int lhc_version(void) { return 100; }
+
+int lhc_create(lhc_ctx *out, int device, size_t hbm_budget_bytes) {
+  if (!out) return fail(LHC_EINVAL, "ctx pointer is NULL");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    return fail(LHC_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+  }
+  if (device < 0 || device >= n) return fail(LHC_EINVAL, "device %d out of range (%d devices)", device, n);
+  LHC_CHECK_CUDA(cudaSetDevice(device));
+  cudaDeviceProp prop;
+  LHC_CHECK_CUDA(cudaGetDeviceProperties(&prop, device));
+  if (prop.major * 10 + prop.minor < 100)
+    return fail(LHC_ECUDA, "device %d is sm_%d%d; this library is built for sm_103a", device, prop.major,
+                prop.minor);
+  lhc_ctx c = new lhc_ctx_s();
+  c->device = device;
+  c->budget = hbm_budget_bytes;
+  c->num_sms = prop.multiProcessorCount;
+  *out = c;
+  return LHC_OK;
+}
+
+int lhc_destroy(lhc_ctx ctx) {
+  if (!ctx) return fail(LHC_EINVAL, "ctx is NULL");
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  dev_free(ctx, ctx->ws);
+  dev_free(ctx, ctx->stage);
+  for (auto &kv : ctx->phases) dev_free(ctx, kv.second.buf);
+  for (auto &r : ctx->prof) {
+    cudaEventDestroy(r.start);
+    cudaEventDestroy(r.stop);
+  }
+  {
+    std::lock_guard<std::mutex> g(g_sync_mu);
+    auto it = g_sync.find(ctx);
+    if (it != g_sync.end()) {
+      if (it->second.ev) cudaEventDestroy(it->second.ev);
+      g_sync.erase(it);
+    }
+  }
+  delete ctx;
+  return LHC_OK;
+}
+
+int lhc_set_gamma5(lhc_ctx ctx, const int g5[4]) {
+  if (!ctx || !g5) return fail(LHC_EINVAL, "NULL argument");
+  for (int s = 0; s < 4; ++s)
+    if (g5[s] != 1 && g5[s] != -1) return fail(LHC_EINVAL, "gamma5 diagonal entries must be +1 or -1");
+  std::lock_guard<std::mutex> g(ctx->mu);
+  for (int s = 0; s < 4; ++s) ctx->g5[s] = g5[s];
+  return LHC_OK;
+}
+
+int lhc_profile(lhc_ctx ctx, int enable) {
+  if (!ctx) return fail(LHC_EINVAL, "ctx is NULL");
+  std::lock_guard<std::mutex> g(ctx->mu);
+  if (enable) {
+    for (auto &r : ctx->prof) {
+      cudaEventSynchronize(r.stop);
+      cudaEventDestroy(r.start);
+      cudaEventDestroy(r.stop);
+    }
+    ctx->prof.clear();
+  }
+  ctx->prof_on = enable != 0;
+  return LHC_OK;
+}
+
+int lhc_profile_read(lhc_ctx ctx, int kernel, double *total_ms, long long *launches, double *work) {
+  if (!ctx || !total_ms || !launches || !work) return fail(LHC_EINVAL, "NULL argument");
+  if (kernel < 0 || kernel >= LHC_KERNEL_COUNT) return fail(LHC_EINVAL, "unknown kernel id %d", kernel);
+  std::lock_guard<std::mutex> g(ctx->mu);
+  double ms = 0, w = 0;
+  long long n = 0;
+  for (auto &r : ctx->prof) {
+    if (r.kernel != kernel) continue;
+    LHC_CHECK_CUDA(cudaEventSynchronize(r.stop));
+    float e = 0;
+    LHC_CHECK_CUDA(cudaEventElapsedTime(&e, r.start, r.stop));
+    ms += e;
+    w += r.work;
+    ++n;
+  }
+  *total_ms = ms;
+  *launches = n;
+  *work = w;
+  return LHC_OK;
+}
+
+int lhc_momenta(int n2max, int cmax, int *k, int cap, int *nq) {
+  if (n2max < 0 || !nq || cap < 0 || (cap > 0 && !k)) return fail(LHC_EINVAL, "bad momentum arguments");
+  int c = cmax >= 0 ? cmax : (int)std::floor(std::sqrt((double)n2max) + 1e-9);
+  struct K { int n2, x, y, z; };
+  std::vector<K> v;
+  for (int x = -c; x <= c; ++x)
+    for (int y = -c; y <= c; ++y)
+      for (int z = -c; z <= c; ++z) {
+        int n2 = x * x + y * y + z * z;
+        if (n2 <= n2max) v.push_back({n2, x, y, z});
+      }
+  std::sort(v.begin(), v.end(), [](const K &a, const K &b) {
+    if (a.n2 != b.n2) return a.n2 < b.n2;
+    if (a.x != b.x) return a.x < b.x;
+    if (a.y != b.y) return a.y < b.y;
+    return a.z < b.z;
+  });
+  *nq = (int)v.size();
+  for (int j = 0; j < (int)v.size() && j < cap; ++j) {
+    k[3 * j] = v[j].x;
+    k[3 * j + 1] = v[j].y;
+    k[3 * j + 2] = v[j].z;
+  }
+  return LHC_OK;
+}
+
+}  // extern "C"
+
+// run_slice dispatch for the mixed path lives in k_mixed.cu
+namespace lhc {
+int run_slice_mixed(lhc_ctx ctx, const SliceJob &job, const int *k, int nq, const int r[4], int sign,
+                    cudaStream_t st);
+}
+
+namespace {
+
+// Common driver of the insertion and spectator calls.
+struct PartCall {
+  Part part;
+  const lhc_lattice *lat;
+  const void *S, *SB, *vec;
+  int n_r;
+  int t0, nt;          // slices t0 .. t0+nt-1 (mod T)
+  bool vec_has_time;   // psi carries a time axis, eta does not
+  const int *r, *k;
+  int nq, prec;
+  void *out;
+  int sign;
+};
+
+int run_part(lhc_ctx ctx, const PartCall &c, cudaStream_t st) {
+  const int L = c.lat->L, T = c.lat->T, V3 = L * L * L;
+  const size_t es = esize(c.lat->dtype);
+  const int cols = (c.part == PART_SPEC_BARYON ? kBarCols : 192);
+  const size_t slice_elems = (size_t)V3 * 144;
+  const size_t vec_slice = (size_t)V3 * 12;
+  const size_t out_bytes = (size_t)c.nt * c.nq * c.n_r * cols * sizeof(double2);
+
+  bool hS = !is_device_ptr(c.S), hSB = c.SB && !is_device_ptr(c.SB), hV = !is_device_ptr(c.vec);
+  bool hO = !is_device_ptr(c.out);
+  bool any_host = hS || hSB || hV || hO;
+
+  // staging layout: [S slices][SB slices][vec][out]
+  size_t bS = hS ? c.nt * slice_elems * es : 0;
+  size_t bSB = hSB ? c.nt * slice_elems * es : 0;
+  size_t nvt = c.vec_has_time ? c.nt : 1;
+  size_t bV = hV ? (size_t)c.n_r * nvt * vec_slice * es : 0;
+  size_t bO = hO ? out_bytes : 0;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  if (any_host) LHC_TRY(ensure(ctx, ctx->stage, al(bS) + al(bSB) + al(bV) + al(bO)));
+  char *sp = static_cast<char *>(ctx->stage.p);
+  const char *S = static_cast<const char *>(c.S), *SB = static_cast<const char *>(c.SB),
+             *V = static_cast<const char *>(c.vec);
+  size_t S_tstride = slice_elems * es;   // bytes between slices
+  if (hS || hSB) {
+    // copy the needed slices into [nt][V3][144]
+    for (int j = 0; j < c.nt; ++j) {
+      int t = (c.t0 + j) % T;
+      if (hS)
+        LHC_CHECK_CUDA(cudaMemcpyAsync(sp + j * slice_elems * es, S + (size_t)t * slice_elems * es,
+                                       slice_elems * es, cudaMemcpyHostToDevice, st));
+      if (hSB)
+        LHC_CHECK_CUDA(cudaMemcpyAsync(sp + al(bS) + j * slice_elems * es,
+                                       SB + (size_t)t * slice_elems * es, slice_elems * es,
+                                       cudaMemcpyHostToDevice, st));
+    }
+  }
+  const char *Sd = hS ? sp : S;
+  const char *SBd = hSB ? sp + al(bS) : SB;
+  // vec layout on device: noise stride and slice base
+  const char *Vd = V;
+  size_t v_noise_stride = c.vec_has_time ? (size_t)T * vec_slice : vec_slice;   // elements
+  bool v_staged = false;
+  if (hV) {
+    char *dst = sp + al(bS) + al(bSB);
+    for (int i = 0; i < c.n_r; ++i)
+      for (size_t j = 0; j < nvt; ++j) {
+        size_t t = c.vec_has_time ? (size_t)((c.t0 + (int)j) % T) : 0;
+        size_t src_off = c.vec_has_time ? ((size_t)i * T + t) * vec_slice : (size_t)i * vec_slice;
+        LHC_CHECK_CUDA(cudaMemcpyAsync(dst + (i * nvt + j) * vec_slice * es, V + src_off * es,
+                                       vec_slice * es, cudaMemcpyHostToDevice, st));
+      }
+    Vd = dst;
+    v_noise_stride = nvt * vec_slice;
+    v_staged = true;
+  }
+  double2 *Od = hO ? reinterpret_cast<double2 *>(sp + al(bS) + al(bSB) + al(bV))
+                   : static_cast<double2 *>(c.out);
+
+  const double2 *phase = nullptr;
+  if (c.prec == LHC_FP64) LHC_TRY(get_phase_f64(ctx, L, c.k, c.nq, c.r, c.sign, st, &phase));
+
+  for (int j = 0; j < c.nt; ++j) {
+    int t = (c.t0 + j) % T;
+    SliceJob job;
+    job.part = c.part;
+    job.dtype = c.lat->dtype;
+    job.L = L;
+    job.V3 = V3;
+    job.n_r = c.n_r;
+    job.nq = c.nq;
+    job.S = Sd + (hS ? (size_t)j : (size_t)t) * S_tstride;
+    job.SB = c.SB ? SBd + (hSB ? (size_t)j : (size_t)t) * S_tstride : nullptr;
+    size_t vt = c.vec_has_time ? (v_staged ? (size_t)j : (size_t)t) : 0;
+    job.vec = Vd + vt * vec_slice * es;
+    job.vec_stride = v_noise_stride;
+    job.g5mask = g5mask_of(ctx);
+    job.out = Od + (size_t)j * c.nq * c.n_r * cols;
+    if (c.prec == LHC_FP64)
+      LHC_TRY(run_slice_f64(ctx, job, phase, st));
+    else
+      LHC_TRY(run_slice_mixed(ctx, job, c.k, c.nq, c.r, c.sign, st));
+  }
+  if (hO) {
+    LHC_CHECK_CUDA(cudaMemcpyAsync(c.out, Od, out_bytes, cudaMemcpyDeviceToHost, st));
+  }
+  if (any_host) LHC_CHECK_CUDA(cudaStreamSynchronize(st));
+  return LHC_OK;
+}
+
+int common_checks(lhc_ctx ctx, const lhc_lattice *lat, const void *S, const void *vec, int n_r,
+                  const int r[4], const int *k, int nq, int prec, void *out) {
+  if (!ctx) return fail(LHC_EINVAL, "ctx is NULL");
+  LHC_TRY(check_lattice(lat));
+  if (!S || !vec || !out || !r || !k) return fail(LHC_EINVAL, "NULL buffer argument");
+  if (n_r < 1 || n_r > 4096) return fail(LHC_EINVAL, "n_r=%d out of range", n_r);
+  if (nq < 1 || nq > 65536) return fail(LHC_EINVAL, "nq=%d out of range", nq);
+  if (prec != LHC_FP64 && prec != LHC_MIXED) return fail(LHC_EINVAL, "unknown precision %d", prec);
+  return LHC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lhc_insertion(lhc_ctx ctx, const lhc_lattice *lat, const void *S3, const void *psi, int n_r,
+                  int t_lo, int t_hi, const int r[4], const int *k, int nq, int prec, void *out,
+                  void *stream) {
+  LHC_TRY(common_checks(ctx, lat, S3, psi, n_r, r, k, nq, prec, out));
+  if (t_hi < t_lo || t_hi - t_lo >= lat->T) return fail(LHC_EINVAL, "bad slice range %d..%d", t_lo, t_hi);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> g(ctx->mu);
+  LHC_TRY(begin_call(ctx, st));
+  PartCall c{PART_INS, lat, S3, nullptr, psi, n_r, ((t_lo % lat->T) + lat->T) % lat->T,
+             t_hi - t_lo + 1, true, r, k, nq, prec, out, +1};
+  int s = run_part(ctx, c, st);
+  int e = end_call(ctx, st);
+  return s != LHC_OK ? s : e;
+}
+
+int lhc_spectator(lhc_ctx ctx, const lhc_lattice *lat, int kind, const void *S1_or_GA, const void *GB,
+                  const void *eta, int n_r, int t_sink, const int r[4], const int *k, int nq, int prec,
+                  void *out, void *stream) {
+  LHC_TRY(common_checks(ctx, lat, S1_or_GA, eta, n_r, r, k, nq, prec, out));
+  if (kind != LHC_MESON && kind != LHC_BARYON) return fail(LHC_EINVAL, "unknown kind %d", kind);
+  if ((kind == LHC_MESON) != (GB == nullptr))
+    return fail(LHC_EINVAL, "GB must be NULL for mesons and given for baryons");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> g(ctx->mu);
+  LHC_TRY(begin_call(ctx, st));
+  PartCall c{kind == LHC_MESON ? PART_SPEC_MESON : PART_SPEC_BARYON, lat, S1_or_GA, GB, eta, n_r,
+             ((t_sink % lat->T) + lat->T) % lat->T, 1, false, r, k, nq, prec, out, -1};
+  int s = run_part(ctx, c, st);
+  int e = end_call(ctx, st);
+  return s != LHC_OK ? s : e;
+}
+
+int lhc_combine(lhc_ctx ctx, int kind, const void *spec, int np, const void *ins, int nq, int n_r,
+                const void *snk, const void *ins_g, const void *src, int ng, void *out, void *stream) {
+  if (!ctx) return fail(LHC_EINVAL, "ctx is NULL");
+  if (kind != LHC_MESON && kind != LHC_BARYON) return fail(LHC_EINVAL, "unknown kind %d", kind);
+  if (!spec || !ins || !snk || !ins_g || !src || !out) return fail(LHC_EINVAL, "NULL buffer argument");
+  if (np < 1 || nq < 1 || n_r < 1 || ng < 1) return fail(LHC_EINVAL, "sizes must be positive");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> g(ctx->mu);
+  LHC_TRY(begin_call(ctx, st));
+  const int scols = kind == LHC_MESON ? 192 : kBarCols;
+  const size_t nw = kind == LHC_MESON ? 16 : 64;
+  size_t b_spec = (size_t)np * n_r * scols * 16, b_ins = (size_t)nq * n_r * 192 * 16;
+  size_t b_snk = (size_t)ng * nw * 16, b_g = (size_t)ng * 16 * 16, b_src = (size_t)ng * nw * 16;
+  size_t b_out = (size_t)ng * np * nq * 16;
+  const void *ptr[6] = {spec, ins, snk, ins_g, src, out};
+  size_t bytes[6] = {b_spec, b_ins, b_snk, b_g, b_src, b_out};
+  bool host[6];
+  bool any = false;
+  size_t need = 0;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  for (int j = 0; j < 6; ++j) {
+    host[j] = !is_device_ptr(ptr[j]);
+    any |= host[j];
+    if (host[j]) need += al(bytes[j]);
+  }
+  int s = LHC_OK;
+  const void *dev[6];
+  if (any) s = ensure(ctx, ctx->stage, need);
+  if (s == LHC_OK) {
+    char *sp = static_cast<char *>(ctx->stage.p);
+    size_t off = 0;
+    for (int j = 0; j < 6; ++j) {
+      if (host[j]) {
+        dev[j] = sp + off;
+        if (j < 5) {
+          cudaError_t e = cudaMemcpyAsync(sp + off, ptr[j], bytes[j], cudaMemcpyHostToDevice, st);
+          if (e != cudaSuccess) {
+            s = fail(LHC_ECUDA, "staging copy: %s", cudaGetErrorString(e));
+            break;
+          }
+        }
+        off += al(bytes[j]);
+      } else {
+        dev[j] = ptr[j];
+      }
+    }
+  }
+  if (s == LHC_OK)
+    s = run_combine(ctx, kind, (const double2 *)dev[0], np, (const double2 *)dev[1], nq, n_r,
+                    (const double2 *)dev[2], (const double2 *)dev[3], (const double2 *)dev[4], ng,
+                    (double2 *)dev[5], st);
+  if (s == LHC_OK && host[5]) {
+    cudaError_t e = cudaMemcpyAsync(out, dev[5], b_out, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) s = fail(LHC_ECUDA, "output copy: %s", cudaGetErrorString(e));
+  }
+  if (s == LHC_OK && any) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = fail(LHC_ECUDA, "stream sync: %s", cudaGetErrorString(e));
+  }
+  int e2 = end_call(ctx, st);
+  return s != LHC_OK ? s : e2;
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// Internal declarations of liblhc (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <list>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "lhc.h"
+
+namespace lhc {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char *fmt, ...);
+#define LHC_CHECK_CUDA(call)                                                     \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess) {                                                     \
+      ::lhc::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call,                 \
+                       cudaGetErrorString(e_));                                  \
+      return LHC_ECUDA;                                                          \
+    }                                                                            \
+  } while (0)
+#define LHC_TRY(expr)                 \
+  do {                                \
+    int s_ = (expr);                  \
+    if (s_ != LHC_OK) return s_;      \
+  } while (0)
+
+// ---------------------------------------------------------------- problem shapes
+constexpr int kInsCols = 192;       // (alpha~, beta~, beta, a) per noise
+constexpr int kMesCols = 192;       // (beta', alpha', alpha, a) per noise
+constexpr int kBarCols = 3072;      // (alpha1', alpha1, alpha2', alpha2, beta', c) per noise
+
+enum Part { PART_INS = 0, PART_SPEC_MESON = 1, PART_SPEC_BARYON = 2 };
+
+// One slice worth of contraction + projection.  Pointers are device pointers.
+struct SliceJob {
+  Part part;
+  int dtype;            // lhc_dtype of the inputs
+  int L, V3, n_r, nq;
+  const void *S;        // propagator slice [V3][144] (S3, S1 or GA)
+  const void *SB;       // baryon: GB slice [V3][144]
+  const void *vec;      // psi slice of noise 0 (ins) or eta (spec): [V3][12]
+  size_t vec_stride;    // elements between consecutive noises of vec
+  int g5mask;           // bit s set when g5(s) = -1
+  double2 *out;         // [nq][n_r * cols]
+};
+
+// ---------------------------------------------------------------- context
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+struct PhaseKey {
+  int L, nq, sign, fmt, rx, ry, rz;
+  uint64_t khash;
+  bool operator<(const PhaseKey &o) const;
+  bool operator==(const PhaseKey &o) const { return !(*this < o) && !(o < *this); }
+};
+
+struct ProfRecord {
+  int kernel;
+  cudaEvent_t start, stop;
+  double work;
+};
+
+// Records CUDA events around one kernel launch when profiling is on.
+struct ProfScope {
+  lhc_ctx ctx;
+  cudaStream_t st;
+  int kernel;
+  double work;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(lhc_ctx c, cudaStream_t s, int k, double w);
+  ~ProfScope();
+};
+
+struct PhaseEntry {
+  DevBuf buf;
+  int nq_pad = 0;
+};
+
+}  // namespace lhc
+
+struct lhc_ctx_s {
+  int device = 0;
+  size_t budget = 0;   // 0 = unbounded
+  size_t used = 0;     // bytes the library holds
+  int g5[4] = {1, 1, -1, -1};
+  std::mutex mu;
+  lhc::DevBuf ws;                         // general workspace (grown on demand)
+  lhc::DevBuf stage;                      // host-staging buffer
+  std::map<lhc::PhaseKey, lhc::PhaseEntry> phases;
+  std::list<lhc::PhaseKey> phase_lru;     // front = most recent
+  int num_sms = 0;
+  bool prof_on = false;
+  std::vector<lhc::ProfRecord> prof;
+};
+
+namespace lhc {
+
+// memory accounting
+int dev_alloc(lhc_ctx ctx, DevBuf &b, size_t bytes);
+void dev_free(lhc_ctx ctx, DevBuf &b);
+int ensure(lhc_ctx ctx, DevBuf &b, size_t bytes);   // grows b (synchronizes the device first)
+
+int g5mask_of(const lhc_ctx ctx);
+uint64_t hash_k(const int *k, int nq);
+
+// phase tables
+// fmt 0: complex128 [nq][V3], P[q][x] = exp(sign*2*pi*i*((k.(x-r)) mod L)/L)
+int get_phase_f64(lhc_ctx ctx, int L, const int *k, int nq, const int r[4], int sign,
+                  cudaStream_t st, const double2 **out);
+
+// FP64 path: contraction into a workspace, then projection (k_f64.cu)
+int run_slice_f64(lhc_ctx ctx, const SliceJob &job, const double2 *phase, cudaStream_t st);
+
+// combine (k_combine.cu)
+int run_combine(lhc_ctx ctx, int kind, const double2 *spec, int np, const double2 *ins, int nq,
+                int n_r, const double2 *snk, const double2 *ins_g, const double2 *src, int ng,
+                double2 *out, cudaStream_t st);
+
+// kernels' launch wrappers
+void launch_phase_f64(double2 *P, const int *k_dev, int nq, int L, int rx, int ry, int rz,
+                      int sign, const double2 *roots_dev, cudaStream_t st);
+
+}  // namespace lhc

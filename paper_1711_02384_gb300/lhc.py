@@ -1,0 +1,217 @@
+"""Thin ctypes binding of liblhc (argument marshalling only).
+
+Every computation runs in the CUDA library.  If ``liblhc.so`` has not been built
+this module raises at load time; there is no CPU fallback.
+
+Tensors are torch tensors (complex128 or complex64, C-contiguous) on a CUDA
+device or on the host; the library stages host buffers itself.  Layouts are the
+ones of ``include/lhc.h``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblhc.so")
+
+KERNEL_PROJECT, KERNEL_CONTRACT, KERNEL_FUSED, KERNEL_REDUCE = range(4)
+OK, EINVAL, ENOMEM, EBUDGET, ETIMEOUT, ECUDA, EBUSY, ENOTFOUND, ECANCELED = range(9)
+FP64, MIXED = 0, 1
+C128, C64 = 0, 1
+MESON, BARYON = 0, 1
+PRECISIONS = {"fp64": FP64, "mixed": MIXED}
+
+
+class LhcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"liblhc status {status}: {msg}")
+        self.status = status
+
+
+class Lattice(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("T", ctypes.c_int), ("dtype", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build() "
+                               "(paper_1711_02384_gb300/build.py) first")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, ci, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        ip = ctypes.POINTER(ctypes.c_int)
+        lp = ctypes.POINTER(Lattice)
+        L.lhc_strerror.restype = ctypes.c_char_p
+        L.lhc_strerror.argtypes = [ci]
+        L.lhc_last_error.restype = ctypes.c_char_p
+        L.lhc_last_error.argtypes = []
+        L.lhc_version.restype = ci
+        L.lhc_create.argtypes = [ctypes.POINTER(vp), ci, sz]
+        L.lhc_destroy.argtypes = [vp]
+        L.lhc_set_gamma5.argtypes = [vp, ip]
+        L.lhc_momenta.argtypes = [ci, ci, ip, ci, ip]
+        L.lhc_insertion.argtypes = [vp, lp, vp, vp, ci, ci, ci, ip, ip, ci, ci, vp, vp]
+        L.lhc_spectator.argtypes = [vp, lp, ci, vp, vp, vp, ci, ci, ip, ip, ci, ci, vp, vp]
+        L.lhc_combine.argtypes = [vp, ci, vp, ci, vp, ci, ci, vp, vp, vp, ci, vp, vp]
+        L.lhc_profile.argtypes = [vp, ci]
+        L.lhc_profile_read.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
+        for name in ("lhc_create", "lhc_destroy", "lhc_set_gamma5", "lhc_momenta", "lhc_insertion",
+                     "lhc_spectator", "lhc_combine", "lhc_profile", "lhc_profile_read"):
+            getattr(L, name).restype = ci
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != OK:
+        raise LhcError(status, lib().lhc_last_error().decode())
+
+
+def momenta(n2max: int, cmax: int = -1) -> np.ndarray:
+    """Momentum set of the library (|k|^2 <= n2max, |k_j| <= cmax if cmax >= 0)."""
+    nq = ctypes.c_int(0)
+    _check(lib().lhc_momenta(n2max, cmax, None, 0, ctypes.byref(nq)))
+    k = np.zeros((nq.value, 3), dtype=np.int32)
+    _check(lib().lhc_momenta(n2max, cmax, k.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), nq.value,
+                             ctypes.byref(nq)))
+    return k
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dtype_code(t):
+    if t.dtype == torch.complex128:
+        return C128
+    if t.dtype == torch.complex64:
+        return C64
+    raise ValueError(f"unsupported dtype {t.dtype}")
+
+
+def _ints(v, n=None):
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.int32).reshape(-1))
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} integers")
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _stream(t, stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    if t.is_cuda:
+        return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def _L_of(V3):
+    L = int(round(V3 ** (1.0 / 3.0)))
+    if L ** 3 != V3:
+        raise ValueError(f"{V3} sites is not a cube")
+    return L
+
+
+class Context:
+    """An lhc context on one CUDA device."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0, gamma5=(1, 1, -1, -1)):
+        self._h = ctypes.c_void_p()
+        _check(lib().lhc_create(ctypes.byref(self._h), int(device), int(hbm_budget)))
+        self.device = device
+        self.set_gamma5(gamma5)
+
+    def close(self):
+        if self._h:
+            lib().lhc_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def profile(self, enable: bool):
+        """Start (clearing old records) or stop CUDA-event timing of the kernels."""
+        _check(lib().lhc_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self, kernel: int):
+        """(total device ms, launches, algorithmic work) recorded for one kernel class."""
+        ms, n, w = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+        _check(lib().lhc_profile_read(self._h, kernel, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)))
+        return ms.value, n.value, w.value
+
+    def set_gamma5(self, g5):
+        self._g5, p = _ints(g5, 4)
+        _check(lib().lhc_set_gamma5(self._h, p))
+
+    def insertion(self, S3, psi, t_lo, t_hi, r, k, prec="mixed", out=None, stream=None):
+        """Insertion part (Eq. 10).  S3: [T][V3][12][12]; psi: [n_r][T][V3][12];
+        returns complex128 [t_hi - t_lo + 1][nq][n_r][192]."""
+        T, V3 = S3.shape[0], S3.shape[1]
+        n_r = psi.shape[0]
+        lat = Lattice(_L_of(V3), T, _dtype_code(S3))
+        ka, kp = _ints(k)
+        nq = ka.size // 3
+        ra, rp = _ints(r, 4)
+        nt = t_hi - t_lo + 1
+        if out is None:
+            out = torch.empty((nt, nq, n_r, 192), dtype=torch.complex128, device=S3.device)
+        _check(lib().lhc_insertion(self._h, ctypes.byref(lat), _ptr(S3), _ptr(psi), n_r, t_lo, t_hi,
+                                   rp, kp, nq, PRECISIONS[prec], _ptr(out), _stream(S3, stream)))
+        return out
+
+    def spectator(self, S1, eta, t_sink, r, k, prec="mixed", GB=None, out=None, stream=None):
+        """Spectator part on slice t_sink: meson (Eq. 9) when GB is None, else the
+        baryon eps-eps spectator with GA = S1.  eta: [n_r][V3][12].
+        Returns complex128 [nq][n_r][192 | 3072]."""
+        T, V3 = S1.shape[0], S1.shape[1]
+        n_r = eta.shape[0]
+        lat = Lattice(_L_of(V3), T, _dtype_code(S1))
+        ka, kp = _ints(k)
+        nq = ka.size // 3
+        ra, rp = _ints(r, 4)
+        kind = MESON if GB is None else BARYON
+        cols = 192 if GB is None else 3072
+        if out is None:
+            out = torch.empty((nq, n_r, cols), dtype=torch.complex128, device=S1.device)
+        _check(lib().lhc_spectator(self._h, ctypes.byref(lat), kind, _ptr(S1), _ptr(GB), _ptr(eta), n_r,
+                                   t_sink, rp, kp, nq, PRECISIONS[prec], _ptr(out), _stream(S1, stream)))
+        return out
+
+    def combine(self, spec, ins, snk, ins_g, src, out=None, stream=None):
+        """Noise-averaged combine.  spec: [np][n_r][192 | 3072]; ins: [nq][n_r][192];
+        snk/src: [ng][4][4] (meson) or [ng][4][4][4] (baryon); ins_g: [ng][4][4].
+        Returns complex128 [ng][np][nq]."""
+        np_, n_r = spec.shape[0], spec.shape[1]
+        nq = ins.shape[0]
+        kind = MESON if spec.shape[2] == 192 else BARYON
+        ng = ins_g.shape[0]
+        if out is None:
+            out = torch.empty((ng, np_, nq), dtype=torch.complex128, device=spec.device)
+        _check(lib().lhc_combine(self._h, kind, _ptr(spec), np_, _ptr(ins), nq, n_r, _ptr(snk), _ptr(ins_g),
+                                 _ptr(src), ng, _ptr(out), _stream(spec, stream)))
+        return out
