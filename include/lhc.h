@@ -92,6 +92,12 @@ int lhc_create(lhc_ctx *ctx, int device, size_t hbm_budget_bytes);
 /* Destroy a context: synchronizes the device, then frees everything it owns. */
 int lhc_destroy(lhc_ctx ctx);
 
+/* Wait for `stream`, then report whether any kernel of this context gave up a
+ * bounded wait since the last check (LHC_ETIMEOUT; results of the affected calls
+ * are invalid).  Kernels never spin without limit: a wait that exceeds about two
+ * seconds raises this flag and the kernel returns. */
+int lhc_sync(lhc_ctx ctx, void *stream);
+
 /* Diagonal of gamma5 (each entry +1 or -1) used by every later call on ctx. */
 int lhc_set_gamma5(lhc_ctx ctx, const int g5[4]);
 

@@ -252,6 +252,11 @@ int lhc_create(lhc_ctx *out, int device, size_t hbm_budget_bytes) {
   c->device = device;
   c->budget = hbm_budget_bytes;
   c->num_sms = prop.multiProcessorCount;
+  if (cudaMalloc(&c->dev_err, 256) != cudaSuccess || cudaMemset(c->dev_err, 0, 256) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return fail(LHC_ENOMEM, "cannot allocate the device error word");
+  }
   *out = c;
   return LHC_OK;
 }
@@ -262,6 +267,7 @@ int lhc_destroy(lhc_ctx ctx) {
   cudaDeviceSynchronize();
   dev_free(ctx, ctx->ws);
   dev_free(ctx, ctx->stage);
+  if (ctx->dev_err) cudaFree(ctx->dev_err);
   for (auto &kv : ctx->phases) dev_free(ctx, kv.second.buf);
   for (auto &r : ctx->prof) {
     cudaEventDestroy(r.start);
@@ -276,6 +282,20 @@ int lhc_destroy(lhc_ctx ctx) {
     }
   }
   delete ctx;
+  return LHC_OK;
+}
+
+int lhc_sync(lhc_ctx ctx, void *stream) {
+  if (!ctx) return fail(LHC_EINVAL, "ctx is NULL");
+  LHC_CHECK_CUDA(cudaSetDevice(ctx->device));
+  LHC_CHECK_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  int code = 0;
+  LHC_CHECK_CUDA(cudaMemcpy(&code, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (code) {
+    LHC_CHECK_CUDA(cudaMemset(ctx->dev_err, 0, sizeof(int)));
+    return fail(LHC_ETIMEOUT, "a bounded device wait gave up (site %d); results of the affected calls are invalid",
+                code);
+  }
   return LHC_OK;
 }
 
@@ -351,12 +371,6 @@ int lhc_momenta(int n2max, int cmax, int *k, int cap, int *nq) {
 }
 
 }  // extern "C"
-
-// run_slice dispatch for the mixed path lives in k_mixed.cu
-namespace lhc {
-int run_slice_mixed(lhc_ctx ctx, const SliceJob &job, const int *k, int nq, const int r[4], int sign,
-                    cudaStream_t st);
-}
 
 namespace {
 
@@ -436,9 +450,10 @@ int run_part(lhc_ctx ctx, const PartCall &c, cudaStream_t st) {
   const double2 *phase = nullptr;
   if (c.prec == LHC_FP64) LHC_TRY(get_phase_f64(ctx, L, c.k, c.nq, c.r, c.sign, st, &phase));
 
+  std::vector<SliceJob> jobs(c.nt);
   for (int j = 0; j < c.nt; ++j) {
     int t = (c.t0 + j) % T;
-    SliceJob job;
+    SliceJob &job = jobs[j];
     job.part = c.part;
     job.dtype = c.lat->dtype;
     job.L = L;
@@ -452,11 +467,9 @@ int run_part(lhc_ctx ctx, const PartCall &c, cudaStream_t st) {
     job.vec_stride = v_noise_stride;
     job.g5mask = g5mask_of(ctx);
     job.out = Od + (size_t)j * c.nq * c.n_r * cols;
-    if (c.prec == LHC_FP64)
-      LHC_TRY(run_slice_f64(ctx, job, phase, st));
-    else
-      LHC_TRY(run_slice_mixed(ctx, job, c.k, c.nq, c.r, c.sign, st));
+    if (c.prec == LHC_FP64) LHC_TRY(run_slice_f64(ctx, job, phase, st));
   }
+  if (c.prec == LHC_MIXED) LHC_TRY(run_part_mixed(ctx, jobs.data(), c.nt, c.k, c.nq, c.r, c.sign, st));
   if (hO) {
     LHC_CHECK_CUDA(cudaMemcpyAsync(c.out, Od, out_bytes, cudaMemcpyDeviceToHost, st));
   }

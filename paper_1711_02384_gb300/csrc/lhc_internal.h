@@ -101,6 +101,7 @@ struct lhc_ctx_s {
   std::list<lhc::PhaseKey> phase_lru;     // front = most recent
   int num_sms = 0;
   bool prof_on = false;
+  int *dev_err = nullptr;                 // sticky device error word (bounded waits that gave up)
   std::vector<lhc::ProfRecord> prof;
 };
 
@@ -121,6 +122,10 @@ int get_phase_f64(lhc_ctx ctx, int L, const int *k, int nq, const int r[4], int 
 
 // FP64 path: contraction into a workspace, then projection (k_f64.cu)
 int run_slice_f64(lhc_ctx ctx, const SliceJob &job, const double2 *phase, cudaStream_t st);
+
+// mixed path: all slices of one call in one set of launches (k_mixed.cu)
+int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int nq, const int r[4], int sign,
+                   cudaStream_t st);
 
 // combine (k_combine.cu)
 int run_combine(lhc_ctx ctx, int kind, const double2 *spec, int np, const double2 *ins, int nq,

@@ -61,11 +61,12 @@ def lib():
         L.lhc_insertion.argtypes = [vp, lp, vp, vp, ci, ci, ci, ip, ip, ci, ci, vp, vp]
         L.lhc_spectator.argtypes = [vp, lp, ci, vp, vp, vp, ci, ci, ip, ip, ci, ci, vp, vp]
         L.lhc_combine.argtypes = [vp, ci, vp, ci, vp, ci, ci, vp, vp, vp, ci, vp, vp]
+        L.lhc_sync.argtypes = [vp, vp]
         L.lhc_profile.argtypes = [vp, ci]
         L.lhc_profile_read.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
         for name in ("lhc_create", "lhc_destroy", "lhc_set_gamma5", "lhc_momenta", "lhc_insertion",
-                     "lhc_spectator", "lhc_combine", "lhc_profile", "lhc_profile_read"):
+                     "lhc_spectator", "lhc_combine", "lhc_profile", "lhc_profile_read", "lhc_sync"):
             getattr(L, name).restype = ci
         _lib = L
     return _lib
@@ -153,6 +154,12 @@ class Context:
     @property
     def handle(self):
         return self._h
+
+    def sync(self, stream=None):
+        """Wait for the stream; raise if a kernel of this context gave up a bounded wait."""
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+        _check(lib().lhc_sync(self._h, ctypes.c_void_p(int(stream))))
 
     def profile(self, enable: bool):
         """Start (clearing old records) or stop CUDA-event timing of the kernels."""
