@@ -168,6 +168,18 @@ def run_reference(args):
 
 # --------------------------------------------------------------------------- GPU arm
 
+def gpu_launches_per_step(prec, nq):
+    """Kernels this library launches per step (phase tables are cached after warm-up)."""
+    n = 0
+    for tf in TFS:
+        if prec == "mixed":
+            n += 2 + 2                     # insertion, spectator: fused contraction+projection, FP64 reduce
+        else:
+            n += 2 * (tf + 1) + 2          # per slice: FP64 contraction, FP64 projection
+        n += 1 + (tf + 1) + 1              # combine: sink side, insertion side per slice, GEMM
+    return n
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -205,8 +217,7 @@ def main():
         for j, tf in enumerate(TFS):
             ctx.insertion(S, psis[j], 0, tf, r, k, prec=args.prec, out=outs_ins[j])
             ctx.spectator(S, etas[j], tf, r, k, prec=args.prec, out=outs_spec[j])
-            for y in range(tf + 1):
-                ctx.combine(outs_spec[j], outs_ins[j][y], G[0], G[1], G[2], out=outs_c[j][y])
+            ctx.combine(outs_spec[j], outs_ins[j], G[0], G[1], G[2], prec=args.prec, out=outs_c[j])
 
     def barrier():
         if world > 1:
@@ -253,14 +264,11 @@ def main():
                 "frac": (achieved / peak) if achieved else None, "traffic": None,
                 "kernel_ms_per_launch": kms / kn if kn else None, "launches_per_step": kn,
                 "peak_source": peak_src}
-    gpu_launches_step = None
-    try:
-        tot = 0
-        for kid in range(4):
-            tot += ctx.profile_read(kid)[1]
-        gpu_launches_step = tot
-    except Exception:
-        pass
+    kernels = {}
+    for kid, name in enumerate(lhc.KERNEL_NAMES):
+        kms_i, kn_i, _ = ctx.profile_read(kid)
+        if kn_i:
+            kernels[name] = {"ms_per_step": kms_i, "launches_per_step": kn_i}
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -277,8 +285,8 @@ def main():
             for j, tf in enumerate(TFS):
                 ctx.insertion(S_p, psis_p[j], 0, tf, r, k, prec=args.prec, out=hi[j], stream=st.cuda_stream)
                 ctx.spectator(S_p, etas_p[j], tf, r, k, prec=args.prec, out=hs[j], stream=st.cuda_stream)
-                for y in range(tf + 1):
-                    ctx.combine(hs[j], hi[j][y], G_p[0], G_p[1], G_p[2], out=hc[j][y], stream=st.cuda_stream)
+                ctx.combine(hs[j], hi[j], G_p[0], G_p[1], G_p[2], prec=args.prec, out=hc[j],
+                            stream=st.cuda_stream)
 
         step_host()
         torch.cuda.synchronize(dev)
@@ -295,7 +303,7 @@ def main():
             h2d += (tf + 1) * V3 * 144 * 16 + N_R * (tf + 1) * V3 * 12 * 16      # S + psi slices
             h2d += V3 * 144 * 16 + N_R * V3 * 12 * 16                             # S + eta (spectator)
             d2h += (tf + 1) * nq * N_R * 192 * 16 + nq * N_R * 192 * 16           # open-spin outputs
-            h2d += (tf + 1) * (2 * nq * N_R * 192 * 16 + 3 * 16 * 16 * 16)        # combine inputs
+            h2d += (tf + 2) * nq * N_R * 192 * 16 + 3 * 16 * 16 * 16             # combine inputs
             d2h += (tf + 1) * 16 * nq * nq * 16                                   # correlators
         e2e = {"value": upstep / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": dt * 1e3}
@@ -317,7 +325,7 @@ def main():
             "config": {"workload": WORKLOAD, "precision": args.prec, "parallelism": f"replicas x{world}",
                        "l2": "inputs (2.1 GB per step) larger than L2", "units_per_step": upstep},
             "clocks": clk, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": gpu_launches_step,
+            "gpu_launches": gpu_launches_per_step(args.prec, nq) * args.steps, "kernels": kernels,
         }))
     ctx.close()
     if world > 1:

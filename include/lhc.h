@@ -140,19 +140,22 @@ int lhc_spectator(lhc_ctx ctx, const lhc_lattice *lat, int kind, const void *S1_
                   const void *GB, const void *eta, int n_r, int t_sink, const int r[4],
                   const int *k, int nq, int prec, void *out, void *stream);
 
-/* Noise-averaged combine (Eqs. 5 and 8), FP64, for ng spin structures:
+/* Noise-averaged combine (Eqs. 5 and 8) for ng spin structures and nt insertion
+ * slices (index t):
  *
- * LHC_MESON:  out[g][p][q] = (1/n_r) sum_i sum Gsnk[g][ap][bp] Gins[g][at][bt] Gsrc[g][b][al]
- *                            spec[p][i][(bp, ap, al, a)] ins[q][i][(at, bt, b, a)]
+ * LHC_MESON:  out[t][g][p][q] = (1/n_r) sum_i sum Gsnk[g][ap][bp] Gins[g][at][bt] Gsrc[g][b][al]
+ *                               spec[p][i][(bp, ap, al, a)] ins[t][q][i][(at, bt, b, a)]
  *             snk, src: complex128 [ng][4][4]
- * LHC_BARYON: out[g][p][q] = (1/n_r) sum_{i,c} sum Wsnk[g][a1p][a2p][bp] Wsrc[g][a1][a2][b]
- *                            Gins[g][at][bt] spec[p][i][(a1p,a1,a2p,a2,bp,c)] ins[q][i][(at,bt,b,c)]
+ * LHC_BARYON: out[t][g][p][q] = (1/n_r) sum_{i,c} sum Wsnk[g][a1p][a2p][bp] Wsrc[g][a1][a2][b]
+ *                               Gins[g][at][bt] spec[p][i][(a1p,a1,a2p,a2,bp,c)] ins[t][q][i][(at,bt,b,c)]
  *             snk, src: complex128 [ng][4][4][4]
- * ins_g: complex128 [ng][4][4]; spec: [np][n_r][192 | 3072]; ins: [nq][n_r][192]
- * (one insertion slice); out: complex128 [ng][np][nq]. */
+ * ins_g: complex128 [ng][4][4]; spec: [np][n_r][192 | 3072]; ins: [nt][nq][n_r][192] (the
+ * output of lhc_insertion); out: complex128 [nt][ng][np][nq].
+ * prec LHC_FP64: everything in FP64.  LHC_MIXED: the Gamma contractions in FP64, the
+ * 12-term spin-colour sum of each noise in FP32, the sum over noises in FP64. */
 int lhc_combine(lhc_ctx ctx, int kind, const void *spec, int np, const void *ins, int nq,
-                int n_r, const void *snk, const void *ins_g, const void *src, int ng,
-                void *out, void *stream);
+                int n_r, int nt, const void *snk, const void *ins_g, const void *src, int ng,
+                int prec, void *out, void *stream);
 
 /* Kernel-level timing with CUDA events recorded on the launching stream, for
  * roofline measurements.  lhc_profile(ctx, 1) clears the records and starts
@@ -168,7 +171,8 @@ typedef enum {
   LHC_KERNEL_CONTRACT = 1,   /* FP64 site contraction                                  */
   LHC_KERNEL_FUSED = 2,      /* mixed path: fused contraction + tensor-core projection */
   LHC_KERNEL_REDUCE = 3,     /* mixed path: FP64 cross-block reduction                 */
-  LHC_KERNEL_COUNT = 4
+  LHC_KERNEL_COMBINE = 4,    /* FP64 combine (all of its kernels)                      */
+  LHC_KERNEL_COUNT = 5
 } lhc_kernel_id;
 
 int lhc_profile(lhc_ctx ctx, int enable);

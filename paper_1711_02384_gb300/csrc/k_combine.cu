@@ -6,6 +6,9 @@
 //           Xi[g][q][i,al,a] = sum_b Gsrc[b][al] sum_{at,bt} Gins[at][bt] I[q][i][at,bt,b,a]
 //   baryon  Xs[g][p][i,b,c]  = sum Wsnk[a1p][a2p][bp] Wsrc[a1][a2][b] B[p][i][a1p,a1,a2p,a2,bp,c]
 //           Xi[g][q][i,b,c]  = sum_{at,bt} Gins[at][bt] I[q][i][at,bt,b,c]
+// for every insertion slice t of the call.
+#include <type_traits>
+
 #include "lhc_internal.h"
 
 namespace lhc {
@@ -101,25 +104,69 @@ __global__ void comb_ins_baryon(const double2 *__restrict__ I, int nq, int n_r,
   Xi[idx] = acc;
 }
 
-// out[g][p][q] = (1/N) sum_K Xs[g][p][K] Xi[g][q][K]; one warp per output, fixed order
-__global__ void comb_dot(const double2 *__restrict__ Xs, const double2 *__restrict__ Xi, int np,
-                         int nq, int K, int ng, double inv_n, double2 *__restrict__ out) {
-  size_t w = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (w >= (size_t)ng * np * nq) return;
-  int q = (int)(w % nq);
-  size_t rest = w / nq;
-  int p = (int)(rest % np), g = (int)(rest / np);
-  const double2 *a = Xs + ((size_t)g * np + p) * K;
-  const double2 *b = Xi + ((size_t)g * nq + q) * K;
-  double2 acc = make_double2(0.0, 0.0);
-  for (int k = lane; k < K; k += 32) cfma(acc, a[k], b[k]);
+// out[t][g][p][q] = (1/N) sum_i sum_{j<12} Xs[g][p][12i+j] Xi[t][g][q][12i+j]: a tiled complex
+// GEMM.  FP64: all in double.  MIXED: the 12-term spin-colour sum of each noise in FP32,
+// the sum over noises (the noise average of Eq. 5) in FP64.
+constexpr int CT = 32;
+template <bool MIXED>
+__global__ void __launch_bounds__(256) comb_gemm(const double2 *__restrict__ Xs, const double2 *__restrict__ Xi,
+                                                 int np, int nq, int n_r, int ng, double inv_n,
+                                                 double2 *__restrict__ out) {
+  using E = typename std::conditional<MIXED, float2, double2>::type;
+  __shared__ E As[CT][13];
+  __shared__ E Bs[CT][13];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int q0 = blockIdx.x * CT, p0 = blockIdx.y * CT;
+  const int tg = blockIdx.z;                 // t * ng + g
+  const int g = tg % ng;
+  const size_t K = (size_t)12 * n_r;
+  const double2 *A = Xs + ((size_t)g * np) * K;
+  const double2 *B = Xi + ((size_t)tg * nq) * K;
+  double2 acc[2][2];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) acc[a][b] = make_double2(0.0, 0.0);
+  for (int i = 0; i < n_r; ++i) {
+    for (int e = threadIdx.x; e < CT * 12; e += 256) {
+      int r = e / 12, k = e % 12;
+      double2 va = (p0 + r < np) ? A[(size_t)(p0 + r) * K + 12 * i + k] : make_double2(0.0, 0.0);
+      double2 vb = (q0 + r < nq) ? B[(size_t)(q0 + r) * K + 12 * i + k] : make_double2(0.0, 0.0);
+      if constexpr (MIXED) {
+        As[r][k] = make_float2((float)va.x, (float)va.y);
+        Bs[r][k] = make_float2((float)vb.x, (float)vb.y);
+      } else {
+        As[r][k] = va;
+        Bs[r][k] = vb;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        E pa;
+        pa.x = 0;
+        pa.y = 0;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          E x = As[ty + 16 * a][k], y = Bs[tx + 16 * b][k];
+          pa.x = fma(x.x, y.x, fma(-x.y, y.y, pa.x));
+          pa.y = fma(x.x, y.y, fma(x.y, y.x, pa.y));
+        }
+        acc[a][b].x += (double)pa.x;
+        acc[a][b].y += (double)pa.y;
+      }
+    __syncthreads();
   }
-  if (lane == 0) out[w] = make_double2(acc.x * inv_n, acc.y * inv_n);
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      int p = p0 + ty + 16 * a, q = q0 + tx + 16 * b;
+      if (p < np && q < nq)
+        out[((size_t)tg * np + p) * nq + q] = make_double2(acc[a][b].x * inv_n, acc[a][b].y * inv_n);
+    }
 }
 
 unsigned blocks(size_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
@@ -127,22 +174,32 @@ unsigned blocks(size_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
 }  // namespace
 
 int run_combine(lhc_ctx ctx, int kind, const double2 *spec, int np, const double2 *ins, int nq,
-                int n_r, const double2 *snk, const double2 *ins_g, const double2 *src, int ng,
-                double2 *out, cudaStream_t st) {
+                int n_r, int nt, const double2 *snk, const double2 *ins_g, const double2 *src, int ng,
+                int prec, double2 *out, cudaStream_t st) {
   size_t K = (size_t)12 * n_r;
-  size_t ns = (size_t)ng * np * K, ni = (size_t)ng * nq * K;
+  size_t ns = (size_t)ng * np * K, ni = (size_t)nt * ng * nq * K;
   LHC_TRY(ensure(ctx, ctx->ws, (ns + ni) * sizeof(double2)));
   double2 *Xs = static_cast<double2 *>(ctx->ws.p);
   double2 *Xi = Xs + ns;
+  ProfScope ps(ctx, st, LHC_KERNEL_COMBINE, 8.0 * nt * ng * (double)np * nq * K);
   if (kind == LHC_MESON) {
     comb_spec_meson<<<blocks(ns, 256), 256, 0, st>>>(spec, np, n_r, snk, ng, Xs);
-    comb_ins_meson<<<blocks(ni, 256), 256, 0, st>>>(ins, nq, n_r, ins_g, src, ng, Xi);
+    // the insertion slices are consecutive [nq][n_r][192] blocks: treat them as nt*nq momenta
+    // with the Gamma sets repeated per slice (index g of slice t is t*ng + g)
+    for (int t = 0; t < nt; ++t)
+      comb_ins_meson<<<blocks((size_t)ng * nq * K, 256), 256, 0, st>>>(ins + (size_t)t * nq * n_r * 192, nq, n_r,
+                                                                       ins_g, src, ng, Xi + (size_t)t * ng * nq * K);
   } else {
     comb_spec_baryon<<<blocks(ns, 256), 256, 0, st>>>(spec, np, n_r, snk, src, ng, Xs);
-    comb_ins_baryon<<<blocks(ni, 256), 256, 0, st>>>(ins, nq, n_r, ins_g, ng, Xi);
+    for (int t = 0; t < nt; ++t)
+      comb_ins_baryon<<<blocks((size_t)ng * nq * K, 256), 256, 0, st>>>(ins + (size_t)t * nq * n_r * 192, nq, n_r,
+                                                                        ins_g, ng, Xi + (size_t)t * ng * nq * K);
   }
-  size_t nout = (size_t)ng * np * nq;
-  comb_dot<<<blocks(nout * 32, 256), 256, 0, st>>>(Xs, Xi, np, nq, (int)K, ng, 1.0 / n_r, out);
+  dim3 grid((nq + CT - 1) / CT, (np + CT - 1) / CT, nt * ng);
+  if (prec == LHC_MIXED)
+    comb_gemm<true><<<grid, 256, 0, st>>>(Xs, Xi, np, nq, n_r, ng, 1.0 / n_r, out);
+  else
+    comb_gemm<false><<<grid, 256, 0, st>>>(Xs, Xi, np, nq, n_r, ng, 1.0 / n_r, out);
   LHC_CHECK_CUDA(cudaGetLastError());
   return LHC_OK;
 }

@@ -1,15 +1,24 @@
-// Mixed-precision path (meson insertion and spectator):
+// Mixed-precision path for the meson insertion (Eq. 10) and spectator (Eq. 9): one
+// fused kernel per call that performs the site contraction in FP32 and the momentum
+// projection on tcgen05 tensor cores, plus an FP64 cross-block reduction.
 //
-//   1. contract_split: the site contraction (Eq. 10 / Eq. 9) in FP32, each value split
-//      into an FP16 pair hi + lo (hi = fp16(u), lo = fp16(u - hi)), written as the
-//      K-major operand tiles of the tensor-core GEMM (core matrices of 8 rows x 16 B).
-//   2. proj_mma: the momentum projection out[q][col] = sum_x P[q][x] U[x][col] as a
-//      complex GEMM on tcgen05 tensor cores.  Real and imaginary parts are two halves
-//      of one accumulator: D[:, 0:Np] = Ur Re - Ui Im, D[:, Np:2Np] = Ur Im + Ui Re, with
-//      three products per split pair (hi*hi + hi*lo + lo*hi), FP32 accumulation in
-//      tensor memory, drained every few k-steps into FP32 registers.  Operand tiles
-//      arrive by 1-D bulk copies into a ring of shared-memory stages.
-//   3. reduce_f64: FP64 sum of the per-site-range FP32 partials into complex128.
+// GEMM view: out[q][col] = sum_x P[q][x] U[x][col], x over the sites of a timeslice.
+// A CTA owns one tile of 128 columns (2 noises x 4 "vector" spins x 16 "matrix"
+// indices s), one chunk of <= 96 momenta and one range of sites:
+//
+//   warp 0      bulk-copies the phase tiles (FP16 hi/lo of [-Im | Re | Im], K-major)
+//   warp 1      allocates tensor memory and issues the MMAs
+//   warps 2-9   drain the accumulator every KD k-steps into an FP32 running sum
+//   warps 10-17 producers: gather the site inputs of 32 sites into shared memory,
+//               contract them in FP32, split each value into fp16 hi + lo and write
+//               the four A tiles (Ur hi, Ur lo, Ui hi, Ui lo), MN-major
+//
+// Per k-step (16 sites) the accumulator D (128 x 2Np, FP32, tensor memory) receives
+//   Ur_h [Re|Im]_h + Ur_h [Re|Im]_l + Ur_l [Re|Im]_h + Ui_h [-Im|Re]_h + Ui_h [-Im|Re]_l
+//   + Ui_l [-Im|Re]_h,
+// so D[:, :Np] = Re(P U) and D[:, Np:] = Im(P U) with the lo*lo term dropped.  Tensor
+// memory accumulation truncates, so D is double-buffered and drained every KD k-steps;
+// each CTA writes FP32 partial sums that reduce_f64 adds in FP64.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -20,15 +29,23 @@
 namespace lhc {
 namespace {
 
-constexpr int MT = 128;            // GEMM M tile: output columns per CTA
-constexpr int KSTEP = 16;          // sites per MMA k-step
-constexpr int ATILE = MT * KSTEP * 2;   // bytes of one 128x16 fp16 operand tile
-constexpr int ASTAGE = 4 * ATILE;  // Ur hi, Ur lo, Ui hi, Ui lo
+constexpr int MT = 128;                  // GEMM M tile: output columns per CTA
+constexpr int KSTEP = 16;                // sites per MMA k-step
+constexpr int QCHUNK = 96;               // momenta per CTA (accumulator registers bound this)
+constexpr int ATILE = MT * KSTEP * 2;    // bytes of one 128 x 16 fp16 operand tile
+constexpr int ASTAGE = 4 * ATILE;        // Ur hi, Ur lo, Ui hi, Ui lo
 constexpr int NSTAGE = 4;
-constexpr int kThreads = 320;      // warp 0 bulk copies, warp 1 MMA, warps 2..9 drain
+constexpr int PSITES = 32;               // sites per producer iteration (two k-steps)
+constexpr int RVALS = 72;                // gathered complex values per site and tile
+constexpr int RPITCH = PSITES + 1;       // padded row of the transposed gather buffer
+constexpr int kWarps = 18;
+constexpr int kThreads = kWarps * 32;
+constexpr int kDrainWarp0 = 2;
+constexpr int kProdWarp0 = 10;
+constexpr uint32_t kTmemCols = 512;
 
-// byte offset of element (row, k) in a K-major no-swizzle tile with 16 k per row block
-__host__ __device__ __forceinline__ uint32_t core_off(int row, int k) {
+// K-major, no swizzle: (row, k) -> core matrices of 8 rows x 16 B; 16 k per row block
+__host__ __device__ __forceinline__ uint32_t kmajor_off(int row, int k) {
   return (uint32_t)((row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
@@ -37,14 +54,20 @@ struct SlicePtrs {
   const void *vec;
 };
 
-__device__ __forceinline__ float2 ldc(const double2 *p) {
-  double2 v = *p;
-  return make_float2((float)v.x, (float)v.y);
+__device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ float2 to_f2(float2 v) { return v; }
+template <typename CT>
+__device__ __forceinline__ CT czero() {
+  CT z;
+  z.x = 0;
+  z.y = 0;
+  return z;
 }
-__device__ __forceinline__ float2 ldc(const float2 *p) { return *p; }
+
+__device__ __forceinline__ void bar_producers() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 // ------------------------------------------------------------ phase table (FP16 split)
-// layout [qc][kb][hl][3*Np rows: -Im | Re | Im][16 sites], each (qc,kb,hl) block in core order
+// layout [qc][kb][hl][3*Np rows: -Im | Re | Im][16 sites], each (qc,kb,hl) block K-major
 __global__ void phase_split_kernel(__half *out, const int *k, int nq, int Np, int nqc, int nkb, int L,
                                    int rx, int ry, int rz, int sign, const double2 *roots) {
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -60,8 +83,8 @@ __global__ void phase_split_kernel(__half *out, const int *k, int nq, int Np, in
   int kb = (int)(rest % nkb);
   int qc = (int)(rest / nkb);
   int g = n / Np, qi = n % Np;
-  int q = qc * 128 + qi;
-  int qend = min(nq, (qc + 1) * 128);
+  int q = qc * QCHUNK + qi;
+  int qend = min(nq, (qc + 1) * QCHUNK);
   int V3 = L * L * L;
   int x = kb * KSTEP + kk;
   double v = 0.0;
@@ -78,115 +101,64 @@ __global__ void phase_split_kernel(__half *out, const int *k, int nq, int Np, in
   __half lo = __double2half(v - (double)__half2float(hi));
   size_t block = ((size_t)qc * nkb + kb) * 2 + hl;
   char *base = reinterpret_cast<char *>(out) + block * (size_t)rows * 32;
-  *reinterpret_cast<__half *>(base + core_off(n, kk)) = hl ? lo : hi;
+  *reinterpret_cast<__half *>(base + kmajor_off(n, kk)) = hl ? lo : hi;
 }
 
-// ------------------------------------------------------------ contraction + split
-// One thread per (slice, column tile, site block, row, 8-site half): computes U for
-// column ct*128 + row on 8 sites and writes 16 bytes into each of the 4 tiles.
-template <typename CT, int MODE>
-__global__ void contract_split(const SlicePtrs *__restrict__ sl, size_t vec_stride, int n_r, int V3,
-                               int nct, int nkb, int g5mask, char *__restrict__ ws) {
-  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (size_t)gridDim.x * blockDim.x) return;
-  int kc = (int)(idx & 1);
-  size_t rest = idx >> 1;
-  int row = (int)(rest % MT);
-  rest /= MT;
-  int kb = (int)(rest % nkb);
-  rest /= nkb;
-  int ct = (int)(rest % nct);
-  int j = (int)(rest / nct);
-  const int ncols = n_r * 192;
-  int col = ct * MT + row;
-  const CT *S = static_cast<const CT *>(sl[j].S);
-  const CT *vec = static_cast<const CT *>(sl[j].vec);
-  uint32_t pk[4][4];   // [tile][packed pairs]
-  int i = col / 192, c = col % 192, v = c / 48, s = c % 48;
-  int srow = (s / 12) * 3, scol = s % 12;
-  float g;
-  if (MODE == 0)
-    g = ((g5mask >> v) & 1) ? -1.f : 1.f;
-  else
-    g = (((g5mask >> v) ^ (g5mask >> (s / 12)) ^ (g5mask >> ((s % 12) / 3))) & 1) ? -1.f : 1.f;
-#pragma unroll
-  for (int e = 0; e < 8; e += 2) {
-    __half h[2][4];
-#pragma unroll
-    for (int e2 = 0; e2 < 2; ++e2) {
-      int x = kb * KSTEP + kc * 8 + e + e2;
-      float2 u = make_float2(0.f, 0.f);
-      if (col < ncols && x < V3) {
-        const CT *Sx = S + (size_t)x * 144;
-        const CT *vx = vec + (size_t)i * vec_stride + (size_t)x * 12 + v * 3;
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc) {
-          float2 a = ldc(vx + cc);
-          float2 b = ldc(Sx + (srow + cc) * 12 + scol);
-          if (MODE == 0) {   // conj(psi) * S
-            u.x += a.x * b.x + a.y * b.y;
-            u.y += a.x * b.y - a.y * b.x;
-          } else {           // eta * conj(S)
-            u.x += a.x * b.x + a.y * b.y;
-            u.y += a.y * b.x - a.x * b.y;
-          }
-        }
-        u.x *= g;
-        u.y *= g;
-      }
-      __half rh = __float2half_rn(u.x), ih = __float2half_rn(u.y);
-      h[e2][0] = rh;
-      h[e2][1] = __float2half_rn(u.x - __half2float(rh));
-      h[e2][2] = ih;
-      h[e2][3] = __float2half_rn(u.y - __half2float(ih));
-    }
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      __half2 p = __halves2half2(h[0][t], h[1][t]);
-      pk[t][e / 2] = *reinterpret_cast<uint32_t *>(&p);
-    }
-  }
-  char *tile = ws + (((size_t)j * nct + ct) * nkb + kb) * ASTAGE;
-#pragma unroll
-  for (int t = 0; t < 4; ++t)
-    *reinterpret_cast<uint4 *>(tile + t * ATILE + core_off(row, kc * 8)) =
-        make_uint4(pk[t][0], pk[t][1], pk[t][2], pk[t][3]);
-}
+// ------------------------------------------------------------ fused kernel
+constexpr int kMaxSlices = 64;   // slices per launch (pointers travel as kernel parameters)
 
-// ------------------------------------------------------------ tensor-core projection
-struct MmaParams {
-  const char *A;        // [nt][nct][nkb][ASTAGE]
-  const __half *B;      // [nqc][nkb][2][3Np][16]
-  float2 *partial;      // [nt][nsplit][nq][ncols]
+struct FusedParams {
+  SlicePtrs slices[kMaxSlices];   // per slice: propagator slice [V3][144], vec (psi or eta) noise 0
+  size_t vec_stride;         // elements between noises of vec
+  const __half *B;           // phase table
+  float2 *partial;           // [nt][nsplit][nq][ncols]
   int *err;
-  int nct, nkb, nqc, nq, ncols, nsplit, kd;
+  int n_r, V3, nct, nkb, nqc, nq, ncols, nsplit, kd, g5mask;
 };
 
-template <int NP>
-__global__ void __launch_bounds__(kThreads, 1) proj_mma(MmaParams p) {
-  constexpr int BSTAGE = 2 * 3 * NP * 32;                 // hi and lo blocks of [-Im|Re|Im]
-  constexpr uint32_t TMEM_COLS = (4 * NP <= 32) ? 32 : (4 * NP <= 64) ? 64 : (4 * NP <= 128) ? 128
-                                 : (4 * NP <= 256) ? 256 : 512;
+// fp16 hi/lo split of two floats, packed as half2 pairs
+__device__ __forceinline__ void split2(float v0, float v1, uint32_t &hi, uint32_t &lo) {
+  __half2 h = __floats2half2_rn(v0, v1);
+  float2 hf = __half22float2(h);
+  __half2 l = __floats2half2_rn(v0 - hf.x, v1 - hf.y);
+  hi = *reinterpret_cast<uint32_t *>(&h);
+  lo = *reinterpret_cast<uint32_t *>(&l);
+}
+
+template <typename CT, int MODE, int NP>
+__global__ void __launch_bounds__(kThreads, 1) fused_meson(FusedParams p) {
+  static_assert(NP % 16 == 0 && NP <= QCHUNK, "momentum chunk");
+  constexpr int BSTAGE = 2 * 3 * NP * 32;
+  // tensor memory: D buffers [0, 2NP) and [2NP, 4NP); the rest holds NT columns of each
+  // half's running sum, the remaining NR = NP - NT columns stay in registers
+  constexpr int NT = ((kTmemCols - 4 * NP) / 2 / 16 * 16) < NP ? ((kTmemCols - 4 * NP) / 2 / 16 * 16) : NP;
+  constexpr int NR = NP - NT;
   extern __shared__ __align__(1024) char smem[];
   char *sA = smem;
-  char *sB = smem + NSTAGE * ASTAGE;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(sB + NSTAGE * BSTAGE);
-  uint64_t *full = bars, *empty = bars + NSTAGE, *tfull = bars + 2 * NSTAGE, *tempty = bars + 2 * NSTAGE + 2,
-           *done = bars + 2 * NSTAGE + 4;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NSTAGE + 5);
+  char *sB = sA + NSTAGE * ASTAGE;
+  float2 *R = reinterpret_cast<float2 *>(sB + NSTAGE * BSTAGE);        // [RVALS][RPITCH]
+  uint64_t *bars = reinterpret_cast<uint64_t *>(R + RVALS * RPITCH);
+  uint64_t *fullA = bars, *fullB = bars + NSTAGE, *empty = bars + 2 * NSTAGE,
+           *tfull = bars + 3 * NSTAGE, *tempty = bars + 3 * NSTAGE + 2, *done = bars + 3 * NSTAGE + 4;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 3 * NSTAGE + 5);
+  volatile int *stop_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ct = blockIdx.x, split = blockIdx.y;
   const int j = blockIdx.z / p.nqc, qc = blockIdx.z % p.nqc;
-  const int kb0 = (int)((long long)p.nkb * split / p.nsplit);
-  const int kb1 = (int)((long long)p.nkb * (split + 1) / p.nsplit);
+  // site range in k-steps; splits start on even k-steps so producer iterations align
+  const int npair = (p.nkb + 1) / 2;
+  const int kb0 = 2 * (int)((long long)npair * split / p.nsplit);
+  const int kb1 = min(p.nkb, 2 * (int)((long long)npair * (split + 1) / p.nsplit));
   const int nk = kb1 - kb0;
   const int nchunks = (nk + p.kd - 1) / p.kd;
   volatile int *err = p.err;
+  const int i0 = 2 * (ct / 3), s0 = 16 * (ct % 3);   // first noise and first s of this tile
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
-      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&fullA[s], 1);
+      tc::mbar_init(&fullB[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -194,38 +166,39 @@ __global__ void __launch_bounds__(kThreads, 1) proj_mma(MmaParams p) {
       tc::mbar_init(&tempty[b], 8);
     }
     tc::mbar_init(done, 1);
+    *stop_flag = 0;
     tc::fence_mbar_init();
   }
-  if (warp == 1) tc::tmem_alloc(tmem_slot, TMEM_COLS);
+  if (warp == 1) tc::tmem_alloc(tmem_slot, kTmemCols);
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tbase = *tmem_slot;
 
   if (warp == 0) {
-    if (lane == 0) {
-      const char *Asrc = p.A + (((size_t)j * p.nct + ct) * p.nkb + kb0) * ASTAGE;
+    // ---------------------------------------------------- phase tiles
+    if (lane == 0 && nk > 0) {
       const char *Bsrc = reinterpret_cast<const char *>(p.B) + ((size_t)qc * p.nkb + kb0) * BSTAGE;
       int issued = 0;
       for (int i = 0; i < nk; ++i) {
         int s = i % NSTAGE, u = i / NSTAGE;
         if (u > 0 && !tc::mbar_wait(&empty[s], (u - 1) & 1, err, 1)) break;
-        tc::mbar_arrive_expect_tx(&full[s], ASTAGE + BSTAGE);
-        tc::bulk_g2s(sA + s * ASTAGE, Asrc + (size_t)i * ASTAGE, ASTAGE, &full[s]);
-        tc::bulk_g2s(sB + s * BSTAGE, Bsrc + (size_t)i * BSTAGE, BSTAGE, &full[s]);
+        tc::mbar_arrive_expect_tx(&fullB[s], BSTAGE);
+        tc::bulk_g2s(sB + s * BSTAGE, Bsrc + (size_t)i * BSTAGE, BSTAGE, &fullB[s]);
         issued = i + 1;
       }
-      // never leave the CTA with copies still landing in shared memory
-      for (int i = max(0, issued - NSTAGE); i < issued; ++i) {
+      for (int i = max(0, issued - NSTAGE); i < issued; ++i) {   // nothing may still be landing
         int s = i % NSTAGE, u = i / NSTAGE;
         long long t0 = clock64();
-        while (!tc::mbar_try_wait(&full[s], u & 1) && clock64() - t0 < tc::kSpinLimit) {
+        while (!tc::mbar_try_wait(&fullB[s], u & 1) && clock64() - t0 < tc::kSpinLimit) {
         }
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      constexpr uint32_t idesc = tc::idesc_f16(MT, 2 * NP);
+    // ---------------------------------------------------- MMA issue
+    if (lane == 0 && nk > 0) {
+      // A: MN-major (row m = s*8 + noise*4 + spin), core matrices 8 k x 16 B: LBO (k) 128, SBO (m) 256
+      constexpr uint32_t idesc = tc::idesc_f16(MT, 2 * NP) | (1u << 15);
       const uint32_t aBase = tc::smem_u32(sA), bBase = tc::smem_u32(sB);
       int i = 0;
       bool ok = true;
@@ -237,14 +210,12 @@ __global__ void __launch_bounds__(kThreads, 1) proj_mma(MmaParams p) {
         int iend = min(nk, (c + 1) * p.kd);
         for (; i < iend; ++i) {
           int s = i % NSTAGE, u = i / NSTAGE;
-          if (!tc::mbar_wait(&full[s], u & 1, err, 3)) {
+          if (!tc::mbar_wait(&fullB[s], u & 1, err, 3) || !tc::mbar_wait(&fullA[s], u & 1, err, 4)) {
             ok = false;
             break;
           }
           tc::tc_fence_after();
           uint32_t a = aBase + s * ASTAGE, bb = bBase + s * BSTAGE;
-          // A tiles: 0 Ur hi, 1 Ur lo, 2 Ui hi, 3 Ui lo; B: hl block h at bb + h*3*NP*32,
-          // rows [0,NP) = -Im, [NP,2NP) = Re, [2NP,3NP) = Im
           auto dA = [&](int t) { return tc::smem_desc(a + t * ATILE, 128, 256); };
           auto dB = [&](int h, int row0) { return tc::smem_desc(bb + h * 3 * NP * 32 + row0 * 32, 128, 256); };
           uint32_t acc0 = (i == c * p.kd) ? 0u : 1u;
@@ -263,43 +234,196 @@ __global__ void __launch_bounds__(kThreads, 1) proj_mma(MmaParams p) {
       while (!tc::mbar_try_wait(done, 0) && clock64() - t0 < tc::kSpinLimit) {
       }
     }
-  } else {
-    // drain warps: quadrant = warp % 4 (TMEM lane access rule), half 0 = real, 1 = imag
-    const int qd = warp & 3, h = (warp - 2) >> 2;
+  } else if (warp < kProdWarp0) {
+    // ---------------------------------------------------- drain (quadrant = warp % 4)
+    const int qd = warp & 3, h = (warp - kDrainWarp0) >> 2;
     const int row = qd * 32 + lane;
-    float acc[NP];
+    const uint32_t lane_base = tbase + ((uint32_t)(qd * 32) << 16);
+    const uint32_t rsum = lane_base + (uint32_t)(4 * NP + h * NT);   // this half's running sum in TMEM
+    float acc[NR > 0 ? NR : 1];
 #pragma unroll
-    for (int n = 0; n < NP; ++n) acc[n] = 0.f;
+    for (int n = 0; n < NR; ++n) acc[n] = 0.f;
     for (int c = 0; c < nchunks; ++c) {
       int b = c & 1, ub = c >> 1;
-      if (!tc::mbar_wait(&tfull[b], ub & 1, err, 4)) break;
+      if (!tc::mbar_wait(&tfull[b], ub & 1, err, 5)) break;
       tc::tc_fence_after();
-      const uint32_t t = tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * 2 * NP + h * NP);
+      const uint32_t t = lane_base + (uint32_t)(b * 2 * NP + h * NP);
 #pragma unroll
       for (int n0 = 0; n0 < NP; n0 += 16) {
         float v[16];
         tc::tmem_ld16(t + n0, v);
-        tc::tmem_wait_ld();
+        if (n0 < NT) {
+          float r[16];
+          if (c > 0) tc::tmem_ld16(rsum + n0, r);
+          tc::tmem_wait_ld();
 #pragma unroll
-        for (int e = 0; e < 16; ++e) acc[n0 + e] += v[e];
+          for (int e = 0; e < 16; ++e) r[e] = c > 0 ? r[e] + v[e] : v[e];
+          tc::tmem_st16(rsum + n0, r);
+        } else {
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 16; ++e) acc[n0 - NT + e] += v[e];
+        }
       }
+      tc::tmem_wait_st();
       tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&tempty[b]);
     }
-    const int col = ct * MT + row;
-    const int qend = min(p.nq - qc * 128, NP);
-    if (col < p.ncols && !*err) {
+    // row -> (s, noise, spin): m = sl*8 + ii*4 + v
+    const int sl = row >> 3, ii = (row >> 2) & 1, v = row & 3;
+    const int noise = i0 + ii;
+    const int col = noise * 192 + v * 48 + s0 + sl;
+    const int qend = min(p.nq - qc * QCHUNK, NP);
+    if (noise < p.n_r && !*err && nk > 0) {
       float *out = reinterpret_cast<float *>(p.partial + ((size_t)j * p.nsplit + split) * p.nq * p.ncols);
 #pragma unroll
-      for (int n = 0; n < NP; ++n)
-        if (n < qend) out[((size_t)(qc * 128 + n) * p.ncols + col) * 2 + h] = acc[n];
+      for (int n0 = 0; n0 < NT; n0 += 16) {
+        float r[16];
+        tc::tmem_ld16(rsum + n0, r);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+          if (n0 + e < qend) out[((size_t)(qc * QCHUNK + n0 + e) * p.ncols + col) * 2 + h] = r[e];
+      }
+#pragma unroll
+      for (int n = 0; n < NR; ++n)
+        if (NT + n < qend) out[((size_t)(qc * QCHUNK + NT + n) * p.ncols + col) * 2 + h] = acc[n];
+    }
+  } else {
+    // ---------------------------------------------------- producers
+    const int pt = threadIdx.x - kProdWarp0 * 32;      // 0..255
+    const int slp = warp - kProdWarp0;                  // compute role: s pair (2*slp, 2*slp+1)
+    const CT *S = static_cast<const CT *>(p.slices[j].S);
+    const CT *vec = static_cast<const CT *>(p.slices[j].vec);
+    const int nit = (nk + 1) / 2;
+    // gather role: values e = pt + 256*jj of the 32 x 72 per iteration; e < 1536 are the
+    // 48 propagator entries (colour c, s) of each site, the rest the 2 x 12 noise-vector
+    // entries.  The next iteration's lines are prefetched into L1 one iteration ahead.
+    auto source = [&](int it, int jj, int &w, int &x) -> const CT * {
+      int e = pt + 256 * jj, off;
+      size_t stride;
+      const CT *src;
+      if (e < 1536) {
+        x = e / 48;
+        w = e % 48;
+        int c = w >> 4, s = s0 + (w & 15);
+        off = ((s / 12) * 3 + c) * 12 + s % 12;
+        src = S;
+        stride = 144;
+      } else {
+        int e2 = e - 1536;
+        x = e2 / 24;
+        int ww = e2 % 24, noise = i0 + ww / 12;
+        w = 48 + ww;
+        off = ww % 12;
+        src = noise < p.n_r ? vec + (size_t)noise * p.vec_stride : nullptr;
+        stride = 12;
+      }
+      int site = 16 * kb0 + PSITES * it + x;
+      if (src == nullptr || site >= 16 * kb1 || site >= p.V3) return nullptr;
+      return src + (size_t)site * stride + off;
+    };
+    auto prefetch = [&](int it) {
+#pragma unroll
+      for (int jj = 0; jj < 9; ++jj) {
+        int w, x;
+        const CT *a = source(it, jj, w, x);
+        if (a) asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+      }
+    };
+    auto gather = [&](int it) {
+#pragma unroll
+      for (int jj = 0; jj < 9; ++jj) {
+        int w, x;
+        const CT *a = source(it, jj, w, x);
+        R[w * RPITCH + x] = a ? to_f2(__ldg(a)) : make_float2(0.f, 0.f);
+      }
+    };
+    // gamma5 signs: the vector spin v (both modes) and, for the spectator, the two matrix
+    // spins carried by s = (bt, b, a); folded into the operands below
+    float sgs[2];
+#pragma unroll
+    for (int jx = 0; jx < 2; ++jx) {
+      int s = s0 + 2 * slp + jx;
+      int m = MODE == 0 ? 0 : ((p.g5mask >> (s / 12)) ^ (p.g5mask >> ((s % 12) / 3)));
+      sgs[jx] = (m & 1) ? -1.f : 1.f;
+    }
+    if (nit > 0) prefetch(0);
+    for (int it = 0; it < nit; ++it) {
+      if (it + 1 < nit) prefetch(it + 1);
+      gather(it);
+      if (pt == 0) *stop_flag = *err;
+      bar_producers();
+      if (*stop_flag) break;
+      // this thread: site x = lane (k-step 2*it + lane/16), s = s0 + 2*slp + {0,1}
+      const int x = lane, kstep = 2 * it + (x >> 4), kk = x & 15;
+      if (kstep < nk) {
+        const int s = kstep % NSTAGE, u = kstep / NSTAGE;
+        if (u > 0) tc::mbar_wait(&empty[s], (u - 1) & 1, err, 6);
+        float2 acc[2][8];
+#pragma unroll
+        for (int jx = 0; jx < 2; ++jx)
+#pragma unroll
+          for (int iv = 0; iv < 8; ++iv) acc[jx][iv] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float2 sv[2];
+#pragma unroll
+          for (int jx = 0; jx < 2; ++jx) {
+            sv[jx] = R[(c * 16 + 2 * slp + jx) * RPITCH + x];
+            sv[jx].x *= sgs[jx];
+            sv[jx].y *= sgs[jx];
+          }
+#pragma unroll
+          for (int iv = 0; iv < 8; ++iv) {
+            float2 pv = R[(48 + (iv >> 2) * 12 + (iv & 3) * 3 + c) * RPITCH + x];
+            if ((p.g5mask >> (iv & 3)) & 1) {
+              pv.x = -pv.x;
+              pv.y = -pv.y;
+            }
+#pragma unroll
+            for (int jx = 0; jx < 2; ++jx) {
+              float2 &a = acc[jx][iv];
+              if (MODE == 0) {   // conj(psi) * S
+                a.x = fmaf(pv.x, sv[jx].x, fmaf(pv.y, sv[jx].y, a.x));
+                a.y = fmaf(pv.x, sv[jx].y, fmaf(-pv.y, sv[jx].x, a.y));
+              } else {           // eta * conj(S)
+                a.x = fmaf(pv.x, sv[jx].x, fmaf(pv.y, sv[jx].y, a.x));
+                a.y = fmaf(pv.y, sv[jx].x, fmaf(-pv.x, sv[jx].y, a.y));
+              }
+            }
+          }
+        }
+        char *a_st = sA + s * ASTAGE;
+#pragma unroll
+        for (int jx = 0; jx < 2; ++jx) {
+          uint32_t rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+          for (int pr = 0; pr < 4; ++pr) {
+            split2(acc[jx][2 * pr].x, acc[jx][2 * pr + 1].x, rh[pr], rl[pr]);
+            split2(acc[jx][2 * pr].y, acc[jx][2 * pr + 1].y, ih[pr], il[pr]);
+          }
+          // MN-major tile: m-group = s (2*slp + jx), its 8 rows contiguous at k = kk
+          uint32_t off = (uint32_t)((2 * slp + jx) * 256 + (kk >> 3) * 128 + (kk & 7) * 16);
+          *reinterpret_cast<uint4 *>(a_st + 0 * ATILE + off) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+          *reinterpret_cast<uint4 *>(a_st + 1 * ATILE + off) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+          *reinterpret_cast<uint4 *>(a_st + 2 * ATILE + off) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+          *reinterpret_cast<uint4 *>(a_st + 3 * ATILE + off) = make_uint4(il[0], il[1], il[2], il[3]);
+        }
+      }
+      tc::fence_proxy_async_smem();
+      bar_producers();
+      if (pt == 0) {
+        tc::mbar_arrive(&fullA[(2 * it) % NSTAGE]);
+        if (2 * it + 1 < nk) tc::mbar_arrive(&fullA[(2 * it + 1) % NSTAGE]);
+      }
     }
   }
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  if (warp == 1) tc::tmem_dealloc(tbase, TMEM_COLS);
+  if (warp == 1) tc::tmem_dealloc(tbase, kTmemCols);
 }
 
 // out[j][q][col] = sum over splits of the FP32 partials, in FP64
@@ -320,37 +444,55 @@ __global__ void reduce_f64(const float2 *__restrict__ part, int nsplit, size_t p
 }
 
 template <int NP>
-int launch_mma(const MmaParams &p, int nt, cudaStream_t st) {
-  constexpr int BSTAGE = 2 * 3 * NP * 32;
-  size_t smem = (size_t)NSTAGE * (ASTAGE + BSTAGE) + 2 * NSTAGE * 8 + 5 * 8 + 16;
-  smem = std::max<size_t>(smem, 120 * 1024);   // one CTA per SM: tensor memory is never contended
+constexpr size_t fused_smem() {
+  return (size_t)NSTAGE * (ASTAGE + 2 * 3 * NP * 32) + (size_t)RVALS * RPITCH * 8 + (3 * NSTAGE + 5) * 8 + 16;
+}
+
+template <typename CT, int MODE, int NP>
+int launch_fused_t(const FusedParams &p, int nt, cudaStream_t st) {
+  const size_t smem = std::max<size_t>(fused_smem<NP>(), 120 * 1024);   // one CTA per SM
   static bool attr = false;
   if (!attr) {
-    LHC_CHECK_CUDA(cudaFuncSetAttribute(proj_mma<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LHC_CHECK_CUDA(cudaFuncSetAttribute(fused_meson<CT, MODE, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
     attr = true;
   }
   dim3 grid(p.nct, p.nsplit, nt * p.nqc);
-  proj_mma<NP><<<grid, kThreads, smem, st>>>(p);
+  fused_meson<CT, MODE, NP><<<grid, kThreads, smem, st>>>(p);
   return LHC_OK;
 }
 
-int launch_mma_np(int Np, const MmaParams &p, int nt, cudaStream_t st) {
+template <typename CT, int MODE>
+int launch_fused_np(int Np, const FusedParams &p, int nt, cudaStream_t st) {
   switch (Np) {
-    case 16: return launch_mma<16>(p, nt, st);
-    case 32: return launch_mma<32>(p, nt, st);
-    case 48: return launch_mma<48>(p, nt, st);
-    case 64: return launch_mma<64>(p, nt, st);
-    case 80: return launch_mma<80>(p, nt, st);
-    case 96: return launch_mma<96>(p, nt, st);
-    case 112: return launch_mma<112>(p, nt, st);
-    case 128: return launch_mma<128>(p, nt, st);
-    default: set_error("unsupported Np %d", Np); return LHC_EINVAL;
+    case 16: return launch_fused_t<CT, MODE, 16>(p, nt, st);
+    case 32: return launch_fused_t<CT, MODE, 32>(p, nt, st);
+    case 48: return launch_fused_t<CT, MODE, 48>(p, nt, st);
+    case 64: return launch_fused_t<CT, MODE, 64>(p, nt, st);
+    case 80: return launch_fused_t<CT, MODE, 80>(p, nt, st);
+    case 96: return launch_fused_t<CT, MODE, 96>(p, nt, st);
+    default: set_error("unsupported momentum chunk %d", Np); return LHC_EINVAL;
   }
+}
+
+// number of site splits: fill whole waves of one CTA per SM as well as possible
+int choose_nsplit(int base_ctas, int nk_pairs, int sms) {
+  int best = 1;
+  double best_eff = 0.0;
+  for (int s = 1; s <= 8 && s <= std::max(1, nk_pairs / 2); ++s) {
+    long long w = (long long)base_ctas * s;
+    long long waves = (w + sms - 1) / sms;
+    double eff = (double)w / (double)(waves * sms);
+    if (eff > best_eff + 0.02) {
+      best_eff = eff;
+      best = s;
+    }
+  }
+  return best;
 }
 
 }  // namespace
 
-// Mixed phase table: cached like the FP64 one (fmt 1).
 static int get_phase_split(lhc_ctx ctx, int L, const int *k, int nq, const int r[4], int sign, int Np, int nqc,
                            int nkb, cudaStream_t st, const __half **out) {
   PhaseKey key{L, nq, sign, 1, ((r[0] % L) + L) % L, ((r[1] % L) + L) % L, ((r[2] % L) + L) % L, hash_k(k, nq)};
@@ -393,76 +535,55 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
   }
   const int V3 = j0.V3, n_r = j0.n_r;
   const int ncols = n_r * 192;
-  const int nct = (ncols + MT - 1) / MT;
+  const int nct = 3 * ((n_r + 1) / 2);
   const int nkb = (V3 + KSTEP - 1) / KSTEP;
-  const int nqc = (nq + 127) / 128;
-  const int nq_max_chunk = std::min(nq, 128);
-  const int Np = ((nq_max_chunk + 15) / 16) * 16;
+  const int nqc = (nq + QCHUNK - 1) / QCHUNK;
+  const int Np = ((std::min(nq, QCHUNK) + 15) / 16) * 16;
   const __half *phase = nullptr;
   LHC_TRY(get_phase_split(ctx, j0.L, k, nq, r, sign, Np, nqc, nkb, st, &phase));
 
-  // site-range split so that the grid covers the GPU about twice
-  int ctas = nct * nt * nqc;
-  int nsplit = std::max(1, std::min(nkb / 8, (2 * ctx->num_sms + ctas - 1) / ctas));
-  int kd = 4;   // k-steps accumulated in tensor memory between drains
-  // tuning overrides (benchmarks and accuracy studies)
+  int nsplit = choose_nsplit(nct * nt * nqc, (nkb + 1) / 2, ctx->num_sms);
+  int kd = 4;   // k-steps accumulated in tensor memory between drains (truncating accumulation)
   if (const char *e = getenv("LHC_KD")) kd = std::max(1, atoi(e));
-  if (const char *e = getenv("LHC_NSPLIT")) nsplit = std::max(1, std::min(nkb, atoi(e)));
+  if (const char *e = getenv("LHC_NSPLIT")) nsplit = std::max(1, std::min((nkb + 1) / 2, atoi(e)));
 
-  size_t a_bytes = (size_t)nt * nct * nkb * ASTAGE;
-  size_t p_bytes = (size_t)nt * nsplit * nq * ncols * sizeof(float2);
-  size_t s_bytes = (size_t)nt * sizeof(SlicePtrs);
-  size_t off_p = (a_bytes + 255) & ~(size_t)255;
-  size_t off_s = (off_p + p_bytes + 255) & ~(size_t)255;
-  size_t off_e = (off_s + s_bytes + 255) & ~(size_t)255;
-  LHC_TRY(ensure(ctx, ctx->ws, off_e + 256));
+  const int ntl = std::min(nt, kMaxSlices);   // slices per launch
+  size_t p_bytes = (size_t)ntl * nsplit * nq * ncols * sizeof(float2);
+  LHC_TRY(ensure(ctx, ctx->ws, p_bytes));
   char *ws = static_cast<char *>(ctx->ws.p);
-  std::vector<SlicePtrs> sp(nt);
-  for (int j = 0; j < nt; ++j) sp[j] = SlicePtrs{jobs[j].S, jobs[j].vec};
-  LHC_CHECK_CUDA(cudaMemcpyAsync(ws + off_s, sp.data(), s_bytes, cudaMemcpyHostToDevice, st));
-  int *err = ctx->dev_err;
 
-  {
-    size_t threads = (size_t)nt * nct * nkb * MT * 2;
-    unsigned grid = (unsigned)((threads + 255) / 256);
-    size_t es = j0.dtype == LHC_C128 ? 16 : 8;
-    ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT,
-                 (double)nt * V3 * (144.0 + 12.0 * n_r) * es + (double)a_bytes);
-    const SlicePtrs *spd = reinterpret_cast<const SlicePtrs *>(ws + off_s);
-    bool ins = j0.part == PART_INS;
-    if (j0.dtype == LHC_C128) {
-      if (ins)
-        contract_split<double2, 0><<<grid, 256, 0, st>>>(spd, j0.vec_stride, n_r, V3, nct, nkb, j0.g5mask, ws);
+  FusedParams fp;
+  fp.vec_stride = j0.vec_stride;
+  fp.B = phase;
+  fp.partial = reinterpret_cast<float2 *>(ws);
+  fp.err = ctx->dev_err;
+  fp.n_r = n_r;
+  fp.V3 = V3;
+  fp.nct = nct;
+  fp.nkb = nkb;
+  fp.nqc = nqc;
+  fp.nq = nq;
+  fp.ncols = ncols;
+  fp.nsplit = nsplit;
+  fp.kd = kd;
+  fp.g5mask = j0.g5mask;
+  const size_t n_out = (size_t)nq * ncols;
+  for (int jb = 0; jb < nt; jb += kMaxSlices) {
+    const int nb = std::min(kMaxSlices, nt - jb);
+    for (int j = 0; j < nb; ++j) fp.slices[j] = SlicePtrs{jobs[jb + j].S, jobs[jb + j].vec};
+    {
+      ProfScope ps(ctx, st, LHC_KERNEL_FUSED, 8.0 * nb * (double)nq * ncols * V3);
+      bool ins = j0.part == PART_INS;
+      if (j0.dtype == LHC_C128)
+        LHC_TRY((ins ? launch_fused_np<double2, 0>(Np, fp, nb, st) : launch_fused_np<double2, 1>(Np, fp, nb, st)));
       else
-        contract_split<double2, 1><<<grid, 256, 0, st>>>(spd, j0.vec_stride, n_r, V3, nct, nkb, j0.g5mask, ws);
-    } else {
-      if (ins)
-        contract_split<float2, 0><<<grid, 256, 0, st>>>(spd, j0.vec_stride, n_r, V3, nct, nkb, j0.g5mask, ws);
-      else
-        contract_split<float2, 1><<<grid, 256, 0, st>>>(spd, j0.vec_stride, n_r, V3, nct, nkb, j0.g5mask, ws);
+        LHC_TRY((ins ? launch_fused_np<float2, 0>(Np, fp, nb, st) : launch_fused_np<float2, 1>(Np, fp, nb, st)));
     }
-  }
-  MmaParams mp;
-  mp.A = ws;
-  mp.B = phase;
-  mp.partial = reinterpret_cast<float2 *>(ws + off_p);
-  mp.err = err;
-  mp.nct = nct;
-  mp.nkb = nkb;
-  mp.nqc = nqc;
-  mp.nq = nq;
-  mp.ncols = ncols;
-  mp.nsplit = nsplit;
-  mp.kd = kd;
-  {
-    ProfScope ps(ctx, st, LHC_KERNEL_FUSED, 8.0 * nt * (double)nq * ncols * V3);
-    LHC_TRY(launch_mma_np(Np, mp, nt, st));
-  }
-  {
-    size_t n_out = (size_t)nq * ncols;
-    ProfScope ps(ctx, st, LHC_KERNEL_REDUCE, (double)p_bytes + (double)nt * n_out * 16);
-    reduce_f64<<<(unsigned)((n_out * nt + 255) / 256), 256, 0, st>>>(
-        mp.partial, nsplit, n_out, j0.out, n_out, nt, n_out);
+    {
+      ProfScope ps(ctx, st, LHC_KERNEL_REDUCE, (double)nb * nsplit * n_out * 8 + (double)nb * n_out * 16);
+      reduce_f64<<<(unsigned)((n_out * nb + 255) / 256), 256, 0, st>>>(fp.partial, nsplit, n_out,
+                                                                          jobs[jb].out, n_out, nb, n_out);
+    }
   }
   LHC_CHECK_CUDA(cudaGetLastError());
   return LHC_OK;

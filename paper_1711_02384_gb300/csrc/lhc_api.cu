@@ -524,20 +524,21 @@ int lhc_spectator(lhc_ctx ctx, const lhc_lattice *lat, int kind, const void *S1_
   return s != LHC_OK ? s : e;
 }
 
-int lhc_combine(lhc_ctx ctx, int kind, const void *spec, int np, const void *ins, int nq, int n_r,
-                const void *snk, const void *ins_g, const void *src, int ng, void *out, void *stream) {
+int lhc_combine(lhc_ctx ctx, int kind, const void *spec, int np, const void *ins, int nq, int n_r, int nt,
+                const void *snk, const void *ins_g, const void *src, int ng, int prec, void *out, void *stream) {
   if (!ctx) return fail(LHC_EINVAL, "ctx is NULL");
   if (kind != LHC_MESON && kind != LHC_BARYON) return fail(LHC_EINVAL, "unknown kind %d", kind);
   if (!spec || !ins || !snk || !ins_g || !src || !out) return fail(LHC_EINVAL, "NULL buffer argument");
-  if (np < 1 || nq < 1 || n_r < 1 || ng < 1) return fail(LHC_EINVAL, "sizes must be positive");
+  if (np < 1 || nq < 1 || n_r < 1 || ng < 1 || nt < 1) return fail(LHC_EINVAL, "sizes must be positive");
+  if (prec != LHC_FP64 && prec != LHC_MIXED) return fail(LHC_EINVAL, "unknown precision %d", prec);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> g(ctx->mu);
   LHC_TRY(begin_call(ctx, st));
   const int scols = kind == LHC_MESON ? 192 : kBarCols;
   const size_t nw = kind == LHC_MESON ? 16 : 64;
-  size_t b_spec = (size_t)np * n_r * scols * 16, b_ins = (size_t)nq * n_r * 192 * 16;
+  size_t b_spec = (size_t)np * n_r * scols * 16, b_ins = (size_t)nt * nq * n_r * 192 * 16;
   size_t b_snk = (size_t)ng * nw * 16, b_g = (size_t)ng * 16 * 16, b_src = (size_t)ng * nw * 16;
-  size_t b_out = (size_t)ng * np * nq * 16;
+  size_t b_out = (size_t)nt * ng * np * nq * 16;
   const void *ptr[6] = {spec, ins, snk, ins_g, src, out};
   size_t bytes[6] = {b_spec, b_ins, b_snk, b_g, b_src, b_out};
   bool host[6];
@@ -572,8 +573,8 @@ int lhc_combine(lhc_ctx ctx, int kind, const void *spec, int np, const void *ins
     }
   }
   if (s == LHC_OK)
-    s = run_combine(ctx, kind, (const double2 *)dev[0], np, (const double2 *)dev[1], nq, n_r,
-                    (const double2 *)dev[2], (const double2 *)dev[3], (const double2 *)dev[4], ng,
+    s = run_combine(ctx, kind, (const double2 *)dev[0], np, (const double2 *)dev[1], nq, n_r, nt,
+                    (const double2 *)dev[2], (const double2 *)dev[3], (const double2 *)dev[4], ng, prec,
                     (double2 *)dev[5], st);
   if (s == LHC_OK && host[5]) {
     cudaError_t e = cudaMemcpyAsync(out, dev[5], b_out, cudaMemcpyDeviceToHost, st);

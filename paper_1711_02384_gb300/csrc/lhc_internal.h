@@ -129,8 +129,8 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
 
 // combine (k_combine.cu)
 int run_combine(lhc_ctx ctx, int kind, const double2 *spec, int np, const double2 *ins, int nq,
-                int n_r, const double2 *snk, const double2 *ins_g, const double2 *src, int ng,
-                double2 *out, cudaStream_t st);
+                int n_r, int nt, const double2 *snk, const double2 *ins_g, const double2 *src, int ng,
+                int prec, double2 *out, cudaStream_t st);
 
 // kernels' launch wrappers
 void launch_phase_f64(double2 *P, const int *k_dev, int nq, int L, int rx, int ry, int rz,

@@ -18,7 +18,8 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "liblhc.so")
 
-KERNEL_PROJECT, KERNEL_CONTRACT, KERNEL_FUSED, KERNEL_REDUCE = range(4)
+KERNEL_PROJECT, KERNEL_CONTRACT, KERNEL_FUSED, KERNEL_REDUCE, KERNEL_COMBINE = range(5)
+KERNEL_NAMES = ("project_f64", "contract", "fused_mma", "reduce_f64", "combine")
 OK, EINVAL, ENOMEM, EBUDGET, ETIMEOUT, ECUDA, EBUSY, ENOTFOUND, ECANCELED = range(9)
 FP64, MIXED = 0, 1
 C128, C64 = 0, 1
@@ -60,7 +61,7 @@ def lib():
         L.lhc_momenta.argtypes = [ci, ci, ip, ci, ip]
         L.lhc_insertion.argtypes = [vp, lp, vp, vp, ci, ci, ci, ip, ip, ci, ci, vp, vp]
         L.lhc_spectator.argtypes = [vp, lp, ci, vp, vp, vp, ci, ci, ip, ip, ci, ci, vp, vp]
-        L.lhc_combine.argtypes = [vp, ci, vp, ci, vp, ci, ci, vp, vp, vp, ci, vp, vp]
+        L.lhc_combine.argtypes = [vp, ci, vp, ci, vp, ci, ci, ci, vp, vp, vp, ci, ci, vp, vp]
         L.lhc_sync.argtypes = [vp, vp]
         L.lhc_profile.argtypes = [vp, ci]
         L.lhc_profile_read.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double),
@@ -209,16 +210,20 @@ class Context:
                                    t_sink, rp, kp, nq, PRECISIONS[prec], _ptr(out), _stream(S1, stream)))
         return out
 
-    def combine(self, spec, ins, snk, ins_g, src, out=None, stream=None):
-        """Noise-averaged combine.  spec: [np][n_r][192 | 3072]; ins: [nq][n_r][192];
-        snk/src: [ng][4][4] (meson) or [ng][4][4][4] (baryon); ins_g: [ng][4][4].
-        Returns complex128 [ng][np][nq]."""
+    def combine(self, spec, ins, snk, ins_g, src, prec="fp64", out=None, stream=None):
+        """Noise-averaged combine.  spec: [np][n_r][192 | 3072]; ins: [nq][n_r][192] (one
+        insertion slice) or [nt][nq][n_r][192]; snk/src: [ng][4][4] (meson) or
+        [ng][4][4][4] (baryon); ins_g: [ng][4][4].
+        Returns complex128 [ng][np][nq] for one slice, else [nt][ng][np][nq]."""
         np_, n_r = spec.shape[0], spec.shape[1]
-        nq = ins.shape[0]
+        single = ins.dim() == 3
+        nt = 1 if single else ins.shape[0]
+        nq = ins.shape[-3]
         kind = MESON if spec.shape[2] == 192 else BARYON
         ng = ins_g.shape[0]
+        shape = (ng, np_, nq) if single else (nt, ng, np_, nq)
         if out is None:
-            out = torch.empty((ng, np_, nq), dtype=torch.complex128, device=spec.device)
-        _check(lib().lhc_combine(self._h, kind, _ptr(spec), np_, _ptr(ins), nq, n_r, _ptr(snk), _ptr(ins_g),
-                                 _ptr(src), ng, _ptr(out), _stream(spec, stream)))
+            out = torch.empty(shape, dtype=torch.complex128, device=spec.device)
+        _check(lib().lhc_combine(self._h, kind, _ptr(spec), np_, _ptr(ins), nq, n_r, nt, _ptr(snk), _ptr(ins_g),
+                                 _ptr(src), ng, PRECISIONS[prec], _ptr(out), _stream(spec, stream)))
         return out

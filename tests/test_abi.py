@@ -61,7 +61,7 @@ def test_invalid_arguments_rejected_before_launch(lib):
     lib.lhc_insertion.argtypes = [ctypes.c_void_p] * 13
     # NULL context -> LHC_EINVAL, without touching any device
     assert lib.lhc_insertion(*([None] * 13)) == 1
-    assert lib.lhc_combine(None, 0, None, 1, None, 1, 1, None, None, None, 1, None, None) == 1
+    assert lib.lhc_combine(None, 0, None, 1, None, 1, 1, 1, None, None, None, 1, 0, None, None) == 1
     assert lib.lhc_momenta(-1, -1, None, 0, None) == 1
 
 

@@ -103,3 +103,25 @@ def test_combine(ctx, kind):
     fn = OC.combine_meson if kind == "meson" else OC.combine_baryon
     ref = fn(spec, ins, snk, gi, src)
     assert CS.block_err(got, ref, 1) < CS.FP64_TOL
+
+
+@pytest.mark.parametrize("kind", ["meson", "baryon"])
+@pytest.mark.parametrize("prec,tol", [("fp64", CS.FP64_TOL), ("mixed", CS.MIXED_TOL)])
+def test_combine_batched(ctx, kind, prec, tol):
+    """nt insertion slices in one call; the mixed combine (FP32 per-noise sums, FP64
+    noise average) within 1e-6 per correlator."""
+    from oracle import contractions as OC
+    rng = np.random.default_rng(8)
+    np_, nq, n_r, ng, nt = 33, 40, 5, 3, 4
+    cols = 192 if kind == "meson" else 3072
+    spec = rng.standard_normal((np_, n_r, cols)) + 1j * rng.standard_normal((np_, n_r, cols))
+    ins = rng.standard_normal((nt, nq, n_r, 192)) + 1j * rng.standard_normal((nt, nq, n_r, 192))
+    wshape = (4, 4) if kind == "meson" else (4, 4, 4)
+    snk = CS.random_gammas(4, ng, wshape)
+    gi = CS.random_gammas(5, ng, (4, 4))
+    src = CS.random_gammas(6, ng, wshape)
+    got = ctx.combine(dev(spec), dev(ins), dev(snk), dev(gi), dev(src), prec=prec).cpu().numpy()
+    fn = OC.combine_meson if kind == "meson" else OC.combine_baryon
+    for t in range(nt):
+        ref = fn(spec, ins[t], snk, gi, src)
+        assert CS.block_err(got[t], ref, 1) < tol
