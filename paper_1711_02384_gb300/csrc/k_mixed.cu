@@ -64,7 +64,7 @@ __device__ __forceinline__ CT czero() {
   return z;
 }
 
-__device__ __forceinline__ void bar_producers() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void bar_producers() { asm volatile("barrier.sync 1, 256;" ::: "memory"); }
 
 // ------------------------------------------------------------ phase table (FP16 split)
 // layout [qc][kb][hl][3*Np rows: -Im | Re | Im][16 sites], each (qc,kb,hl) block K-major
@@ -245,7 +245,12 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(FusedParams p) {
     for (int n = 0; n < NR; ++n) acc[n] = 0.f;
     for (int c = 0; c < nchunks; ++c) {
       int b = c & 1, ub = c >> 1;
-      if (!tc::mbar_wait(&tfull[b], ub & 1, err, 5)) break;
+      // one lane waits, the warp follows its verdict: the tensor-memory loads below are
+      // warp-collective and must never see a split warp
+      int ok = 0;
+      if (lane == 0) ok = tc::mbar_wait(&tfull[b], ub & 1, err, 5) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
       tc::tc_fence_after();
       const uint32_t t = lane_base + (uint32_t)(b * 2 * NP + h * NP);
 #pragma unroll
@@ -275,7 +280,10 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(FusedParams p) {
     const int noise = i0 + ii;
     const int col = noise * 192 + v * 48 + s0 + sl;
     const int qend = min(p.nq - qc * QCHUNK, NP);
-    if (noise < p.n_r && !*err && nk > 0) {
+    // tcgen05.ld is warp-collective: every lane executes it, only the stores are per lane
+    const int failed = __shfl_sync(0xffffffffu, *err, 0);
+    if (!failed && nk > 0) {
+      const bool mine = noise < p.n_r;
       float *out = reinterpret_cast<float *>(p.partial + ((size_t)j * p.nsplit + split) * p.nq * p.ncols);
 #pragma unroll
       for (int n0 = 0; n0 < NT; n0 += 16) {
@@ -284,11 +292,11 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(FusedParams p) {
         tc::tmem_wait_ld();
 #pragma unroll
         for (int e = 0; e < 16; ++e)
-          if (n0 + e < qend) out[((size_t)(qc * QCHUNK + n0 + e) * p.ncols + col) * 2 + h] = r[e];
+          if (mine && n0 + e < qend) out[((size_t)(qc * QCHUNK + n0 + e) * p.ncols + col) * 2 + h] = r[e];
       }
 #pragma unroll
       for (int n = 0; n < NR; ++n)
-        if (NT + n < qend) out[((size_t)(qc * QCHUNK + NT + n) * p.ncols + col) * 2 + h] = acc[n];
+        if (mine && NT + n < qend) out[((size_t)(qc * QCHUNK + NT + n) * p.ncols + col) * 2 + h] = acc[n];
     }
   } else {
     // ---------------------------------------------------- producers
