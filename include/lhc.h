@@ -151,8 +151,8 @@ int lhc_spectator(lhc_ctx ctx, const lhc_lattice *lat, int kind, const void *S1_
  *             snk, src: complex128 [ng][4][4][4]
  * ins_g: complex128 [ng][4][4]; spec: [np][n_r][192 | 3072]; ins: [nt][nq][n_r][192] (the
  * output of lhc_insertion); out: complex128 [nt][ng][np][nq].
- * prec LHC_FP64: everything in FP64.  LHC_MIXED: the Gamma contractions in FP64, the
- * 12-term spin-colour sum of each noise in FP32, the sum over noises in FP64. */
+ * prec LHC_FP64: everything in FP64.  LHC_MIXED: the Gamma contractions and the 12-term
+ * spin-colour sum of each noise in FP32, the sum over noises (the noise average) in FP64. */
 int lhc_combine(lhc_ctx ctx, int kind, const void *spec, int np, const void *ins, int nq,
                 int n_r, int nt, const void *snk, const void *ins_g, const void *src, int ng,
                 int prec, void *out, void *stream);

@@ -9,9 +9,9 @@
 //   warp 0      bulk-copies the phase tiles (FP16 hi/lo of [-Im | Re | Im], K-major)
 //   warp 1      allocates tensor memory and issues the MMAs
 //   warps 2-9   drain the accumulator every KD k-steps into an FP32 running sum
-//   warps 10-17 producers: gather the site inputs of 32 sites into shared memory,
-//               contract them in FP32, split each value into fp16 hi + lo and write
-//               the four A tiles (Ur hi, Ur lo, Ui hi, Ui lo), MN-major
+//   warps 10-17 producers: each gathers the inputs of its 4 sites per 32-site iteration
+//               into shared memory (cp.async), contracts them in FP32, splits each value
+//               into fp16 hi + lo and writes the four A tiles (Ur hi/lo, Ui hi/lo), MN-major
 //
 // Per k-step (16 sites) the accumulator D (128 x 2Np, FP32, tensor memory) receives
 //   Ur_h [Re|Im]_h + Ur_h [Re|Im]_l + Ur_l [Re|Im]_h + Ui_h [-Im|Re]_h + Ui_h [-Im|Re]_l
@@ -34,10 +34,11 @@ constexpr int KSTEP = 16;                // sites per MMA k-step
 constexpr int QCHUNK = 96;               // momenta per CTA (accumulator registers bound this)
 constexpr int ATILE = MT * KSTEP * 2;    // bytes of one 128 x 16 fp16 operand tile
 constexpr int ASTAGE = 4 * ATILE;        // Ur hi, Ur lo, Ui hi, Ui lo
-constexpr int NSTAGE = 4;
+constexpr int NSTAGE = 5;
 constexpr int PSITES = 32;               // sites per producer iteration (two k-steps)
 constexpr int RVALS = 72;                // gathered complex values per site and tile
-constexpr int RPITCH = PSITES + 1;       // padded row of the transposed gather buffer
+constexpr int WSITES = 4;                // sites per producer warp and iteration
+constexpr int RBUF = RVALS * WSITES;     // float2 per warp gather buffer (two per warp)
 constexpr int kWarps = 18;
 constexpr int kThreads = kWarps * 32;
 constexpr int kDrainWarp0 = 2;
@@ -54,17 +55,7 @@ struct SlicePtrs {
   const void *vec;
 };
 
-__device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
-__device__ __forceinline__ float2 to_f2(float2 v) { return v; }
-template <typename CT>
-__device__ __forceinline__ CT czero() {
-  CT z;
-  z.x = 0;
-  z.y = 0;
-  return z;
-}
 
-__device__ __forceinline__ void bar_producers() { asm volatile("barrier.sync 1, 256;" ::: "memory"); }
 
 // ------------------------------------------------------------ phase table (FP16 split)
 // layout [qc][kb][hl][3*Np rows: -Im | Re | Im][16 sites], each (qc,kb,hl) block K-major
@@ -136,12 +127,11 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(FusedParams p) {
   extern __shared__ __align__(1024) char smem[];
   char *sA = smem;
   char *sB = sA + NSTAGE * ASTAGE;
-  float2 *R = reinterpret_cast<float2 *>(sB + NSTAGE * BSTAGE);        // [RVALS][RPITCH]
-  uint64_t *bars = reinterpret_cast<uint64_t *>(R + RVALS * RPITCH);
+  float2 *R = reinterpret_cast<float2 *>(sB + NSTAGE * BSTAGE);        // [8 warps][2][RVALS][WSITES]
+  uint64_t *bars = reinterpret_cast<uint64_t *>(R + 8 * 2 * RBUF);
   uint64_t *fullA = bars, *fullB = bars + NSTAGE, *empty = bars + 2 * NSTAGE,
            *tfull = bars + 3 * NSTAGE, *tempty = bars + 3 * NSTAGE + 2, *done = bars + 3 * NSTAGE + 4;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 3 * NSTAGE + 5);
-  volatile int *stop_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ct = blockIdx.x, split = blockIdx.y;
@@ -157,7 +147,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(FusedParams p) {
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
-      tc::mbar_init(&fullA[s], 1);
+      tc::mbar_init(&fullA[s], 4);   // the four producer warps that write a k-step
       tc::mbar_init(&fullB[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
@@ -166,7 +156,6 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(FusedParams p) {
       tc::mbar_init(&tempty[b], 8);
     }
     tc::mbar_init(done, 1);
-    *stop_flag = 0;
     tc::fence_mbar_init();
   }
   if (warp == 1) tc::tmem_alloc(tmem_slot, kTmemCols);
@@ -279,6 +268,12 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(FusedParams p) {
     const int sl = row >> 3, ii = (row >> 2) & 1, v = row & 3;
     const int noise = i0 + ii;
     const int col = noise * 192 + v * 48 + s0 + sl;
+    // gamma5 signs of this row: g5(v) for the insertion, g5(v) g5(bt) g5(b) for the spectator
+    // (s = bt*12 + b*3 + a); the projection is linear, so they act on the finished sums
+    const int sidx = s0 + sl;
+    const int smask = MODE == 0 ? (p.g5mask >> v)
+                                : ((p.g5mask >> v) ^ (p.g5mask >> (sidx / 12)) ^ (p.g5mask >> ((sidx % 12) / 3)));
+    const float sgn = (smask & 1) ? -1.f : 1.f;
     const int qend = min(p.nq - qc * QCHUNK, NP);
     // tcgen05.ld is warp-collective: every lane executes it, only the stores are per lane
     const int failed = __shfl_sync(0xffffffffu, *err, 0);
@@ -292,83 +287,81 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(FusedParams p) {
         tc::tmem_wait_ld();
 #pragma unroll
         for (int e = 0; e < 16; ++e)
-          if (mine && n0 + e < qend) out[((size_t)(qc * QCHUNK + n0 + e) * p.ncols + col) * 2 + h] = r[e];
+          if (mine && n0 + e < qend) out[((size_t)(qc * QCHUNK + n0 + e) * p.ncols + col) * 2 + h] = sgn * r[e];
       }
 #pragma unroll
       for (int n = 0; n < NR; ++n)
-        if (mine && NT + n < qend) out[((size_t)(qc * QCHUNK + NT + n) * p.ncols + col) * 2 + h] = acc[n];
+        if (mine && NT + n < qend) out[((size_t)(qc * QCHUNK + NT + n) * p.ncols + col) * 2 + h] = sgn * acc[n];
     }
   } else {
     // ---------------------------------------------------- producers
-    const int pt = threadIdx.x - kProdWarp0 * 32;      // 0..255
-    const int slp = warp - kProdWarp0;                  // compute role: s pair (2*slp, 2*slp+1)
-    const CT *S = static_cast<const CT *>(p.slices[j].S);
-    const CT *vec = static_cast<const CT *>(p.slices[j].vec);
+    // Each producer warp owns 4 sites of every 32-site iteration (warps 0-3 fill the first
+    // k-step, warps 4-7 the second) and computes all 128 rows for them, so the warps only
+    // synchronise through the stage barriers.  Lane = (site x in 0..3, s pair slp in 0..7).
+    const int pw = warp - kProdWarp0;                    // 0..7
+    const int xl = lane & 3, slp = lane >> 2;
+    const float2 *S = static_cast<const float2 *>(p.slices[j].S);
+    const float2 *vec = static_cast<const float2 *>(p.slices[j].vec);
     const int nit = (nk + 1) / 2;
-    // gather role: values e = pt + 256*jj of the 32 x 72 per iteration; e < 1536 are the
-    // 48 propagator entries (colour c, s) of each site, the rest the 2 x 12 noise-vector
-    // entries.  The next iteration's lines are prefetched into L1 one iteration ahead.
-    auto source = [&](int it, int jj, int &w, int &x) -> const CT * {
-      int e = pt + 256 * jj, off;
-      size_t stride;
-      const CT *src;
-      if (e < 1536) {
-        x = e / 48;
-        w = e % 48;
-        int c = w >> 4, s = s0 + (w & 15);
-        off = ((s / 12) * 3 + c) * 12 + s % 12;
-        src = S;
-        stride = 144;
+    float2 *Rw = R + pw * 2 * RBUF;                      // this warp's two gather buffers [72][4]
+    // gather: value v = lane + 32*jj of the warp's 4 x 72; jj < 6: the 48 propagator entries
+    // (colour c, s) of each site, jj >= 6: the 2 x 12 noise-vector entries.  Copies go
+    // global -> shared with cp.async (zero-filled out of range), one iteration ahead.
+    int goff[9], soff[9], xs[9];
+    bool live[9];
+#pragma unroll
+    for (int jj = 0; jj < 9; ++jj) {
+      if (jj < 6) {
+        int v = lane + 32 * jj, x = v / 48, w = v % 48, c = w >> 4, sv = s0 + (w & 15);
+        xs[jj] = x;
+        goff[jj] = x * 144 + ((sv / 12) * 3 + c) * 12 + sv % 12;
+        soff[jj] = w * WSITES + x;
+        live[jj] = true;
       } else {
-        int e2 = e - 1536;
-        x = e2 / 24;
-        int ww = e2 % 24, noise = i0 + ww / 12;
-        w = 48 + ww;
-        off = ww % 12;
-        src = noise < p.n_r ? vec + (size_t)noise * p.vec_stride : nullptr;
-        stride = 12;
+        int v = lane + 32 * (jj - 6), x = v / 24, ww = v % 24, noise = i0 + ww / 12;
+        xs[jj] = x;
+        live[jj] = noise < p.n_r;
+        goff[jj] = (live[jj] ? noise : 0) * (int)p.vec_stride + x * 12 + ww % 12;
+        soff[jj] = (48 + ww) * WSITES + x;
       }
-      int site = 16 * kb0 + PSITES * it + x;
-      if (src == nullptr || site >= 16 * kb1 || site >= p.V3) return nullptr;
-      return src + (size_t)site * stride + off;
-    };
-    auto prefetch = [&](int it) {
-#pragma unroll
-      for (int jj = 0; jj < 9; ++jj) {
-        int w, x;
-        const CT *a = source(it, jj, w, x);
-        if (a) asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
-      }
-    };
-    auto gather = [&](int it) {
-#pragma unroll
-      for (int jj = 0; jj < 9; ++jj) {
-        int w, x;
-        const CT *a = source(it, jj, w, x);
-        R[w * RPITCH + x] = a ? to_f2(__ldg(a)) : make_float2(0.f, 0.f);
-      }
-    };
-    // gamma5 signs: the vector spin v (both modes) and, for the spectator, the two matrix
-    // spins carried by s = (bt, b, a); folded into the operands below
-    float sgs[2];
-#pragma unroll
-    for (int jx = 0; jx < 2; ++jx) {
-      int s = s0 + 2 * slp + jx;
-      int m = MODE == 0 ? 0 : ((p.g5mask >> (s / 12)) ^ (p.g5mask >> ((s % 12) / 3)));
-      sgs[jx] = (m & 1) ? -1.f : 1.f;
     }
-    if (nit > 0) prefetch(0);
+    const int site_end = min(16 * kb1, p.V3);
+    auto issue = [&](int it) {
+      const int base = 16 * kb0 + PSITES * it + WSITES * pw;
+      const int lim = site_end - base;
+      float2 *Rb = Rw + (it & 1) * RBUF;
+      const float2 *Sb = S + (size_t)base * 144, *Vb = vec + (size_t)base * 12;
+#pragma unroll
+      for (int jj = 0; jj < 9; ++jj) {
+        bool ok = live[jj] && xs[jj] < lim;
+        const float2 *src = ok ? (jj < 6 ? Sb : Vb) + goff[jj] : S;
+        tc::cp_async8(Rb + soff[jj], src, ok);
+      }
+      tc::cp_async_commit();
+    };
+    // (the gamma5 signs are per output row and are applied to the sums in the epilogue)
+    const int kofs = pw >> 2;                            // k-step of this warp within the iteration
+    const int kk = WSITES * (pw & 3) + xl;               // site within the k-step
+    if (nit > 0) issue(0);
     for (int it = 0; it < nit; ++it) {
-      if (it + 1 < nit) prefetch(it + 1);
-      gather(it);
-      if (pt == 0) *stop_flag = *err;
-      bar_producers();
-      if (*stop_flag) break;
-      // this thread: site x = lane (k-step 2*it + lane/16), s = s0 + 2*slp + {0,1}
-      const int x = lane, kstep = 2 * it + (x >> 4), kk = x & 15;
+      if (it + 1 < nit) {
+        issue(it + 1);
+        tc::cp_async_wait<1>();   // this lane's copies for iteration it have landed
+      } else {
+        tc::cp_async_wait<0>();
+      }
+      const int failed = __shfl_sync(0xffffffffu, lane == 0 ? *err : 0, 0);
+      if (failed) break;
+      __syncwarp();                // the warp's copies are visible to all its lanes
+      const int kstep = 2 * it + kofs;
       if (kstep < nk) {
         const int s = kstep % NSTAGE, u = kstep / NSTAGE;
-        if (u > 0) tc::mbar_wait(&empty[s], (u - 1) & 1, err, 6);
+        if (u > 0) {
+          int ok = 1;
+          if (lane == 0) ok = tc::mbar_wait(&empty[s], (u - 1) & 1, err, 6) ? 1 : 0;
+          __syncwarp();
+        }
+        const float2 *Rc = Rw + (it & 1) * RBUF;
         float2 acc[2][8];
 #pragma unroll
         for (int jx = 0; jx < 2; ++jx)
@@ -378,18 +371,10 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(FusedParams p) {
         for (int c = 0; c < 3; ++c) {
           float2 sv[2];
 #pragma unroll
-          for (int jx = 0; jx < 2; ++jx) {
-            sv[jx] = R[(c * 16 + 2 * slp + jx) * RPITCH + x];
-            sv[jx].x *= sgs[jx];
-            sv[jx].y *= sgs[jx];
-          }
+          for (int jx = 0; jx < 2; ++jx) sv[jx] = Rc[(c * 16 + 2 * slp + jx) * WSITES + xl];
 #pragma unroll
           for (int iv = 0; iv < 8; ++iv) {
-            float2 pv = R[(48 + (iv >> 2) * 12 + (iv & 3) * 3 + c) * RPITCH + x];
-            if ((p.g5mask >> (iv & 3)) & 1) {
-              pv.x = -pv.x;
-              pv.y = -pv.y;
-            }
+            const float2 pv = Rc[(48 + (iv >> 2) * 12 + (iv & 3) * 3 + c) * WSITES + xl];
 #pragma unroll
             for (int jx = 0; jx < 2; ++jx) {
               float2 &a = acc[jx][iv];
@@ -419,14 +404,13 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(FusedParams p) {
           *reinterpret_cast<uint4 *>(a_st + 2 * ATILE + off) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
           *reinterpret_cast<uint4 *>(a_st + 3 * ATILE + off) = make_uint4(il[0], il[1], il[2], il[3]);
         }
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&fullA[s]);
       }
-      tc::fence_proxy_async_smem();
-      bar_producers();
-      if (pt == 0) {
-        tc::mbar_arrive(&fullA[(2 * it) % NSTAGE]);
-        if (2 * it + 1 < nk) tc::mbar_arrive(&fullA[(2 * it + 1) % NSTAGE]);
-      }
+      __syncwarp();                // all lanes are done reading this buffer before it is refilled
     }
+    tc::cp_async_wait<0>();        // no copy may still be landing when the CTA retires
   }
   tc::tc_fence_before();
   __syncthreads();
@@ -453,32 +437,32 @@ __global__ void reduce_f64(const float2 *__restrict__ part, int nsplit, size_t p
 
 template <int NP>
 constexpr size_t fused_smem() {
-  return (size_t)NSTAGE * (ASTAGE + 2 * 3 * NP * 32) + (size_t)RVALS * RPITCH * 8 + (3 * NSTAGE + 5) * 8 + 16;
+  return (size_t)NSTAGE * (ASTAGE + 2 * 3 * NP * 32) + (size_t)8 * 2 * RBUF * 8 + (3 * NSTAGE + 5) * 8 + 16;
 }
 
-template <typename CT, int MODE, int NP>
+template <int MODE, int NP>
 int launch_fused_t(const FusedParams &p, int nt, cudaStream_t st) {
   const size_t smem = std::max<size_t>(fused_smem<NP>(), 120 * 1024);   // one CTA per SM
   static bool attr = false;
   if (!attr) {
-    LHC_CHECK_CUDA(cudaFuncSetAttribute(fused_meson<CT, MODE, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    LHC_CHECK_CUDA(cudaFuncSetAttribute(fused_meson<float2, MODE, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem));
     attr = true;
   }
   dim3 grid(p.nct, p.nsplit, nt * p.nqc);
-  fused_meson<CT, MODE, NP><<<grid, kThreads, smem, st>>>(p);
+  fused_meson<float2, MODE, NP><<<grid, kThreads, smem, st>>>(p);
   return LHC_OK;
 }
 
-template <typename CT, int MODE>
+template <int MODE>
 int launch_fused_np(int Np, const FusedParams &p, int nt, cudaStream_t st) {
   switch (Np) {
-    case 16: return launch_fused_t<CT, MODE, 16>(p, nt, st);
-    case 32: return launch_fused_t<CT, MODE, 32>(p, nt, st);
-    case 48: return launch_fused_t<CT, MODE, 48>(p, nt, st);
-    case 64: return launch_fused_t<CT, MODE, 64>(p, nt, st);
-    case 80: return launch_fused_t<CT, MODE, 80>(p, nt, st);
-    case 96: return launch_fused_t<CT, MODE, 96>(p, nt, st);
+    case 16: return launch_fused_t<MODE, 16>(p, nt, st);
+    case 32: return launch_fused_t<MODE, 32>(p, nt, st);
+    case 48: return launch_fused_t<MODE, 48>(p, nt, st);
+    case 64: return launch_fused_t<MODE, 64>(p, nt, st);
+    case 80: return launch_fused_t<MODE, 80>(p, nt, st);
+    case 96: return launch_fused_t<MODE, 96>(p, nt, st);
     default: set_error("unsupported momentum chunk %d", Np); return LHC_EINVAL;
   }
 }
@@ -497,6 +481,35 @@ int choose_nsplit(int base_ctas, int nk_pairs, int sms) {
     }
   }
   return best;
+}
+
+// complex128 -> complex64 staging of the slices one launch touches: propagator slices
+// to Sst[j][V3*144], noise vectors to Vst[i][j][V3*12] (the contraction runs in FP32)
+struct NarrowParams {
+  SlicePtrs slices[kMaxSlices];
+  size_t vec_stride;   // source elements between noises
+  float2 *Sst, *Vst;
+  int nb, V3;
+};
+
+__global__ void narrow_c128(NarrowParams p) {
+  const int j = blockIdx.y, part = blockIdx.z;   // part 0: propagator, 1 + i: noise i
+  const double2 *src;
+  float2 *dst;
+  size_t n;
+  if (part == 0) {
+    src = static_cast<const double2 *>(p.slices[j].S);
+    dst = p.Sst + (size_t)j * p.V3 * 144;
+    n = (size_t)p.V3 * 144;
+  } else {
+    src = static_cast<const double2 *>(p.slices[j].vec) + (size_t)(part - 1) * p.vec_stride;
+    dst = p.Vst + ((size_t)(part - 1) * p.nb + j) * p.V3 * 12;
+    n = (size_t)p.V3 * 12;
+  }
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double2 v = __ldg(src + e);
+    dst[e] = make_float2((float)v.x, (float)v.y);
+  }
 }
 
 }  // namespace
@@ -556,12 +569,15 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
   if (const char *e = getenv("LHC_NSPLIT")) nsplit = std::max(1, std::min((nkb + 1) / 2, atoi(e)));
 
   const int ntl = std::min(nt, kMaxSlices);   // slices per launch
+  const bool narrow = j0.dtype == LHC_C128;
   size_t p_bytes = (size_t)ntl * nsplit * nq * ncols * sizeof(float2);
-  LHC_TRY(ensure(ctx, ctx->ws, p_bytes));
+  size_t s_bytes = narrow ? (size_t)ntl * V3 * 144 * sizeof(float2) : 0;
+  size_t v_bytes = narrow ? (size_t)n_r * ntl * V3 * 12 * sizeof(float2) : 0;
+  size_t off_s = (p_bytes + 255) & ~(size_t)255, off_v = (off_s + s_bytes + 255) & ~(size_t)255;
+  LHC_TRY(ensure(ctx, ctx->ws, off_v + v_bytes));
   char *ws = static_cast<char *>(ctx->ws.p);
 
   FusedParams fp;
-  fp.vec_stride = j0.vec_stride;
   fp.B = phase;
   fp.partial = reinterpret_cast<float2 *>(ws);
   fp.err = ctx->dev_err;
@@ -578,14 +594,28 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
   const size_t n_out = (size_t)nq * ncols;
   for (int jb = 0; jb < nt; jb += kMaxSlices) {
     const int nb = std::min(kMaxSlices, nt - jb);
-    for (int j = 0; j < nb; ++j) fp.slices[j] = SlicePtrs{jobs[jb + j].S, jobs[jb + j].vec};
+    if (narrow) {
+      NarrowParams np;
+      for (int j = 0; j < nb; ++j) np.slices[j] = SlicePtrs{jobs[jb + j].S, jobs[jb + j].vec};
+      np.vec_stride = j0.vec_stride;
+      np.Sst = reinterpret_cast<float2 *>(ws + off_s);
+      np.Vst = reinterpret_cast<float2 *>(ws + off_v);
+      np.nb = nb;
+      np.V3 = V3;
+      ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT, (double)nb * V3 * (144.0 + 12.0 * n_r) * 24);
+      dim3 grid((unsigned)std::max(1, std::min(1024, (V3 * 144 + 255) / 256 / 4)), nb, 1 + n_r);
+      narrow_c128<<<grid, 256, 0, st>>>(np);
+      for (int j = 0; j < nb; ++j)
+        fp.slices[j] = SlicePtrs{np.Sst + (size_t)j * V3 * 144, np.Vst + (size_t)j * V3 * 12};
+      fp.vec_stride = (size_t)nb * V3 * 12;
+    } else {
+      for (int j = 0; j < nb; ++j) fp.slices[j] = SlicePtrs{jobs[jb + j].S, jobs[jb + j].vec};
+      fp.vec_stride = j0.vec_stride;
+    }
     {
       ProfScope ps(ctx, st, LHC_KERNEL_FUSED, 8.0 * nb * (double)nq * ncols * V3);
       bool ins = j0.part == PART_INS;
-      if (j0.dtype == LHC_C128)
-        LHC_TRY((ins ? launch_fused_np<double2, 0>(Np, fp, nb, st) : launch_fused_np<double2, 1>(Np, fp, nb, st)));
-      else
-        LHC_TRY((ins ? launch_fused_np<float2, 0>(Np, fp, nb, st) : launch_fused_np<float2, 1>(Np, fp, nb, st)));
+      LHC_TRY((ins ? launch_fused_np<0>(Np, fp, nb, st) : launch_fused_np<1>(Np, fp, nb, st)));
     }
     {
       ProfScope ps(ctx, st, LHC_KERNEL_REDUCE, (double)nb * nsplit * n_out * 8 + (double)nb * n_out * 16);

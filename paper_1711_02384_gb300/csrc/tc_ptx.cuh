@@ -46,17 +46,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // Bounded wait for phase `parity` of `bar`.  Returns false (and raises *err) on timeout;
-// once *err is set by anyone, waits give up immediately.
+// once *err is set by anyone, waits give up.  The clock and the error word are looked at
+// every 64 polls only, to keep idle waiters off the memory system.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *err, int code) {
+  if (mbar_try_wait(bar, parity)) return true;
   long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
+  for (;;) {
+#pragma unroll 1
+    for (int k = 0; k < 64; ++k)
+      if (mbar_try_wait(bar, parity)) return true;
     if (*err) return false;
     if (clock64() - t0 > kSpinLimit) {
       atomicExch((int *)err, code);
       return false;
     }
   }
-  return true;
 }
 
 // cp.async.bulk global -> shared (this CTA), completion counted on `bar` in bytes.
@@ -70,6 +74,19 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Asynchronous 8-byte global -> shared copy; zero-fills the destination when !valid
+// (no bytes are read then).
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(valid ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // Register rebalancing between warpgroups (all 4 warps of a warpgroup execute it).
