@@ -157,6 +157,25 @@ int lhc_combine(lhc_ctx ctx, int kind, const void *spec, int np, const void *ins
                 int n_r, int nt, const void *snk, const void *ins_g, const void *src, int ng,
                 int prec, void *out, void *stream);
 
+/* Allocation-free variant of lhc_combine (the paper has no counterpart; this is a
+ * library service).  For callers that cannot let a library allocate device memory:
+ * a process whose device memory is owned by another allocator (for example an analysis
+ * framework's caching pool that has reserved almost all of HBM), or host code that must
+ * not stall, since cudaMalloc/cudaFree can synchronize the device.  Same arguments and
+ * results as lhc_combine, but no context, and every buffer must be device memory
+ * (host buffers give LHC_EINVAL).  The intermediate tensors live in a fixed 32 MiB
+ * scratch array inside the library image, which every GPU that loads the library
+ * holds until the process exits; the call itself never allocates.  A call needs
+ * ng*(np+nq)*12*n_r*16 bytes of it for one insertion slice (larger combines give
+ * LHC_EINVAL with the size; nt is processed in chunks that fit).  The first call on a
+ * device looks up the scratch's device address (cudaGetSymbolAddress), so make that
+ * first call before any stream capture.  All calls on a device share the scratch and
+ * it keeps the last call's contents (nothing in it needs clearing); calls whose kernels
+ * may overlap on the GPU race on it, so order them on one stream or with events. */
+int lhc_combine_noalloc(int kind, const void *spec, int np, const void *ins, int nq, int n_r, int nt,
+                        const void *snk, const void *ins_g, const void *src, int ng, int prec,
+                        void *out, void *stream);
+
 /* Kernel-level timing with CUDA events recorded on the launching stream, for
  * roofline measurements.  lhc_profile(ctx, 1) clears the records and starts
  * recording around every launch of the listed kernels; lhc_profile(ctx, 0) stops.

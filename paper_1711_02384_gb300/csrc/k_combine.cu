@@ -237,4 +237,17 @@ int run_combine(lhc_ctx ctx, int kind, const double2 *spec, int np, const double
   return LHC_OK;
 }
 
+// The same kernels on caller-provided scratch (Xs: ng*np*12*n_r, Xi: nt*ng*nq*12*n_r
+// complex128); no allocation and no context.
+int run_combine_scratch(int kind, const double2 *spec, int np, const double2 *ins, int nq, int n_r, int nt,
+                        const double2 *snk, const double2 *ins_g, const double2 *src, int ng, int prec,
+                        double2 *Xs, double2 *Xi, double2 *out, cudaStream_t st) {
+  if (prec == LHC_MIXED)
+    launch_combine<float>(kind, spec, np, ins, nq, n_r, nt, snk, ins_g, src, ng, Xs, Xi, out, st);
+  else
+    launch_combine<double>(kind, spec, np, ins, nq, n_r, nt, snk, ins_g, src, ng, Xs, Xi, out, st);
+  LHC_CHECK_CUDA(cudaGetLastError());
+  return LHC_OK;
+}
+
 }  // namespace lhc

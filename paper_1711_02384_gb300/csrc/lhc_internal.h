@@ -132,6 +132,11 @@ int run_combine(lhc_ctx ctx, int kind, const double2 *spec, int np, const double
                 int n_r, int nt, const double2 *snk, const double2 *ins_g, const double2 *src, int ng,
                 int prec, double2 *out, cudaStream_t st);
 
+// combine on caller-provided scratch, no allocation (k_combine.cu)
+int run_combine_scratch(int kind, const double2 *spec, int np, const double2 *ins, int nq, int n_r, int nt,
+                        const double2 *snk, const double2 *ins_g, const double2 *src, int ng, int prec,
+                        double2 *Xs, double2 *Xi, double2 *out, cudaStream_t st);
+
 // kernels' launch wrappers
 void launch_phase_f64(double2 *P, const int *k_dev, int nq, int L, int rx, int ry, int rz,
                       int sign, const double2 *roots_dev, cudaStream_t st);
