@@ -158,3 +158,14 @@ def combine_baryon(spec: np.ndarray, ins: np.ndarray, w_snk, g_ins, w_src) -> np
         out[g] = np.einsum("IKE,JLb,GH,piIJKLEc,qiGHbc->pq", w_snk[g], w_src[g], g_ins[g], B, I,
                            optimize=True) / n
     return out
+
+
+def spectator_baryon_component(GA, GB, eta_i, g5, r3, k, L, a1p, a1, a2p, a2, bp, c) -> np.ndarray:
+    """One open component (alpha1', alpha1, alpha2', alpha2, beta', c) of the baryon spectator
+    for one noise, at all momenta: the same sum as spectator_baryon, restricted to one
+    output column so that large lattices stay cheap.  Returns complex128 [nq]."""
+    A = GA.reshape(GA.shape[0], 4, 3, 4, 3)[:, a1p, :, a1, :]      # [x, a', a]
+    B = GB.reshape(GB.shape[0], 4, 3, 4, 3)[:, a2p, :, a2, :]      # [x, b', b]
+    e5 = apply_g5_vec(g5, eta_i).reshape(eta_i.shape[0], 4, 3)[:, bp, :]   # [x, c']
+    D = np.einsum("pqs,uv,xpu,xqv->xs", EPS, EPS[:, :, c], A, B)                    # [x, c']
+    return phases(L, k, r3, -1) @ np.einsum("xs,xs->x", D, e5)

@@ -36,67 +36,106 @@ __device__ __forceinline__ void st(double2 *p, cplx<R> v) {
   *p = make_double2((double)v.x, (double)v.y);
 }
 
-// one thread per (g, p, i, a): the four al values
+// Stage one [n_r][cols] block (and the Gamma matrices) of an input in shared memory and
+// let the CTA's threads serve all (g, i, colour) tasks of that block from there.
 template <typename R>
-__global__ void comb_spec_meson(const double2 *__restrict__ S, int np, int n_r, const double2 *__restrict__ Gsnk,
-                                int ng, double2 *__restrict__ Xs) {
-  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (size_t)ng * np * n_r * 3) return;
-  int a = (int)(idx % 3);
-  size_t rest = idx / 3;
-  int i = (int)(rest % n_r);
-  rest /= n_r;
-  int p = (int)(rest % np), g = (int)(rest / np);
-  const double2 *s = S + ((size_t)p * n_r + i) * 192;
-  const double2 *G = Gsnk + (size_t)g * 16;
-  double2 *o = Xs + ((size_t)g * np + p) * 12 * n_r + i * 12 + a;
+__device__ __forceinline__ void stage(cplx<R> *dst, const double2 *src, int n) {
+  for (int e = threadIdx.x; e < n; e += blockDim.x) dst[e] = ld<R>(src + e);
+}
+
+// CTA per (t, q): Xi[t][g][q][i,al,a] = sum_b Gsrc[g][b][al] sum_{at,bt} Gins[g][at][bt] I[t][q][i][at,bt,b,a]
+template <typename R>
+__global__ void comb_ins_meson(const double2 *__restrict__ I, int nq, int n_r, const double2 *__restrict__ Gins,
+                               const double2 *__restrict__ Gsrc, int ng, cplx<R> *__restrict__ Xi) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cplx<R> *sI = reinterpret_cast<cplx<R> *>(sm_raw);
+  cplx<R> *sGi = sI + n_r * 192, *sGc = sGi + ng * 16;
+  const int tq = blockIdx.x, t = tq / nq, q = tq % nq;
+  stage(sI, I + (size_t)tq * n_r * 192, n_r * 192);
+  stage(sGi, Gins, ng * 16);
+  stage(sGc, Gsrc, ng * 16);
+  __syncthreads();
+  for (int task = threadIdx.x; task < ng * n_r * 3; task += blockDim.x) {
+    const int a = task % 3, i = (task / 3) % n_r, g = task / (3 * n_r);
+    const cplx<R> *v = sI + i * 192, *Gi = sGi + g * 16, *Gc = sGc + g * 16;
+    cplx<R> T[4];
 #pragma unroll
-  for (int al = 0; al < 4; ++al) {
-    cplx<R> acc{0, 0};
-    for (int ap = 0; ap < 4; ++ap)
-      for (int bp = 0; bp < 4; ++bp) cfma(acc, ld<R>(G + ap * 4 + bp), ld<R>(s + bp * 48 + ap * 12 + al * 3 + a));
-    st(o + al * 3, acc);
+    for (int b = 0; b < 4; ++b) {
+      T[b] = {0, 0};
+#pragma unroll
+      for (int at = 0; at < 4; ++at)
+#pragma unroll
+        for (int bt = 0; bt < 4; ++bt) cfma(T[b], Gi[at * 4 + bt], v[at * 48 + bt * 12 + b * 3 + a]);
+    }
+    cplx<R> *o = Xi + (((size_t)t * ng + g) * nq + q) * 12 * n_r + i * 12 + a;
+#pragma unroll
+    for (int al = 0; al < 4; ++al) {
+      cplx<R> acc{0, 0};
+#pragma unroll
+      for (int b = 0; b < 4; ++b) cfma(acc, Gc[b * 4 + al], T[b]);
+      o[al * 3] = acc;
+    }
   }
 }
 
-// one thread per (t, g, q, i, a): T[b] = sum Gins I, then the four al values
+// CTA per (t, q): Xi[t][g][q][i,b,c] = sum_{at,bt} Gins[g][at][bt] I[t][q][i][at,bt,b,c]
 template <typename R>
-__global__ void comb_ins_meson(const double2 *__restrict__ I, int nt, int nq, int n_r,
-                               const double2 *__restrict__ Gins, const double2 *__restrict__ Gsrc, int ng,
-                               double2 *__restrict__ Xi) {
-  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (size_t)nt * ng * nq * n_r * 3) return;
-  int a = (int)(idx % 3);
-  size_t rest = idx / 3;
-  int i = (int)(rest % n_r);
-  rest /= n_r;
-  int q = (int)(rest % nq);
-  rest /= nq;
-  int g = (int)(rest % ng), t = (int)(rest / ng);
-  const double2 *v = I + (((size_t)t * nq + q) * n_r + i) * 192;
-  const double2 *Gi = Gins + (size_t)g * 16;
-  const double2 *Gc = Gsrc + (size_t)g * 16;
-  cplx<R> T[4];
+__global__ void comb_ins_baryon(const double2 *__restrict__ I, int nq, int n_r, const double2 *__restrict__ Gins,
+                                int ng, cplx<R> *__restrict__ Xi) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cplx<R> *sI = reinterpret_cast<cplx<R> *>(sm_raw);
+  cplx<R> *sGi = sI + n_r * 192;
+  const int tq = blockIdx.x, t = tq / nq, q = tq % nq;
+  stage(sI, I + (size_t)tq * n_r * 192, n_r * 192);
+  stage(sGi, Gins, ng * 16);
+  __syncthreads();
+  for (int task = threadIdx.x; task < ng * n_r * 3; task += blockDim.x) {
+    const int c = task % 3, i = (task / 3) % n_r, g = task / (3 * n_r);
+    const cplx<R> *v = sI + i * 192, *Gi = sGi + g * 16;
+    cplx<R> *o = Xi + (((size_t)t * ng + g) * nq + q) * 12 * n_r + i * 12 + c;
 #pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    T[b] = {0, 0};
-    for (int at = 0; at < 4; ++at)
-      for (int bt = 0; bt < 4; ++bt) cfma(T[b], ld<R>(Gi + at * 4 + bt), ld<R>(v + at * 48 + bt * 12 + b * 3 + a));
+    for (int b = 0; b < 4; ++b) {
+      cplx<R> acc{0, 0};
+#pragma unroll
+      for (int at = 0; at < 4; ++at)
+#pragma unroll
+        for (int bt = 0; bt < 4; ++bt) cfma(acc, Gi[at * 4 + bt], v[at * 48 + bt * 12 + b * 3 + c]);
+      o[b * 3] = acc;
+    }
   }
-  double2 *o = Xi + (((size_t)t * ng + g) * nq + q) * 12 * n_r + i * 12 + a;
+}
+
+// CTA per p: Xs[g][p][i,al,a] = sum_{ap,bp} Gsnk[g][ap][bp] S[p][i][bp,ap,al,a]
+template <typename R>
+__global__ void comb_spec_meson(const double2 *__restrict__ S, int np, int n_r, const double2 *__restrict__ Gsnk,
+                                int ng, cplx<R> *__restrict__ Xs) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cplx<R> *sS = reinterpret_cast<cplx<R> *>(sm_raw);
+  cplx<R> *sG = sS + n_r * 192;
+  const int p = blockIdx.x;
+  stage(sS, S + (size_t)p * n_r * 192, n_r * 192);
+  stage(sG, Gsnk, ng * 16);
+  __syncthreads();
+  for (int task = threadIdx.x; task < ng * n_r * 3; task += blockDim.x) {
+    const int a = task % 3, i = (task / 3) % n_r, g = task / (3 * n_r);
+    const cplx<R> *s = sS + i * 192, *G = sG + g * 16;
+    cplx<R> *o = Xs + ((size_t)g * np + p) * 12 * n_r + i * 12 + a;
 #pragma unroll
-  for (int al = 0; al < 4; ++al) {
-    cplx<R> acc{0, 0};
+    for (int al = 0; al < 4; ++al) {
+      cplx<R> acc{0, 0};
 #pragma unroll
-    for (int b = 0; b < 4; ++b) cfma(acc, ld<R>(Gc + b * 4 + al), T[b]);
-    st(o + al * 3, acc);
+      for (int ap = 0; ap < 4; ++ap)
+#pragma unroll
+        for (int bp = 0; bp < 4; ++bp) cfma(acc, G[ap * 4 + bp], s[bp * 48 + ap * 12 + al * 3 + a]);
+      o[al * 3] = acc;
+    }
   }
 }
 
 // one thread per (g, p, i, c): Bhat[a1][a2] = sum Wsnk B, then the four b values
 template <typename R>
 __global__ void comb_spec_baryon(const double2 *__restrict__ B, int np, int n_r, const double2 *__restrict__ Wsnk,
-                                 const double2 *__restrict__ Wsrc, int ng, double2 *__restrict__ Xs) {
+                                 const double2 *__restrict__ Wsrc, int ng, cplx<R> *__restrict__ Xs) {
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (size_t)ng * np * n_r * 3) return;
   int c = (int)(idx % 3);
@@ -119,34 +158,9 @@ __global__ void comb_spec_baryon(const double2 *__restrict__ B, int np, int n_r,
 #pragma unroll
       for (int b = 0; b < 4; ++b) cfma(out[b], ld<R>(Wc + (a1 * 4 + a2) * 4 + b), h);
     }
-  double2 *o = Xs + ((size_t)g * np + p) * 12 * n_r + i * 12 + c;
+  cplx<R> *o = Xs + ((size_t)g * np + p) * 12 * n_r + i * 12 + c;
 #pragma unroll
-  for (int b = 0; b < 4; ++b) st(o + b * 3, out[b]);
-}
-
-// one thread per (t, g, q, i, c): the four b values
-template <typename R>
-__global__ void comb_ins_baryon(const double2 *__restrict__ I, int nt, int nq, int n_r,
-                                const double2 *__restrict__ Gins, int ng, double2 *__restrict__ Xi) {
-  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (size_t)nt * ng * nq * n_r * 3) return;
-  int c = (int)(idx % 3);
-  size_t rest = idx / 3;
-  int i = (int)(rest % n_r);
-  rest /= n_r;
-  int q = (int)(rest % nq);
-  rest /= nq;
-  int g = (int)(rest % ng), t = (int)(rest / ng);
-  const double2 *v = I + (((size_t)t * nq + q) * n_r + i) * 192;
-  const double2 *Gi = Gins + (size_t)g * 16;
-  double2 *o = Xi + (((size_t)t * ng + g) * nq + q) * 12 * n_r + i * 12 + c;
-#pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    cplx<R> acc{0, 0};
-    for (int at = 0; at < 4; ++at)
-      for (int bt = 0; bt < 4; ++bt) cfma(acc, ld<R>(Gi + at * 4 + bt), ld<R>(v + at * 48 + bt * 12 + b * 3 + c));
-    st(o + b * 3, acc);
-  }
+  for (int b = 0; b < 4; ++b) o[b * 3] = out[b];
 }
 
 // out[t][g][p][q] = (1/N) sum_i sum_{j<12} Xs[g][p][12i+j] Xi[t][g][q][12i+j]: a tiled complex
@@ -154,7 +168,7 @@ __global__ void comb_ins_baryon(const double2 *__restrict__ I, int nt, int nq, i
 // noises runs in double.
 constexpr int CTILE = 32;
 template <typename R>
-__global__ void __launch_bounds__(256) comb_gemm(const double2 *__restrict__ Xs, const double2 *__restrict__ Xi,
+__global__ void __launch_bounds__(256) comb_gemm(const cplx<R> *__restrict__ Xs, const cplx<R> *__restrict__ Xi,
                                                  int np, int nq, int n_r, int ng, double inv_n,
                                                  double2 *__restrict__ out) {
   __shared__ cplx<R> As[CTILE][13];
@@ -164,8 +178,8 @@ __global__ void __launch_bounds__(256) comb_gemm(const double2 *__restrict__ Xs,
   const int tg = blockIdx.z;   // t * ng + g
   const int g = tg % ng;
   const size_t K = (size_t)12 * n_r;
-  const double2 *A = Xs + ((size_t)g * np) * K;
-  const double2 *B = Xi + ((size_t)tg * nq) * K;
+  const cplx<R> *A = Xs + ((size_t)g * np) * K;
+  const cplx<R> *B = Xi + ((size_t)tg * nq) * K;
   double2 acc[2][2];
 #pragma unroll
   for (int a = 0; a < 2; ++a)
@@ -174,8 +188,8 @@ __global__ void __launch_bounds__(256) comb_gemm(const double2 *__restrict__ Xs,
   for (int i = 0; i < n_r; ++i) {
     for (int e = threadIdx.x; e < CTILE * 12; e += 256) {
       int r = e / 12, k = e % 12;
-      As[r][k] = (p0 + r < np) ? ld<R>(A + (size_t)(p0 + r) * K + 12 * i + k) : cplx<R>{0, 0};
-      Bs[r][k] = (q0 + r < nq) ? ld<R>(B + (size_t)(q0 + r) * K + 12 * i + k) : cplx<R>{0, 0};
+      As[r][k] = (p0 + r < np) ? A[(size_t)(p0 + r) * K + 12 * i + k] : cplx<R>{0, 0};
+      Bs[r][k] = (q0 + r < nq) ? B[(size_t)(q0 + r) * K + 12 * i + k] : cplx<R>{0, 0};
     }
     __syncthreads();
 #pragma unroll
@@ -203,19 +217,36 @@ __global__ void __launch_bounds__(256) comb_gemm(const double2 *__restrict__ Xs,
 unsigned blocks(size_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
 
 template <typename R>
-void launch_combine(int kind, const double2 *spec, int np, const double2 *ins, int nq, int n_r, int nt,
-                    const double2 *snk, const double2 *ins_g, const double2 *src, int ng, double2 *Xs, double2 *Xi,
-                    double2 *out, cudaStream_t st) {
-  size_t ns = (size_t)ng * np * n_r * 3, ni = (size_t)nt * ng * nq * n_r * 3;
+int launch_combine(int kind, const double2 *spec, int np, const double2 *ins, int nq, int n_r, int nt,
+                   const double2 *snk, const double2 *ins_g, const double2 *src, int ng, void *scratch,
+                   double2 *out, cudaStream_t st) {
+  cplx<R> *Xs = static_cast<cplx<R> *>(scratch);
+  cplx<R> *Xi = Xs + (size_t)ng * np * 12 * n_r;
+  const size_t smem = ((size_t)n_r * 192 + 2 * ng * 16) * sizeof(cplx<R>);
+  if (smem > 200 * 1024) {
+    set_error("combine block of %d noises and %d Gamma structures does not fit shared memory", n_r, ng);
+    return LHC_EINVAL;
+  }
+  if (smem > 48 * 1024) {
+    static bool attr[4] = {false, false, false, false};
+    if (!attr[0]) {
+      LHC_CHECK_CUDA(cudaFuncSetAttribute(comb_ins_meson<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      LHC_CHECK_CUDA(cudaFuncSetAttribute(comb_ins_baryon<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      LHC_CHECK_CUDA(cudaFuncSetAttribute(comb_spec_meson<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      attr[0] = true;
+    }
+  }
   if (kind == LHC_MESON) {
-    comb_spec_meson<R><<<blocks(ns, 256), 256, 0, st>>>(spec, np, n_r, snk, ng, Xs);
-    comb_ins_meson<R><<<blocks(ni, 256), 256, 0, st>>>(ins, nt, nq, n_r, ins_g, src, ng, Xi);
+    comb_spec_meson<R><<<np, 256, smem, st>>>(spec, np, n_r, snk, ng, Xs);
+    comb_ins_meson<R><<<nt * nq, 256, smem, st>>>(ins, nq, n_r, ins_g, src, ng, Xi);
   } else {
+    size_t ns = (size_t)ng * np * n_r * 3;
     comb_spec_baryon<R><<<blocks(ns, 128), 128, 0, st>>>(spec, np, n_r, snk, src, ng, Xs);
-    comb_ins_baryon<R><<<blocks(ni, 256), 256, 0, st>>>(ins, nt, nq, n_r, ins_g, ng, Xi);
+    comb_ins_baryon<R><<<nt * nq, 256, smem, st>>>(ins, nq, n_r, ins_g, ng, Xi);
   }
   dim3 grid((nq + CTILE - 1) / CTILE, (np + CTILE - 1) / CTILE, nt * ng);
   comb_gemm<R><<<grid, 256, 0, st>>>(Xs, Xi, np, nq, n_r, ng, 1.0 / n_r, out);
+  return LHC_OK;
 }
 
 }  // namespace
@@ -223,29 +254,28 @@ void launch_combine(int kind, const double2 *spec, int np, const double2 *ins, i
 int run_combine(lhc_ctx ctx, int kind, const double2 *spec, int np, const double2 *ins, int nq, int n_r, int nt,
                 const double2 *snk, const double2 *ins_g, const double2 *src, int ng, int prec, double2 *out,
                 cudaStream_t st) {
-  size_t K = (size_t)12 * n_r;
-  size_t ns = (size_t)ng * np * K, ni = (size_t)nt * ng * nq * K;
-  LHC_TRY(ensure(ctx, ctx->ws, (ns + ni) * sizeof(double2)));
-  double2 *Xs = static_cast<double2 *>(ctx->ws.p);
-  double2 *Xi = Xs + ns;
+  const size_t es = prec == LHC_MIXED ? sizeof(cplx<float>) : sizeof(cplx<double>);
+  const size_t K = (size_t)12 * n_r;
+  LHC_TRY(ensure(ctx, ctx->ws, ((size_t)ng * np * K + (size_t)nt * ng * nq * K) * es));
   ProfScope ps(ctx, st, LHC_KERNEL_COMBINE, 8.0 * nt * ng * (double)np * nq * K);
   if (prec == LHC_MIXED)
-    launch_combine<float>(kind, spec, np, ins, nq, n_r, nt, snk, ins_g, src, ng, Xs, Xi, out, st);
+    LHC_TRY(launch_combine<float>(kind, spec, np, ins, nq, n_r, nt, snk, ins_g, src, ng, ctx->ws.p, out, st));
   else
-    launch_combine<double>(kind, spec, np, ins, nq, n_r, nt, snk, ins_g, src, ng, Xs, Xi, out, st);
+    LHC_TRY(launch_combine<double>(kind, spec, np, ins, nq, n_r, nt, snk, ins_g, src, ng, ctx->ws.p, out, st));
   LHC_CHECK_CUDA(cudaGetLastError());
   return LHC_OK;
 }
 
-// The same kernels on caller-provided scratch (Xs: ng*np*12*n_r, Xi: nt*ng*nq*12*n_r
-// complex128); no allocation and no context.
+// The same kernels on caller-provided scratch (room for ng*np*12*n_r + nt*ng*nq*12*n_r
+// complex128 values); no allocation and no context.
 int run_combine_scratch(int kind, const double2 *spec, int np, const double2 *ins, int nq, int n_r, int nt,
                         const double2 *snk, const double2 *ins_g, const double2 *src, int ng, int prec,
                         double2 *Xs, double2 *Xi, double2 *out, cudaStream_t st) {
+  (void)Xi;   // the intermediates are laid out from Xs on
   if (prec == LHC_MIXED)
-    launch_combine<float>(kind, spec, np, ins, nq, n_r, nt, snk, ins_g, src, ng, Xs, Xi, out, st);
+    LHC_TRY(launch_combine<float>(kind, spec, np, ins, nq, n_r, nt, snk, ins_g, src, ng, Xs, out, st));
   else
-    launch_combine<double>(kind, spec, np, ins, nq, n_r, nt, snk, ins_g, src, ng, Xs, Xi, out, st);
+    LHC_TRY(launch_combine<double>(kind, spec, np, ins, nq, n_r, nt, snk, ins_g, src, ng, Xs, out, st));
   LHC_CHECK_CUDA(cudaGetLastError());
   return LHC_OK;
 }

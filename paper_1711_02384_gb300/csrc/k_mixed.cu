@@ -18,7 +18,7 @@
 //   + Ui_l [-Im|Re]_h,
 // so D[:, :Np] = Re(P U) and D[:, Np:] = Im(P U) with the lo*lo term dropped.  Tensor
 // memory accumulation truncates, so D is double-buffered and drained every KD k-steps;
-// each CTA writes FP32 partial sums that reduce_f64 adds in FP64.
+// each CTA writes FP32 partial sums that reduce_f64 adds exactly and rounds to FP64.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -143,7 +143,12 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(FusedParams p) {
   const int nk = kb1 - kb0;
   const int nchunks = (nk + p.kd - 1) / p.kd;
   volatile int *err = p.err;
-  const int i0 = 2 * (ct / 3), s0 = 16 * (ct % 3);   // first noise and first s of this tile
+  // tile = (noise pair, block of 16 matrix columns s), noise pairs fastest so that CTAs
+  // sharing the same matrix columns run together (the baryon diquark is reused via L2)
+  constexpr int SCOLS = MODE == 2 ? 768 : 48;        // matrix columns s per noise-vector spin
+  constexpr int MSTRIDE = MODE == 2 ? 2304 : 144;    // complex numbers per site of the matrix operand
+  const int npairs = (p.n_r + 1) / 2;
+  const int i0 = 2 * (ct % npairs), s0 = 16 * (ct / npairs);   // first noise and first s of this tile
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
@@ -267,11 +272,13 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(FusedParams p) {
     // row -> (s, noise, spin): m = sl*8 + ii*4 + v
     const int sl = row >> 3, ii = (row >> 2) & 1, v = row & 3;
     const int noise = i0 + ii;
-    const int col = noise * 192 + v * 48 + s0 + sl;
-    // gamma5 signs of this row: g5(v) for the insertion, g5(v) g5(bt) g5(b) for the spectator
-    // (s = bt*12 + b*3 + a); the projection is linear, so they act on the finished sums
     const int sidx = s0 + sl;
-    const int smask = MODE == 0 ? (p.g5mask >> v)
+    // meson: col = (noise, v, s); baryon: col = (noise, alpha = s/3, beta' = v, c = s%3)
+    const int col = MODE == 2 ? noise * 3072 + (sidx / 3) * 12 + v * 3 + sidx % 3 : noise * 192 + v * 48 + sidx;
+    // gamma5 signs of this row: g5(v) for the insertion and the baryon spectator,
+    // g5(v) g5(bt) g5(b) for the meson spectator (s = bt*12 + b*3 + a); the projection is
+    // linear, so they act on the finished sums
+    const int smask = MODE != 1 ? (p.g5mask >> v)
                                 : ((p.g5mask >> v) ^ (p.g5mask >> (sidx / 12)) ^ (p.g5mask >> ((sidx % 12) / 3)));
     const float sgn = (smask & 1) ? -1.f : 1.f;
     const int qend = min(p.nq - qc * QCHUNK, NP);
@@ -314,7 +321,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(FusedParams p) {
       if (jj < 6) {
         int v = lane + 32 * jj, x = v / 48, w = v % 48, c = w >> 4, sv = s0 + (w & 15);
         xs[jj] = x;
-        goff[jj] = x * 144 + ((sv / 12) * 3 + c) * 12 + sv % 12;
+        goff[jj] = MODE == 2 ? x * MSTRIDE + c * SCOLS + sv : x * MSTRIDE + ((sv / 12) * 3 + c) * 12 + sv % 12;
         soff[jj] = w * WSITES + x;
         live[jj] = true;
       } else {
@@ -330,7 +337,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(FusedParams p) {
       const int base = 16 * kb0 + PSITES * it + WSITES * pw;
       const int lim = site_end - base;
       float2 *Rb = Rw + (it & 1) * RBUF;
-      const float2 *Sb = S + (size_t)base * 144, *Vb = vec + (size_t)base * 12;
+      const float2 *Sb = S + (size_t)base * MSTRIDE, *Vb = vec + (size_t)base * 12;
 #pragma unroll
       for (int jj = 0; jj < 9; ++jj) {
         bool ok = live[jj] && xs[jj] < lim;
@@ -378,12 +385,15 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(FusedParams p) {
 #pragma unroll
             for (int jx = 0; jx < 2; ++jx) {
               float2 &a = acc[jx][iv];
-              if (MODE == 0) {   // conj(psi) * S
+              if (MODE == 0) {          // conj(psi) * S
                 a.x = fmaf(pv.x, sv[jx].x, fmaf(pv.y, sv[jx].y, a.x));
                 a.y = fmaf(pv.x, sv[jx].y, fmaf(-pv.y, sv[jx].x, a.y));
-              } else {           // eta * conj(S)
+              } else if (MODE == 1) {   // eta * conj(S)
                 a.x = fmaf(pv.x, sv[jx].x, fmaf(pv.y, sv[jx].y, a.x));
                 a.y = fmaf(pv.y, sv[jx].x, fmaf(-pv.x, sv[jx].y, a.y));
+              } else {                  // eta * D
+                a.x = fmaf(pv.x, sv[jx].x, fmaf(-pv.y, sv[jx].y, a.x));
+                a.y = fmaf(pv.x, sv[jx].y, fmaf(pv.y, sv[jx].x, a.y));
               }
             }
           }
@@ -418,7 +428,18 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(FusedParams p) {
   if (warp == 1) tc::tmem_dealloc(tbase, kTmemCols);
 }
 
-// out[j][q][col] = sum over splits of the FP32 partials, in FP64
+// out[j][q][col] = sum over splits of the FP32 partials.  The partials are added without
+// error (Knuth's TwoSum keeps the exact sum as an unevaluated FP32 pair hi + lo) and the
+// pair is rounded once to FP64: no less accurate than FP64 accumulation of the partials,
+// with a few FP64 operations per output instead of two per partial.
+__device__ __forceinline__ void two_sum(float &hi, float &lo, float v) {
+  float s = hi + v;
+  float bp = s - hi;
+  float e = (hi - (s - bp)) + (v - bp);
+  hi = s;
+  lo += e;
+}
+
 __global__ void reduce_f64(const float2 *__restrict__ part, int nsplit, size_t per_split,
                            double2 *__restrict__ out, size_t n_out, int nt, size_t out_stride) {
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -426,13 +447,13 @@ __global__ void reduce_f64(const float2 *__restrict__ part, int nsplit, size_t p
   int j = (int)(idx / n_out);
   size_t e = idx % n_out;
   const float2 *pj = part + (size_t)j * nsplit * per_split + e;
-  double sx = 0.0, sy = 0.0;
+  float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f;
   for (int s = 0; s < nsplit; ++s) {
     float2 v = pj[(size_t)s * per_split];
-    sx += v.x;
-    sy += v.y;
+    two_sum(hx, lx, v.x);
+    two_sum(hy, ly, v.y);
   }
-  out[(size_t)j * out_stride + e] = make_double2(sx, sy);
+  out[(size_t)j * out_stride + e] = make_double2((double)hx + (double)lx, (double)hy + (double)ly);
 }
 
 template <int NP>
@@ -487,13 +508,15 @@ int choose_nsplit(int base_ctas, int nk_pairs, int sms) {
 // to Sst[j][V3*144], noise vectors to Vst[i][j][V3*12] (the contraction runs in FP32)
 struct NarrowParams {
   SlicePtrs slices[kMaxSlices];
+  const void *SB;      // baryon: second propagator slice (one slice), else nullptr
   size_t vec_stride;   // source elements between noises
-  float2 *Sst, *Vst;
+  float2 *Sst, *SBst, *Vst;
   int nb, V3;
 };
 
 __global__ void narrow_c128(NarrowParams p) {
-  const int j = blockIdx.y, part = blockIdx.z;   // part 0: propagator, 1 + i: noise i
+  // part 0: propagator, then (baryon) the second propagator, then noise i
+  const int j = blockIdx.y, nprop = p.SB ? 2 : 1, part = blockIdx.z;
   const double2 *src;
   float2 *dst;
   size_t n;
@@ -501,14 +524,46 @@ __global__ void narrow_c128(NarrowParams p) {
     src = static_cast<const double2 *>(p.slices[j].S);
     dst = p.Sst + (size_t)j * p.V3 * 144;
     n = (size_t)p.V3 * 144;
+  } else if (part < nprop) {
+    src = static_cast<const double2 *>(p.SB);
+    dst = p.SBst;
+    n = (size_t)p.V3 * 144;
   } else {
-    src = static_cast<const double2 *>(p.slices[j].vec) + (size_t)(part - 1) * p.vec_stride;
-    dst = p.Vst + ((size_t)(part - 1) * p.nb + j) * p.V3 * 12;
+    src = static_cast<const double2 *>(p.slices[j].vec) + (size_t)(part - nprop) * p.vec_stride;
+    dst = p.Vst + ((size_t)(part - nprop) * p.nb + j) * p.V3 * 12;
     n = (size_t)p.V3 * 12;
   }
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     double2 v = __ldg(src + e);
     dst[e] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+// Noise-independent baryon diquark, FP32: D[x][c'][(alpha, c)] with
+// alpha = ((a1p*4 + a1)*4 + a2p)*4 + a2 and D = sum eps_{a'b'c'} eps_{abc} GA[(a1p,a'),(a1,a)] GB[(a2p,b'),(a2,b)];
+// with p = c'+1, q = c'+2, u = c+1, v = c+2 (mod 3) the four nonzero terms are
+// GA[p,u]GB[q,v] - GA[p,v]GB[q,u] - GA[q,u]GB[p,v] + GA[q,v]GB[p,u].
+// One CTA per site: the two 12x12 propagators are staged in shared memory.
+__global__ void __launch_bounds__(256) baryon_diquark(const float2 *__restrict__ GA, const float2 *__restrict__ GB,
+                                                      int V3, float2 *__restrict__ D) {
+  __shared__ float2 a[144], bm[144];
+  const int x = blockIdx.x;
+  for (int e = threadIdx.x; e < 144; e += 256) {
+    a[e] = GA[(size_t)x * 144 + e];
+    bm[e] = GB[(size_t)x * 144 + e];
+  }
+  __syncthreads();
+  float2 *out = D + (size_t)x * 2304;
+  for (int e = threadIdx.x; e < 2304; e += 256) {
+    const int cp = e / 768, sidx = e % 768, c = sidx % 3, al = sidx / 3;
+    const int a2 = al & 3, a2p = (al >> 2) & 3, a1 = (al >> 4) & 3, a1p = al >> 6;
+    const int pp = (cp + 1) % 3, qq = (cp + 2) % 3, u = (c + 1) % 3, v = (c + 2) % 3;
+    auto A = [&](int r, int s2) { return a[(a1p * 3 + r) * 12 + a1 * 3 + s2]; };
+    auto B = [&](int r, int s2) { return bm[(a2p * 3 + r) * 12 + a2 * 3 + s2]; };
+    auto mul = [](float2 x1, float2 y1) { return make_float2(x1.x * y1.x - x1.y * y1.y, x1.x * y1.y + x1.y * y1.x); };
+    float2 t1 = mul(A(pp, u), B(qq, v)), t2 = mul(A(pp, v), B(qq, u)), t3 = mul(A(qq, u), B(pp, v)),
+           t4 = mul(A(qq, v), B(pp, u));
+    out[e] = make_float2(t1.x - t2.x - t3.x + t4.x, t1.y - t2.y - t3.y + t4.y);
   }
 }
 
@@ -550,13 +605,10 @@ static int get_phase_split(lhc_ctx ctx, int L, const int *k, int nq, const int r
 int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int nq, const int r[4], int sign,
                    cudaStream_t st) {
   const SliceJob &j0 = jobs[0];
-  if (j0.part == PART_SPEC_BARYON) {
-    set_error("mixed baryon spectator not available in this build");
-    return LHC_EINVAL;
-  }
+  const bool baryon = j0.part == PART_SPEC_BARYON;
   const int V3 = j0.V3, n_r = j0.n_r;
-  const int ncols = n_r * 192;
-  const int nct = 3 * ((n_r + 1) / 2);
+  const int ncols = n_r * (baryon ? kBarCols : 192);
+  const int nct = (baryon ? 48 : 3) * ((n_r + 1) / 2);
   const int nkb = (V3 + KSTEP - 1) / KSTEP;
   const int nqc = (nq + QCHUNK - 1) / QCHUNK;
   const int Np = ((std::min(nq, QCHUNK) + 15) / 16) * 16;
@@ -572,9 +624,13 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
   const bool narrow = j0.dtype == LHC_C128;
   size_t p_bytes = (size_t)ntl * nsplit * nq * ncols * sizeof(float2);
   size_t s_bytes = narrow ? (size_t)ntl * V3 * 144 * sizeof(float2) : 0;
+  size_t sb_bytes = narrow && baryon ? (size_t)V3 * 144 * sizeof(float2) : 0;
   size_t v_bytes = narrow ? (size_t)n_r * ntl * V3 * 12 * sizeof(float2) : 0;
-  size_t off_s = (p_bytes + 255) & ~(size_t)255, off_v = (off_s + s_bytes + 255) & ~(size_t)255;
-  LHC_TRY(ensure(ctx, ctx->ws, off_v + v_bytes));
+  size_t d_bytes = baryon ? (size_t)V3 * 2304 * sizeof(float2) : 0;   // diquark (one sink slice)
+  auto al256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  size_t off_s = al256(p_bytes), off_sb = off_s + al256(s_bytes), off_v = off_sb + al256(sb_bytes),
+         off_d = off_v + al256(v_bytes);
+  LHC_TRY(ensure(ctx, ctx->ws, off_d + d_bytes));
   char *ws = static_cast<char *>(ctx->ws.p);
 
   FusedParams fp;
@@ -597,13 +653,15 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
     if (narrow) {
       NarrowParams np;
       for (int j = 0; j < nb; ++j) np.slices[j] = SlicePtrs{jobs[jb + j].S, jobs[jb + j].vec};
+      np.SB = baryon ? j0.SB : nullptr;
       np.vec_stride = j0.vec_stride;
       np.Sst = reinterpret_cast<float2 *>(ws + off_s);
+      np.SBst = reinterpret_cast<float2 *>(ws + off_sb);
       np.Vst = reinterpret_cast<float2 *>(ws + off_v);
       np.nb = nb;
       np.V3 = V3;
-      ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT, (double)nb * V3 * (144.0 + 12.0 * n_r) * 24);
-      dim3 grid((unsigned)std::max(1, std::min(1024, (V3 * 144 + 255) / 256 / 4)), nb, 1 + n_r);
+      ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT, (double)nb * V3 * ((baryon ? 288.0 : 144.0) + 12.0 * n_r) * 24);
+      dim3 grid((unsigned)std::max(1, std::min(1024, (V3 * 144 + 255) / 256 / 4)), nb, (baryon ? 2 : 1) + n_r);
       narrow_c128<<<grid, 256, 0, st>>>(np);
       for (int j = 0; j < nb; ++j)
         fp.slices[j] = SlicePtrs{np.Sst + (size_t)j * V3 * 144, np.Vst + (size_t)j * V3 * 12};
@@ -612,10 +670,22 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
       for (int j = 0; j < nb; ++j) fp.slices[j] = SlicePtrs{jobs[jb + j].S, jobs[jb + j].vec};
       fp.vec_stride = j0.vec_stride;
     }
+    if (baryon) {   // the matrix operand becomes the diquark of the (single) sink slice
+      const float2 *GA = static_cast<const float2 *>(fp.slices[0].S);
+      const float2 *GB = narrow ? reinterpret_cast<const float2 *>(ws + off_sb) : static_cast<const float2 *>(j0.SB);
+      float2 *D = reinterpret_cast<float2 *>(ws + off_d);
+      ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT, (double)V3 * (288.0 + 2304.0) * 8);
+      baryon_diquark<<<V3, 256, 0, st>>>(GA, GB, V3, D);
+      fp.slices[0].S = D;
+    }
     {
       ProfScope ps(ctx, st, LHC_KERNEL_FUSED, 8.0 * nb * (double)nq * ncols * V3);
-      bool ins = j0.part == PART_INS;
-      LHC_TRY((ins ? launch_fused_np<0>(Np, fp, nb, st) : launch_fused_np<1>(Np, fp, nb, st)));
+      if (j0.part == PART_INS)
+        LHC_TRY(launch_fused_np<0>(Np, fp, nb, st));
+      else if (j0.part == PART_SPEC_MESON)
+        LHC_TRY(launch_fused_np<1>(Np, fp, nb, st));
+      else
+        LHC_TRY(launch_fused_np<2>(Np, fp, nb, st));
     }
     {
       ProfScope ps(ctx, st, LHC_KERNEL_REDUCE, (double)nb * nsplit * n_out * 8 + (double)nb * n_out * 16);

@@ -45,16 +45,28 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
+// try_wait that may suspend the thread (up to `ns` nanoseconds) until the phase completes,
+// so waiting warps do not spend issue slots polling
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait for phase `parity` of `bar`.  Returns false (and raises *err) on timeout;
-// once *err is set by anyone, waits give up.  The clock and the error word are looked at
-// every 64 polls only, to keep idle waiters off the memory system.
+// once *err is set by anyone, waits give up.  Each try suspends the thread for up to
+// 20 us; the clock and the error word are looked at between tries.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *err, int code) {
   if (mbar_try_wait(bar, parity)) return true;
   long long t0 = clock64();
   for (;;) {
-#pragma unroll 1
-    for (int k = 0; k < 64; ++k)
-      if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
     if (*err) return false;
     if (clock64() - t0 > kSpinLimit) {
       atomicExch((int *)err, code);

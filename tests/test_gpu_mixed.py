@@ -98,3 +98,63 @@ def test_meson_24c48_sampled_slices(ctx):
         assert report(f"24c48 ins t={t}", CS.block_err(gi[t:t + 1], ref, 2)) < CS.MIXED_TOL
     ref = OC.spectator_meson(S[tf], eta, g5, r[:3], k, L)
     assert report("24c48 spec", CS.block_err(gs, ref, 1)) < CS.MIXED_TOL
+
+
+@pytest.mark.parametrize("L,n_r,n2max,cmax,r,dtype", [
+    (3, 3, 2, -1, (1, 2, 0, 0), np.complex128),   # odd n_r, source off the origin
+    (4, 2, 3, 1, (0, 0, 0, 0), np.complex64),     # 27 momenta, complex64 storage
+])
+def test_spectator_baryon(ctx, L, n_r, n2max, cmax, r, dtype):
+    from oracle.momenta import momenta
+    c = CS.Case(L, 4, n_r, momenta(n2max, None if cmax < 0 else cmax), seed=1600 + L, r=r, dtype=dtype)
+    got = ctx.spectator(dev(c.S), dev(c.eta(1)), 1, c.r, c.k, prec="mixed", GB=dev(c.SB)).cpu().numpy()
+    ctx.sync()
+    assert report(f"baryon L={L}", CS.block_err(got, c.ref_spectator_baryon(1), 1)) < CS.MIXED_TOL
+
+
+def test_baryon_16c_123mom_sampled_noises(ctx):
+    """Baryon spectator on a 16^3 slice with 32 noises and the 123 momenta of |k|^2 <= 9
+    (components <= 3), complex64 storage; two of the 32 noises against the oracle."""
+    from oracle.momenta import momenta
+    from oracle import contractions as OC
+    from paper_1711_02384_gb300 import inputs
+    L, n_r = 16, 32
+    k = momenta(9, 3)
+    GA = inputs.propagator(3000, L, 4, slices=[1]).astype(np.complex64)
+    GB = inputs.propagator(3000, L, 4, slices=[1], tensor_id=inputs.TID_PROP_B).astype(np.complex64)
+    eta = inputs.noise(3003, L, n_r, 1).astype(np.complex64)
+    r = np.zeros(4, dtype=np.int32)
+    got = ctx.spectator(dev(GA), dev(eta), 0, r, k, prec="mixed", GB=dev(GB)).cpu().numpy()
+    ctx.sync()
+    pick = [0, n_r - 1]
+    ref = OC.spectator_baryon(GA[0].astype(complex), GB[0].astype(complex), eta[pick].astype(complex),
+                              CS.g5_matrix(), r[:3], k, L)
+    assert report("baryon 16^3 sampled", CS.block_err(got[:, pick], ref, 1)) < CS.MIXED_TOL
+
+
+def test_baryon_32c_full_size_sampled_components(ctx):
+    """The full 32^3 baryon workload shape (32 noises, 123 momenta, complex64): sampled
+    output components, each computed by the oracle one by one, per-component relative
+    error over all momenta."""
+    from oracle.momenta import momenta
+    from oracle import contractions as OC
+    from paper_1711_02384_gb300 import inputs
+    L, n_r = 32, 32
+    k = momenta(9, 3)
+    GA = inputs.propagator(3100, L, 64, slices=[10]).astype(np.complex64)
+    GB = inputs.propagator(3100, L, 64, slices=[10], tensor_id=inputs.TID_PROP_B).astype(np.complex64)
+    eta = inputs.noise(3103, L, n_r, 10).astype(np.complex64)
+    r = np.array([3, 7, 11, 0], dtype=np.int32)
+    got = ctx.spectator(dev(GA), dev(eta), 0, r, k, prec="mixed", GB=dev(GB)).cpu().numpy()
+    ctx.sync()
+    rng = np.random.default_rng(5)
+    worst = 0.0
+    for _ in range(6):
+        i = int(rng.integers(n_r))
+        comp = tuple(int(v) for v in rng.integers(0, 4, 5)) + (int(rng.integers(3)),)
+        col = ((((comp[0] * 4 + comp[1]) * 4 + comp[2]) * 4 + comp[3]) * 4 + comp[4]) * 3 + comp[5]
+        ref = OC.spectator_baryon_component(GA[0].astype(complex), GB[0].astype(complex), eta[i].astype(complex),
+                                            CS.g5_matrix(), r[:3], k, L, *comp)
+        err = np.linalg.norm(got[:, i, col] - ref) / np.linalg.norm(ref)
+        worst = max(worst, err)
+    assert report("baryon 32^3 sampled components", worst) < CS.MIXED_TOL

@@ -117,6 +117,24 @@ def test_baryon_gauge_invariance():
     P.check_baryon_gauge_invariance()
 
 
+def test_baryon_single_component_matches_full():
+    """The one-component baryon helper (used for sampled checks on large lattices)
+    equals the corresponding column of the full baryon spectator."""
+    L, V3 = 3, 27
+    GA = inputs.gaussian_array(1, 9, (V3, 12, 12))
+    GB = inputs.gaussian_array(2, 9, (V3, 12, 12))
+    eta = inputs.gaussian_array(3, 9, (2, V3, 12))
+    g5 = G.gamma5(G.chiral())
+    k = M.momenta(2)
+    r = (1, 2, 0)
+    full = C.spectator_baryon(GA, GB, eta, g5, r, k, L)
+    for comp in [(0, 0, 0, 0, 0, 0), (3, 2, 1, 0, 2, 1), (1, 3, 2, 2, 3, 2)]:
+        a1p, a1, a2p, a2, bp, c = comp
+        col = ((((a1p * 4 + a1) * 4 + a2p) * 4 + a2) * 4 + bp) * 3 + c
+        one = C.spectator_baryon_component(GA, GB, eta[1], g5, r, k, L, *comp)
+        assert np.max(np.abs(one - full[:, 1, col])) < 1e-12
+
+
 def test_noise_moments():
     """Z2 x Z2 noise: unit modulus, mean 0 and <eta eta*> = delta within the
     statistical 1/sqrt(N) of Eqs. 6-7."""
