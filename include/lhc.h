@@ -157,6 +157,68 @@ int lhc_combine(lhc_ctx ctx, int kind, const void *spec, int np, const void *ins
                 int n_r, int nt, const void *snk, const void *ins_g, const void *src, int ng,
                 int prec, void *out, void *stream);
 
+/* Free the context's workspace and cached phase tables (they are re-created on demand). */
+int lhc_release_workspace(lhc_ctx ctx);
+
+/* Failure-detection self-test: launches a kernel that waits on a barrier nothing will
+ * complete, with a limit of limit_us microseconds (1..2000000).  The wait gives up, sets
+ * the context's device error word and the kernel returns; lhc_sync then reports
+ * LHC_ETIMEOUT and the context stays usable.  Returns the lhc_sync status. */
+int lhc_selftest_timeout(lhc_ctx ctx, int limit_us, void *stream);
+
+/* ---------------------------------------------------------------- job server
+ * Continuous batching of contraction jobs (the serving form of the hot path; the paper
+ * runs measurements as batch jobs and has no counterpart).  lhc_serve_start starts a
+ * scheduler thread with `slots` execution slots, each with its own stream and workspace,
+ * so admitted jobs overlap on the GPU.  Propagators are registered once and stay resident
+ * on the device.  A job is admitted as soon as a slot is free and the context's HBM budget
+ * (lhc_create) covers the resident propagators, the workspace every slot holds and the
+ * job's additional workspace (an upper bound from its shapes); jobs that can never fit are
+ * refused at submission with LHC_EBUDGET.  Admission is first-fit in submission order.
+ * Results do not depend on what else runs: the kernels sum in a fixed order.  Timestamps
+ * (steady clock, seconds) give submit -> start -> poll-visible completion latencies. */
+typedef enum { LHC_JOB_INSERTION = 0, LHC_JOB_SPECTATOR = 1, LHC_JOB_THREEPT = 2 } lhc_job_type;
+typedef enum {
+  LHC_JOB_QUEUED = 0,
+  LHC_JOB_RUNNING = 1,
+  LHC_JOB_DONE = 2,
+  LHC_JOB_FAILED = 3,
+  LHC_JOB_CANCELED = 4
+} lhc_job_state;
+
+typedef struct {
+  int type;           /* lhc_job_type; THREEPT = insertion + spectator                    */
+  int kind;           /* LHC_MESON or LHC_BARYON (spectator part)                          */
+  int prec;           /* lhc_precision                                                     */
+  uint64_t prop;      /* registered propagator: S3 for the insertion, S1 / GA for the
+                         spectator (one source position, the lattice of the handle)      */
+  uint64_t prop_b;    /* registered GB for baryons, else 0                                 */
+  const void *psi;    /* device, [n_r][T][V3][12] (insertion)                             */
+  const void *eta;    /* device, [n_r][V3][12] on t_sink (spectator)                      */
+  int n_r;
+  int t_lo, t_hi;     /* insertion slices                                                  */
+  int t_sink;         /* spectator slice                                                   */
+  int r[4];           /* source position                                                   */
+  const int *k;       /* host [nq][3]; copied at submission                               */
+  int nq;
+  void *out_ins;      /* device, [t_hi - t_lo + 1][nq][n_r][192]                           */
+  void *out_spec;     /* device, [nq][n_r][192 | 3072]                                     */
+} lhc_job;
+
+int lhc_serve_start(lhc_ctx ctx, int slots);
+int lhc_serve_stop(lhc_ctx ctx);   /* waits for running jobs; lhc_destroy calls it */
+int lhc_prop_register(lhc_ctx ctx, const void *dev_ptr, const lhc_lattice *lat, uint64_t *handle);
+int lhc_prop_release(lhc_ctx ctx, uint64_t handle);   /* LHC_EBUSY while jobs use it */
+int lhc_submit(lhc_ctx ctx, const lhc_job *job, uint64_t *job_id);
+/* non-blocking: LHC_EBUSY while queued or running, LHC_OK once finished (any outcome);
+ * *state receives the lhc_job_state */
+int lhc_poll(lhc_ctx ctx, uint64_t job_id, int *state);
+/* the job's final status, or LHC_ETIMEOUT if it has not finished within timeout_ms */
+int lhc_wait(lhc_ctx ctx, uint64_t job_id, int timeout_ms);
+int lhc_cancel(lhc_ctx ctx, uint64_t job_id);   /* queued jobs only, else LHC_EBUSY */
+int lhc_job_times(lhc_ctx ctx, uint64_t job_id, double *t_submit, double *t_start, double *t_done);
+int lhc_serve_stats(lhc_ctx ctx, size_t *bytes_in_use, int *queued, int *running);
+
 /* Allocation-free variant of lhc_combine (the paper has no counterpart; this is a
  * library service).  For callers that cannot let a library allocate device memory:
  * a process whose device memory is owned by another allocator (for example an analysis

@@ -602,6 +602,21 @@ static int get_phase_split(lhc_ctx ctx, int L, const int *k, int nq, const int r
   return LHC_OK;
 }
 
+// Upper bound of the device memory one mixed-precision call takes beyond its caller's
+// buffers: workspace (partials at the largest site split, narrowed inputs, diquark) and
+// the phase table of its momentum set.  Used for admission control by the job server.
+size_t mixed_call_bytes(Part part, int dtype, int V3, int n_r, int nt, int nq) {
+  const bool baryon = part == PART_SPEC_BARYON;
+  const size_t ncols = (size_t)n_r * (baryon ? kBarCols : 192);
+  const size_t ntl = (size_t)std::min(nt, kMaxSlices);
+  const size_t nkb = (V3 + KSTEP - 1) / KSTEP, nqc = (nq + QCHUNK - 1) / QCHUNK;
+  size_t b = ntl * 8 * nq * ncols * sizeof(float2);
+  if (dtype == LHC_C128) b += ntl * V3 * 144 * 8 + (baryon ? (size_t)V3 * 144 * 8 : 0) + (size_t)n_r * ntl * V3 * 12 * 8;
+  if (baryon) b += (size_t)V3 * 2304 * 8;
+  b += nqc * nkb * 2 * 3 * QCHUNK * 32 + 4096;
+  return b + 4 * 256;
+}
+
 int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int nq, const int r[4], int sign,
                    cudaStream_t st) {
   const SliceJob &j0 = jobs[0];

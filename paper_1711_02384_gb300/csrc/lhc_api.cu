@@ -263,6 +263,7 @@ int lhc_create(lhc_ctx *out, int device, size_t hbm_budget_bytes) {
 
 int lhc_destroy(lhc_ctx ctx) {
   if (!ctx) return fail(LHC_EINVAL, "ctx is NULL");
+  lhc_serve_stop(ctx);
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   dev_free(ctx, ctx->ws);
@@ -282,6 +283,19 @@ int lhc_destroy(lhc_ctx ctx) {
     }
   }
   delete ctx;
+  return LHC_OK;
+}
+
+int lhc_release_workspace(lhc_ctx ctx) {
+  if (!ctx) return fail(LHC_EINVAL, "ctx is NULL");
+  std::lock_guard<std::mutex> g(ctx->mu);
+  LHC_CHECK_CUDA(cudaSetDevice(ctx->device));
+  LHC_CHECK_CUDA(cudaDeviceSynchronize());
+  dev_free(ctx, ctx->ws);
+  dev_free(ctx, ctx->stage);
+  for (auto &kv : ctx->phases) dev_free(ctx, kv.second.buf);
+  ctx->phases.clear();
+  ctx->phase_lru.clear();
   return LHC_OK;
 }
 

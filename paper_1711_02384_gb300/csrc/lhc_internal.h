@@ -127,6 +127,8 @@ int run_slice_f64(lhc_ctx ctx, const SliceJob &job, const double2 *phase, cudaSt
 int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int nq, const int r[4], int sign,
                    cudaStream_t st);
 
+size_t mixed_call_bytes(Part part, int dtype, int V3, int n_r, int nt, int nq);
+
 // combine (k_combine.cu)
 int run_combine(lhc_ctx ctx, int kind, const double2 *spec, int np, const double2 *ins, int nq,
                 int n_r, int nt, const double2 *snk, const double2 *ins_g, const double2 *src, int ng,

@@ -37,6 +37,19 @@ class Lattice(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("T", ctypes.c_int), ("dtype", ctypes.c_int)]
 
 
+JOB_INSERTION, JOB_SPECTATOR, JOB_THREEPT = range(3)
+JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED, JOB_CANCELED = range(5)
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("kind", ctypes.c_int), ("prec", ctypes.c_int),
+                ("prop", ctypes.c_uint64), ("prop_b", ctypes.c_uint64),
+                ("psi", ctypes.c_void_p), ("eta", ctypes.c_void_p), ("n_r", ctypes.c_int),
+                ("t_lo", ctypes.c_int), ("t_hi", ctypes.c_int), ("t_sink", ctypes.c_int),
+                ("r", ctypes.c_int * 4), ("k", ctypes.POINTER(ctypes.c_int)), ("nq", ctypes.c_int),
+                ("out_ins", ctypes.c_void_p), ("out_spec", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -63,11 +76,28 @@ def lib():
         L.lhc_spectator.argtypes = [vp, lp, ci, vp, vp, vp, ci, ci, ip, ip, ci, ci, vp, vp]
         L.lhc_combine.argtypes = [vp, ci, vp, ci, vp, ci, ci, ci, vp, vp, vp, ci, ci, vp, vp]
         L.lhc_sync.argtypes = [vp, vp]
+        u64 = ctypes.c_uint64
+        L.lhc_release_workspace.argtypes = [vp]
+        L.lhc_selftest_timeout.argtypes = [vp, ci, vp]
+        L.lhc_serve_start.argtypes = [vp, ci]
+        L.lhc_serve_stop.argtypes = [vp]
+        L.lhc_prop_register.argtypes = [vp, vp, lp, ctypes.POINTER(u64)]
+        L.lhc_prop_release.argtypes = [vp, u64]
+        L.lhc_submit.argtypes = [vp, ctypes.POINTER(Job), ctypes.POINTER(u64)]
+        L.lhc_poll.argtypes = [vp, u64, ip]
+        L.lhc_wait.argtypes = [vp, u64, ci]
+        L.lhc_cancel.argtypes = [vp, u64]
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.lhc_job_times.argtypes = [vp, u64, dp, dp, dp]
+        L.lhc_serve_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t), ip, ip]
         L.lhc_profile.argtypes = [vp, ci]
         L.lhc_profile_read.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
         for name in ("lhc_create", "lhc_destroy", "lhc_set_gamma5", "lhc_momenta", "lhc_insertion",
-                     "lhc_spectator", "lhc_combine", "lhc_profile", "lhc_profile_read", "lhc_sync"):
+                     "lhc_spectator", "lhc_combine", "lhc_profile", "lhc_profile_read", "lhc_sync", "lhc_release_workspace",
+                     "lhc_selftest_timeout", "lhc_serve_start", "lhc_serve_stop", "lhc_prop_register",
+                     "lhc_prop_release", "lhc_submit", "lhc_poll", "lhc_wait", "lhc_cancel", "lhc_job_times",
+                     "lhc_serve_stats"):
             getattr(L, name).restype = ci
         _lib = L
     return _lib
@@ -227,3 +257,72 @@ class Context:
         _check(lib().lhc_combine(self._h, kind, _ptr(spec), np_, _ptr(ins), nq, n_r, nt, _ptr(snk), _ptr(ins_g),
                                  _ptr(src), ng, PRECISIONS[prec], _ptr(out), _stream(spec, stream)))
         return out
+
+    # ------------------------------------------------------------------ job server
+    def serve_start(self, slots: int = 4):
+        _check(lib().lhc_serve_start(self._h, int(slots)))
+
+    def serve_stop(self):
+        _check(lib().lhc_serve_stop(self._h))
+
+    def prop_register(self, S):
+        """Register a resident device propagator [T][V3][12][12]; returns its handle."""
+        if not S.is_cuda:
+            raise ValueError("registered propagators must be device tensors")
+        lat = Lattice(_L_of(S.shape[1]), S.shape[0], _dtype_code(S))
+        h = ctypes.c_uint64()
+        _check(lib().lhc_prop_register(self._h, _ptr(S), ctypes.byref(lat), ctypes.byref(h)))
+        return h.value
+
+    def prop_release(self, handle):
+        _check(lib().lhc_prop_release(self._h, ctypes.c_uint64(handle)))
+
+    def submit(self, type, prop, k, r=(0, 0, 0, 0), prec="mixed", kind=MESON, prop_b=0, psi=None, eta=None,
+               n_r=None, t_lo=0, t_hi=0, t_sink=0, out_ins=None, out_spec=None):
+        """Submit a job; returns its id.  Tensors must stay alive until the job finishes."""
+        ka, kp = _ints(k)
+        j = Job()
+        j.type, j.kind, j.prec = type, kind, PRECISIONS[prec]
+        j.prop, j.prop_b = prop, prop_b
+        j.psi = psi.data_ptr() if psi is not None else None
+        j.eta = eta.data_ptr() if eta is not None else None
+        j.n_r = n_r if n_r is not None else (psi.shape[0] if psi is not None else eta.shape[0])
+        j.t_lo, j.t_hi, j.t_sink = t_lo, t_hi, t_sink
+        for a in range(4):
+            j.r[a] = int(r[a])
+        j.k, j.nq = kp, ka.size // 3
+        j.out_ins = out_ins.data_ptr() if out_ins is not None else None
+        j.out_spec = out_spec.data_ptr() if out_spec is not None else None
+        jid = ctypes.c_uint64()
+        _check(lib().lhc_submit(self._h, ctypes.byref(j), ctypes.byref(jid)))
+        return jid.value
+
+    def poll(self, jid):
+        """(status, state): status LHC_EBUSY (6) while queued/running, else LHC_OK."""
+        st = ctypes.c_int()
+        s = lib().lhc_poll(self._h, ctypes.c_uint64(jid), ctypes.byref(st))
+        return s, st.value
+
+    def wait(self, jid, timeout_ms=60000):
+        _check(lib().lhc_wait(self._h, ctypes.c_uint64(jid), int(timeout_ms)))
+
+    def wait_status(self, jid, timeout_ms=60000):
+        return lib().lhc_wait(self._h, ctypes.c_uint64(jid), int(timeout_ms))
+
+    def cancel(self, jid):
+        return lib().lhc_cancel(self._h, ctypes.c_uint64(jid))
+
+    def job_times(self, jid):
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().lhc_job_times(self._h, ctypes.c_uint64(jid), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def serve_stats(self):
+        b, q, r = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().lhc_serve_stats(self._h, ctypes.byref(b), ctypes.byref(q), ctypes.byref(r)))
+        return b.value, q.value, r.value
+
+    def selftest_timeout(self, limit_us=200000, stream=None):
+        """Run the bounded-wait self-test; returns the lhc_sync status (LHC_ETIMEOUT expected)."""
+        st = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        return lib().lhc_selftest_timeout(self._h, int(limit_us), ctypes.c_void_p(int(st)))

@@ -70,3 +70,12 @@ def test_binding_loads(lib):
     assert lhc.lib() is not None
     k = lhc.momenta(4)
     assert len(k) == 33
+
+
+def test_server_calls_validate_without_a_gpu(lib):
+    lib.lhc_submit.argtypes = [ctypes.c_void_p] * 3
+    lib.lhc_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]
+    lib.lhc_serve_start.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert lib.lhc_submit(None, None, None) == 1          # no server for a NULL context -> EINVAL
+    assert lib.lhc_poll(None, 1, None) == 7               # LHC_ENOTFOUND
+    assert lib.lhc_serve_start(None, 4) == 1
