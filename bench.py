@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="meson24",
+                    choices=["meson24", "baryon32", "batched", "serve", "mom1"],
+                    help="meson24: the headline line; the others measure the further benchmark rows")
     return ap.parse_args()
 
 
@@ -168,22 +171,14 @@ def run_reference(args):
 
 # --------------------------------------------------------------------------- GPU arm
 
-def gpu_launches_per_step(prec, nq):
-    """Kernels this library launches per step (phase tables are cached after warm-up)."""
-    n = 0
-    for tf in TFS:
-        if prec == "mixed":
-            n += 2 + 2                     # insertion, spectator: fused contraction+projection, FP64 reduce
-        else:
-            n += 2 * (tf + 1) + 2          # per slice: FP64 contraction, FP64 projection
-        n += 1 + (tf + 1) + 1              # combine: sink side, insertion side per slice, GEMM
-    return n
-
-
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload != "meson24":
+        import bench_workloads
+        bench_workloads.run(args)
         return
     import torch
     import torch.distributed as dist
@@ -230,12 +225,14 @@ def main():
     clocks = Clocks(local)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_launch0 = lhc.launch_count()
     e0.record(st)
     for _ in range(args.steps):
         step()
     e1.record(st)
     barrier()
     clk = clocks.stop()
+    n_launches = lhc.launch_count() - n_launch0
     ms = e0.elapsed_time(e1)
     if world > 1:
         t = torch.tensor([ms], device=dev)
@@ -329,7 +326,7 @@ def main():
             "config": {"workload": WORKLOAD, "precision": args.prec, "parallelism": f"replicas x{world}",
                        "l2": "inputs (2.1 GB per step) larger than L2", "units_per_step": upstep},
             "clocks": clk, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": gpu_launches_per_step(args.prec, nq) * args.steps, "kernels": kernels,
+            "gpu_launches": n_launches, "kernels": kernels,
         }))
     ctx.close()
     if world > 1:

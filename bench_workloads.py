@@ -1,0 +1,339 @@
+"""Further benchmark rows of the factorized three-point path (driven by bench.py --workload).
+
+baryon32  baryon 3pt on 32^3 x 64: eps-eps spectator of two complex64 propagators (32
+          noises, 4 sink separations, 123 momenta with |k|^2 <= 9), insertion on every slice
+          up to the sink, baryon combine; mixed precision (or --prec fp64)
+batched   16 source positions x 3 sink separations, 16 noises, meson and baryon parts, each
+          job with its own momentum set (|k|^2 <= 4 .. 16, 33 to 257 momenta); every call of a
+          step captured in one CUDA graph and replayed
+serve     a Poisson stream of three-point jobs on 16^3x32 .. 48^3x96 lattices through the job
+          server (resident propagators, 150 GB budget): latency p50/p99 and throughput, beside
+          the plain FP64 path one job at a time
+mom1      the meson 24^3x48 step at 1 momentum vs 93 momenta (the paper's observation that
+          many more momenta cost little extra)
+
+Inputs are seeded random device tensors (torch): these rows measure throughput; parity
+is the tests' job.  Each row prints one JSON line.
+"""
+import json
+import os
+import time
+
+import numpy as np
+import torch
+
+import bench as B
+from paper_1711_02384_gb300 import lhc
+
+UNIT = "contractions/s"
+
+
+def _peak():
+    p = os.path.join(B.ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(p)).get("bf16_tflops", 1900.0) if os.path.exists(p) else 1900.0
+
+
+def _roofline(ctx):
+    kms, kn, kwork = ctx.profile_read(lhc.KERNEL_FUSED)
+    ach = kwork / (kms / 1e3) / 1e12 if kms > 0 else None
+    peak = _peak()
+    return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak if ach else None, "traffic": None,
+            "kernel_ms_per_launch": kms / kn if kn else None, "launches_per_step": kn,
+            "peak_source": "measured bf16 burst (fp16 same rate)"}
+
+
+def _timed(step, steps, warmup, dev, stream=None):
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    clocks = B.Clocks(dev.index)
+    clocks.start()
+    st = stream or torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = lhc.launch_count()
+    e0.record(st)
+    for _ in range(steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1), clocks.stop(), lhc.launch_count() - n0
+
+
+def _rand(shape, dtype, dev, g):
+    return torch.randn(shape, dtype=dtype, device=dev, generator=g)
+
+
+def _line(args, metric, value, ms, workload, extra):
+    d = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+         "dtype": "f32+f16x2->f32 (mixed)" if args.prec == "mixed" else "f64",
+         "data": "synthetic (seeded random device tensors)", "config": {"workload": workload, "precision": args.prec,
+                    "l2": "inputs of every step larger than L2 (129 MB)"}}
+    d.update(extra)
+    print(json.dumps(d))
+
+
+# --------------------------------------------------------------------------- baryon32
+
+def run_baryon32(args, dev, g):
+    L, TFS, NR = 32, (8, 10, 12, 14), 32
+    V3 = L ** 3
+    k = lhc.momenta(9, 3)
+    nq = len(k)
+    slab = max(TFS) + 1
+    GA = _rand((slab, V3, 12, 12), torch.complex64, dev, g)
+    GB = _rand((slab, V3, 12, 12), torch.complex64, dev, g)
+    psis = [_rand((NR, slab, V3, 12), torch.complex64, dev, g) for _ in TFS]
+    etas = [_rand((NR, V3, 12), torch.complex64, dev, g) for _ in TFS]
+    ng = 4
+    Ws = _rand((ng, 4, 4, 4), torch.complex128, dev, g)
+    Gi = _rand((ng, 4, 4), torch.complex128, dev, g)
+    Wc = _rand((ng, 4, 4, 4), torch.complex128, dev, g)
+    ctx = lhc.Context(0)
+    r = (0, 0, 0, 0)
+    oi = [torch.empty((tf + 1, nq, NR, 192), dtype=torch.complex128, device=dev) for tf in TFS]
+    osb = [torch.empty((nq, NR, 3072), dtype=torch.complex128, device=dev) for _ in TFS]
+    oc = [torch.empty((tf + 1, ng, nq, nq), dtype=torch.complex128, device=dev) for tf in TFS]
+
+    def step():
+        for j, tf in enumerate(TFS):
+            ctx.insertion(GA, psis[j], 0, tf, r, k, prec=args.prec, out=oi[j])
+            ctx.spectator(GA, etas[j], tf, r, k, prec=args.prec, GB=GB, out=osb[j])
+            ctx.combine(osb[j], oi[j], Ws, Gi, Wc, prec=args.prec, out=oc[j])
+
+    ms, clk, nl = _timed(step, args.steps, args.warmup, dev)
+    units = sum(tf + 2 for tf in TFS) * V3 * NR * nq
+    ctx.profile(True)
+    step()
+    torch.cuda.synchronize(dev)
+    ctx.profile(False)
+    kern = {}
+    for kid, name in enumerate(lhc.KERNEL_NAMES):
+        t, n, _ = ctx.profile_read(kid)
+        if n:
+            kern[name] = {"ms_per_step": t, "launches_per_step": n}
+    _line(args, B.METRIC, units * args.steps / (ms / 1e3), ms / args.steps,
+          "baryon 3pt 32^3x64, eps-eps spectator of two complex64 propagators, N_r=32, t_f in {8,10,12,14}, "
+          "123 momenta (|k|^2<=9, |k_j|<=3), insertion on slices 0..t_f, combine for 4 structures",
+          {"clocks": clk, "roofline": _roofline(ctx), "kernels": kern, "units_per_step": units, "gpu_launches": nl})
+    ctx.close()
+
+
+# --------------------------------------------------------------------------- batched
+
+def run_batched(args, dev, g):
+    from paper_1711_02384_gb300 import inputs
+    L, T, NR, DTS = 32, 64, 16, (8, 10, 12)
+    V3 = L ** 3
+    src = inputs.source_positions(4000, L, T, 16)
+    rng = np.random.default_rng(4001)
+    S = _rand((T, V3, 12, 12), torch.complex64, dev, g)
+    psi = _rand((NR, T, V3, 12), torch.complex64, dev, g)
+    eta = _rand((NR, V3, 12), torch.complex64, dev, g)
+    ctx = lhc.Context(0)
+    jobs = []
+    for s_i in range(16):
+        for dt in DTS:
+            n2 = int(rng.integers(4, 17))
+            k = lhc.momenta(n2)
+            nq = len(k)
+            r = [int(v) for v in src[s_i]]
+            t0 = r[3]
+            jobs.append(dict(r=r, t0=t0, dt=dt, k=k, nq=nq,
+                             oi=torch.empty((dt + 1, nq, NR, 192), dtype=torch.complex128, device=dev),
+                             om=torch.empty((nq, NR, 192), dtype=torch.complex128, device=dev),
+                             ob=torch.empty((nq, NR, 3072), dtype=torch.complex128, device=dev)))
+    stream = torch.cuda.Stream(dev)
+
+    def calls():
+        for j in jobs:
+            ctx.insertion(S, psi, j["t0"], j["t0"] + j["dt"], j["r"], j["k"], prec=args.prec, out=j["oi"],
+                          stream=stream.cuda_stream)
+            ts = (j["t0"] + j["dt"]) % T
+            ctx.spectator(S, eta, ts, j["r"], j["k"], prec=args.prec, out=j["om"], stream=stream.cuda_stream)
+            ctx.spectator(S, eta, ts, j["r"], j["k"], prec=args.prec, GB=S, out=j["ob"], stream=stream.cuda_stream)
+
+    with torch.cuda.stream(stream):
+        calls()                      # builds the phase tables and sizes the workspace
+        torch.cuda.synchronize(dev)
+        graph = torch.cuda.CUDAGraph()
+        n0 = lhc.launch_count()
+        with torch.cuda.graph(graph, stream=stream):
+            calls()
+        n_graph = lhc.launch_count() - n0
+        # graph.replay() launches on the current stream: keep it, and the events, on `stream`
+        ms, clk, _ = _timed(lambda: graph.replay(), args.steps, args.warmup, dev, stream=stream)
+        # one replay against the same calls issued directly: identical bits expected
+        outs = [o for j in jobs for o in (j["oi"], j["om"], j["ob"])]
+        for o in outs:
+            o.zero_()
+        graph.replay()
+        torch.cuda.synchronize(dev)
+        from_graph = [o.clone() for o in outs]
+        ctx.profile(True)
+        calls()
+        torch.cuda.synchronize(dev)
+        ctx.profile(False)
+        same = all(torch.equal(a, b) for a, b in zip(from_graph, outs))
+        del from_graph
+    units = sum(V3 * NR * j["nq"] * (j["dt"] + 3) for j in jobs)
+    _line(args, B.METRIC, units * args.steps / (ms / 1e3), ms / args.steps,
+          "batched 32^3x64, 16 sources x t_f-t_0 in {8,10,12}, N_r=16, meson insertion + meson and baryon "
+          "spectators, per-job momentum sets |k|^2<=4..16 (33..257), one CUDA graph per step",
+          {"clocks": clk, "roofline": _roofline(ctx), "units_per_step": units, "jobs": len(jobs),
+           "gpu_launches": n_graph * args.steps, "kernels_per_graph": n_graph,
+           "graph_replay_equals_direct_calls": same})
+    ctx.close()
+
+
+# --------------------------------------------------------------------------- serve
+
+def run_serve(args, dev, g):
+    lat_shapes = [(16, 32), (24, 48), (32, 64), (48, 96)]
+    NRMAX = 32
+    ctx = lhc.Context(0, hbm_budget=150 << 30)
+    ctx.serve_start(slots=4)
+    lats = []
+    for L, T in lat_shapes:
+        V3 = L ** 3
+        S = _rand((T, V3, 12, 12), torch.complex64, dev, g)
+        lats.append(dict(L=L, T=T, V3=V3, S=S, h=ctx.prop_register(S),
+                         psi=_rand((NRMAX, T, V3, 12), torch.complex64, dev, g),
+                         eta=_rand((NRMAX, V3, 12), torch.complex64, dev, g)))
+    rng = np.random.default_rng(5000)
+    njobs = 200
+    specs = []
+    for _ in range(njobs):
+        li = int(rng.integers(4))
+        specs.append(dict(li=li, n_r=int(rng.choice([8, 16, 32])), n2=int(rng.integers(4, 17)),
+                          dt=int(rng.choice([8, 10, 12]))))
+    kcache = {}
+
+    def units(sp):
+        return lats[sp["li"]]["V3"] * sp["n_r"] * len(kcache[sp["n2"]]) * (sp["dt"] + 2)
+
+    for sp in specs:
+        kcache.setdefault(sp["n2"], lhc.momenta(sp["n2"]))
+
+    def submit(sp, prec):
+        la = lats[sp["li"]]
+        k = kcache[sp["n2"]]
+        nq = len(k)
+        oi = torch.empty((sp["dt"] + 1, nq, sp["n_r"], 192), dtype=torch.complex128, device=dev)
+        os_ = torch.empty((nq, sp["n_r"], 192), dtype=torch.complex128, device=dev)
+        jid = ctx.submit(lhc.JOB_THREEPT, la["h"], k, prec=prec, psi=la["psi"], eta=la["eta"], n_r=sp["n_r"],
+                         t_lo=0, t_hi=sp["dt"], t_sink=sp["dt"], out_ins=oi, out_spec=os_)
+        return jid, (oi, os_)
+
+    # warm-up: one job per (lattice, momentum set) shape builds phase tables and workspaces
+    seen = set()
+    warm = []
+    for sp in specs:
+        key = (sp["li"], sp["n2"])
+        if key not in seen:
+            seen.add(key)
+            warm.append(submit(sp, args.prec))
+    for jid, _ in warm:
+        ctx.wait(jid, 600000)
+    torch.cuda.synchronize(dev)
+
+    # capacity: everything submitted at once
+    t0 = time.perf_counter()
+    sub = [submit(sp, args.prec) for sp in specs]
+    for jid, _ in sub:
+        ctx.wait(jid, 600000)
+    cap_s = time.perf_counter() - t0
+    del sub
+    total_units = sum(units(sp) for sp in specs)
+    cap_jobs = njobs / cap_s
+
+    # Poisson arrivals at 70 % of capacity
+    lam = 0.7 * cap_jobs
+    gaps = rng.exponential(1.0 / lam, njobs)
+    clocks = B.Clocks(dev.index)
+    clocks.start()
+    n0 = lhc.launch_count()
+    t0 = time.perf_counter()
+    live = []
+    t_next = t0
+    for sp, gap in zip(specs, gaps):
+        t_next += gap
+        while time.perf_counter() < t_next:
+            time.sleep(min(0.0005, max(0.0, t_next - time.perf_counter())))
+        live.append(submit(sp, args.prec))
+    for jid, _ in live:
+        ctx.wait(jid, 600000)
+    stream_s = time.perf_counter() - t0
+    clk = clocks.stop()
+    n_launch = lhc.launch_count() - n0
+    lat_ms = []
+    for jid, _ in live:
+        ts, tst, td = ctx.job_times(jid)
+        lat_ms.append((td - ts) * 1e3)
+    del live
+
+    # plain FP64, one job at a time, on the jobs of the two smaller lattices (FP64 on the
+    # larger ones takes minutes per job); the mixed path one at a time on the same jobs
+    small = [sp for sp in specs if sp["li"] <= 1][:6]
+    res = {}
+    for prec in ("fp64", args.prec):
+        t0 = time.perf_counter()
+        for sp in small:
+            jid, _ = submit(sp, prec)
+            ctx.wait(jid, 600000)
+        res[prec] = sum(units(sp) for sp in small) / (time.perf_counter() - t0)
+    ctx.close()
+    _line(args, B.METRIC + " (served stream)", total_units / stream_s, stream_s * 1e3 / njobs,
+          "served: 200 Poisson-arriving meson 3pt jobs (spectator + insertion) on 16^3x32, 24^3x48, 32^3x64, "
+          "48^3x96 complex64 resident propagators, N_r in {8,16,32}, |k|^2<=4..16, t_f-t_0 in {8,10,12}, "
+          "4 slots, 150 GB budget, arrival rate 0.7 x measured capacity",
+          {"clocks": clk, "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
+                                          "p99": float(np.percentile(lat_ms, 99)),
+                                          "max": float(np.max(lat_ms))},
+           "capacity": {"jobs_per_s": cap_jobs, "value": total_units / cap_s},
+           "one_at_a_time_small_jobs": {"fp64": res["fp64"], args.prec: res[args.prec], "unit": UNIT,
+                                        "jobs": len(small)},
+           "arrival_rate_jobs_per_s": lam, "gpu_launches": n_launch})
+
+
+# --------------------------------------------------------------------------- mom1
+
+def run_mom1(args, dev, g):
+    L, NR, TFS = 24, 16, (8, 10, 12)
+    V3 = L ** 3
+    S = _rand((13, V3, 12, 12), torch.complex128, dev, g)
+    psis = [_rand((NR, 13, V3, 12), torch.complex128, dev, g) for _ in TFS]
+    etas = [_rand((NR, V3, 12), torch.complex128, dev, g) for _ in TFS]
+    ctx = lhc.Context(0)
+    r = (0, 0, 0, 0)
+    out = {}
+    for name, k in (("nq1", np.zeros((1, 3), dtype=np.int32)), ("nq93", lhc.momenta(8))):
+        nq = len(k)
+        oi = [torch.empty((tf + 1, nq, NR, 192), dtype=torch.complex128, device=dev) for tf in TFS]
+        osp = [torch.empty((nq, NR, 192), dtype=torch.complex128, device=dev) for _ in TFS]
+
+        def step():
+            for j, tf in enumerate(TFS):
+                ctx.insertion(S, psis[j], 0, tf, r, k, prec=args.prec, out=oi[j])
+                ctx.spectator(S, etas[j], tf, r, k, prec=args.prec, out=osp[j])
+
+        ms, clk, nl = _timed(step, args.steps, args.warmup, dev)
+        out[name] = {"ms_per_step": ms / args.steps, "nq": nq, "gpu_launches": nl, "clocks": clk,
+                     "value": sum(tf + 2 for tf in TFS) * V3 * NR * nq * args.steps / (ms / 1e3)}
+    ctx.close()
+    print(json.dumps({"metric": "step time at 93 momenta / step time at 1 momentum (meson 24^3x48)",
+                      "value": out["nq93"]["ms_per_step"] / out["nq1"]["ms_per_step"], "unit": "ratio",
+                      "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "dtype": "f32+f16x2->f32 (mixed)" if args.prec == "mixed" else "f64",
+                      "data": "synthetic (seeded random device tensors)",
+                      "config": {"workload": "meson 24^3x48 insertion+spectator, 1 vs 93 momenta",
+                                 "precision": args.prec}, "runs": out}))
+
+
+def run(args):
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(1711)
+    {"baryon32": run_baryon32, "batched": run_batched, "serve": run_serve, "mom1": run_mom1}[args.workload](args, dev, g)

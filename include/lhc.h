@@ -25,7 +25,8 @@
  * output            always complex128, in caller memory.
  *
  * Memory: every buffer argument may be device memory or host memory (pinned or
- * pageable).  Host buffers are staged through the context's workspace; a call
+ * pageable), and must be 16-byte aligned (the kernels move complex64 data in 16-byte
+ * copies); misaligned buffers return LHC_EINVAL.  Host buffers are staged through the context's workspace; a call
  * that touches any host buffer synchronizes its stream before it returns.  With
  * only device buffers a call is asynchronous on `stream` (a cudaStream_t; NULL =
  * legacy default stream).  The caller owns every buffer it passes; the library
@@ -259,6 +260,11 @@ typedef enum {
 int lhc_profile(lhc_ctx ctx, int enable);
 int lhc_profile_read(lhc_ctx ctx, int kernel, double *total_ms, long long *launches,
                      double *work);
+
+/* Number of CUDA kernel launches this library has issued since it was loaded, over
+ * all contexts and threads (launches replayed from a captured CUDA graph are not
+ * counted again).  Never fails; reading it costs one atomic load. */
+unsigned long long lhc_launch_count(void);
 
 #ifdef __cplusplus
 }

@@ -57,7 +57,7 @@ def build(verbose=False, extra=()):
             if verbose and msg:
                 print(msg, file=sys.stderr)
     if jobs or not os.path.exists(LIB):
-        run([NVCC, *ARCH, "-shared", "-o", LIB, *objs, "-lcuda"])
+        run([NVCC, *ARCH, "-shared", "-o", LIB, *objs])
     return LIB
 
 

@@ -238,14 +238,19 @@ int launch_combine(int kind, const double2 *spec, int np, const double2 *ins, in
   }
   if (kind == LHC_MESON) {
     comb_spec_meson<R><<<np, 256, smem, st>>>(spec, np, n_r, snk, ng, Xs);
+    note_launch();
     comb_ins_meson<R><<<nt * nq, 256, smem, st>>>(ins, nq, n_r, ins_g, src, ng, Xi);
+    note_launch();
   } else {
     size_t ns = (size_t)ng * np * n_r * 3;
     comb_spec_baryon<R><<<blocks(ns, 128), 128, 0, st>>>(spec, np, n_r, snk, src, ng, Xs);
+    note_launch();
     comb_ins_baryon<R><<<nt * nq, 256, smem, st>>>(ins, nq, n_r, ins_g, ng, Xi);
+    note_launch();
   }
   dim3 grid((nq + CTILE - 1) / CTILE, (np + CTILE - 1) / CTILE, nt * ng);
   comb_gemm<R><<<grid, 256, 0, st>>>(Xs, Xi, np, nq, n_r, ng, 1.0 / n_r, out);
+  note_launch();
   return LHC_OK;
 }
 

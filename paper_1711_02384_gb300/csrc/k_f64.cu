@@ -207,6 +207,7 @@ void launch_contract(const SliceJob &j, int s0, int ns, double2 *U, cudaStream_t
   else
     spec_baryon_contract_f64<CT><<<grid, 256, 0, st>>>(S, static_cast<const CT *>(j.SB), v,
                                                        j.vec_stride, j.n_r, s0, ns, j.g5mask, U);
+  note_launch();
 }
 
 }  // namespace
@@ -216,6 +217,7 @@ void launch_phase_f64(double2 *P, const int *k_dev, int nq, int L, int rx, int r
   size_t total = (size_t)nq * L * L * L;
   phase_f64_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(P, k_dev, nq, L, rx, ry, rz,
                                                                     sign, roots_dev);
+  note_launch();
 }
 
 int run_slice_f64(lhc_ctx ctx, const SliceJob &j, const double2 *phase, cudaStream_t st) {
@@ -242,6 +244,7 @@ int run_slice_f64(lhc_ctx ctx, const SliceJob &j, const double2 *phase, cudaStre
       ProfScope ps(ctx, st, LHC_KERNEL_PROJECT, 8.0 * j.nq * (double)cols * ns);
       dim3 grid((cols + PBN - 1) / PBN, (j.nq + PBM - 1) / PBM);
       project_f64<<<grid, 256, 0, st>>>(phase, j.V3, s0, ns, j.nq, U, cols, j.out, s0 > 0);
+      note_launch();
     }
   }
   LHC_CHECK_CUDA(cudaGetLastError());

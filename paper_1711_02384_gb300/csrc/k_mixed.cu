@@ -6,12 +6,16 @@
 // A CTA owns one tile of 128 columns (2 noises x 4 "vector" spins x 16 "matrix"
 // indices s), one chunk of <= 96 momenta and one range of sites:
 //
-//   warp 0      bulk-copies the phase tiles (FP16 hi/lo of [-Im | Re | Im], K-major)
+//   warp 0      bulk-copies the phase tiles (FP16 hi/lo of [-Im | Re | Im], K-major) into
+//               the A/B ring, whose stages the MMA frees
+//   warp 22     loads the contraction inputs of each k-step with TMA tensor copies (the
+//               propagator or diquark box and the two noises' vector box) into the input
+//               ring, whose stages the producers free
 //   warp 1      allocates tensor memory and issues the MMAs
 //   warps 2-9   drain the accumulator every KD k-steps into an FP32 running sum
-//   warps 10-17 producers: each gathers the inputs of its 4 sites per 32-site iteration
-//               into shared memory (cp.async), contracts them in FP32, splits each value
-//               into fp16 hi + lo and writes the four A tiles (Ur hi/lo, Ui hi/lo), MN-major
+//   warps 10-21 producers, four per k-step and three k-steps in flight: contract the
+//               inputs in FP32, split each value into fp16 hi + lo and write the four A
+//               tiles (Ur hi/lo, Ui hi/lo), MN-major
 //
 // Per k-step (16 sites) the accumulator D (128 x 2Np, FP32, tensor memory) receives
 //   Ur_h [Re|Im]_h + Ur_h [Re|Im]_l + Ur_l [Re|Im]_h + Ui_h [-Im|Re]_h + Ui_h [-Im|Re]_l
@@ -23,6 +27,9 @@
 #include <cmath>
 #include <cstdlib>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "lhc_internal.h"
 #include "tc_ptx.cuh"
 
@@ -32,17 +39,19 @@ namespace {
 constexpr int MT = 128;                  // GEMM M tile: output columns per CTA
 constexpr int KSTEP = 16;                // sites per MMA k-step
 constexpr int QCHUNK = 96;               // momenta per CTA (accumulator registers bound this)
-constexpr int ATILE = MT * KSTEP * 2;    // bytes of one 128 x 16 fp16 operand tile
+// one 128 x 16 fp16 operand tile, MN-major with 16 B of padding per 8-row group
+// (row groups 144 B apart, the two 8-site k blocks 2304 B apart)
+constexpr int ATILE = 2 * 16 * 144;
 constexpr int ASTAGE = 4 * ATILE;        // Ur hi, Ur lo, Ui hi, Ui lo
-constexpr int NSTAGE = 5;
-constexpr int PSITES = 32;               // sites per producer iteration (two k-steps)
-constexpr int RVALS = 72;                // gathered complex values per site and tile
-constexpr int WSITES = 4;                // sites per producer warp and iteration
-constexpr int RBUF = RVALS * WSITES;     // float2 per warp gather buffer (two per warp)
-constexpr int kWarps = 18;
+constexpr int NSTAGE = 4;                // A/B ring (freed by the MMA)
+constexpr int NIN = 6;                   // input ring (freed by the producers)
+constexpr int NPK = 3;                   // k-steps in flight in the producers (4 warps each)
+// warp roles: 0 phase-tile loader, 1 MMA issue, 2-9 drain, 10-21 producers, 22 input loader
+constexpr int kWarps = 23;
 constexpr int kThreads = kWarps * 32;
 constexpr int kDrainWarp0 = 2;
 constexpr int kProdWarp0 = 10;
+constexpr int kInWarp = kProdWarp0 + 4 * NPK;
 constexpr uint32_t kTmemCols = 512;
 
 // K-major, no swizzle: (row, k) -> core matrices of 8 rows x 16 B; 16 k per row block
@@ -96,13 +105,22 @@ __global__ void phase_split_kernel(__half *out, const int *k, int nq, int Np, in
 }
 
 // ------------------------------------------------------------ fused kernel
-constexpr int kMaxSlices = 64;   // slices per launch (pointers travel as kernel parameters)
+constexpr int kMaxSlices = 64;   // slices per launch (time coordinates travel as kernel parameters)
 
+// Tensor maps (built on the host per launch) of the two contraction inputs, both complex64
+// viewed as 8-byte elements:
+//   tmM  meson/insertion: the propagator as [T][V3][4 bt][3 c][12 ba] (column index
+//        (bt*3 + c)*12 + ba of the 144 per site), box [1][16][2][3][12]: 16 sites, two
+//        consecutive bt blocks (every 16-column tile lies within two), all colours;
+//        baryon: the diquark as [V3][3 c'][768 s], box [16][3][16].
+//   tmV  the vector (psi or eta) as [n_r][T][V3][12], box [2][1][16][12]: the tile's two
+//        noises on 16 sites (noises past n_r and sites past V3 read as zero).
 struct FusedParams {
-  SlicePtrs slices[kMaxSlices];   // per slice: propagator slice [V3][144], vec (psi or eta) noise 0
-  size_t vec_stride;         // elements between noises of vec
-  const __half *B;           // phase table
-  float2 *partial;           // [nt][nsplit][nq][ncols]
+  CUtensorMap tmM;   // (CUtensorMap carries its own 64-byte alignment)
+  CUtensorMap tmV;
+  int tM[kMaxSlices], tV[kMaxSlices];   // per slice: time coordinate in tmM, tmV
+  const __half *B;                      // phase table
+  float2 *partial;                      // [nt][nsplit][nq][ncols]
   int *err;
   int n_r, V3, nct, nkb, nqc, nq, ncols, nsplit, kd, g5mask;
 };
@@ -116,22 +134,41 @@ __device__ __forceinline__ void split2(float v0, float v1, uint32_t &hi, uint32_
   lo = *reinterpret_cast<uint32_t *>(&l);
 }
 
+// Shared memory: NSTAGE stages of the A tiles (Ur hi, Ur lo, Ui hi, Ui lo) and the phase
+// tile B, then NIN stages of the matrix box M and the vector box V.  Every region size is
+// a multiple of 1024 bytes.
+template <int MODE, int NP>
+struct Stage {
+  static constexpr int A = ASTAGE;
+  static constexpr int B = 2 * 3 * NP * 32;
+  static constexpr int M = MODE == 2 ? 16 * 48 * 8 : 16 * 72 * 8;
+  static constexpr int V = 2 * 16 * 12 * 8;
+  static constexpr int ab = A + B;
+  static constexpr int in = M + V;
+  static constexpr int bytes = NSTAGE * ab + NIN * in;
+};
+
 template <typename CT, int MODE, int NP>
-__global__ void __launch_bounds__(kThreads, 1) fused_meson(FusedParams p) {
+__global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant__ FusedParams p) {
   static_assert(NP % 16 == 0 && NP <= QCHUNK, "momentum chunk");
-  constexpr int BSTAGE = 2 * 3 * NP * 32;
+  using St = Stage<MODE, NP>;
   // tensor memory: D buffers [0, 2NP) and [2NP, 4NP); the rest holds NT columns of each
   // half's running sum, the remaining NR = NP - NT columns stay in registers
   constexpr int NT = ((kTmemCols - 4 * NP) / 2 / 16 * 16) < NP ? ((kTmemCols - 4 * NP) / 2 / 16 * 16) : NP;
   constexpr int NR = NP - NT;
-  extern __shared__ __align__(1024) char smem[];
-  char *sA = smem;
-  char *sB = sA + NSTAGE * ASTAGE;
-  float2 *R = reinterpret_cast<float2 *>(sB + NSTAGE * BSTAGE);        // [8 warps][2][RVALS][WSITES]
-  uint64_t *bars = reinterpret_cast<uint64_t *>(R + 8 * 2 * RBUF);
-  uint64_t *fullA = bars, *fullB = bars + NSTAGE, *empty = bars + 2 * NSTAGE,
-           *tfull = bars + 3 * NSTAGE, *tempty = bars + 3 * NSTAGE + 2, *done = bars + 3 * NSTAGE + 4;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 3 * NSTAGE + 5);
+  extern __shared__ __align__(1024) char smem_raw[];
+  // TMA destinations want 128-byte alignment: align the stage ring to 1024 explicitly
+  char *smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + St::bytes);
+  // full[s]: the phase tile has landed (transaction bytes) and the four producer warps of
+  // the k-step have written the A tiles; empty[s]: the MMAs of the stage have completed
+  uint64_t *full = bars, *empty = bars + NSTAGE, *inFull = bars + 2 * NSTAGE, *inEmpty = bars + 2 * NSTAGE + NIN,
+           *tfull = bars + 2 * NSTAGE + 2 * NIN, *tempty = tfull + 2, *done = tfull + 4;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+  auto stA = [&](int s) { return smem + s * St::ab; };
+  auto stB = [&](int s) { return smem + s * St::ab + St::A; };
+  auto stM = [&](int s) { return smem + NSTAGE * St::ab + s * St::in; };
+  auto stV = [&](int s) { return smem + NSTAGE * St::ab + s * St::in + St::M; };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ct = blockIdx.x, split = blockIdx.y;
@@ -145,16 +182,18 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(FusedParams p) {
   volatile int *err = p.err;
   // tile = (noise pair, block of 16 matrix columns s), noise pairs fastest so that CTAs
   // sharing the same matrix columns run together (the baryon diquark is reused via L2)
-  constexpr int SCOLS = MODE == 2 ? 768 : 48;        // matrix columns s per noise-vector spin
-  constexpr int MSTRIDE = MODE == 2 ? 2304 : 144;    // complex numbers per site of the matrix operand
   const int npairs = (p.n_r + 1) / 2;
   const int i0 = 2 * (ct % npairs), s0 = 16 * (ct / npairs);   // first noise and first s of this tile
+  const int bt0 = s0 / 12;                                     // first bt block of the matrix box
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
-      tc::mbar_init(&fullA[s], 4);   // the four producer warps that write a k-step
-      tc::mbar_init(&fullB[s], 1);
+      tc::mbar_init(&full[s], 5);   // phase-tile loader + the four producer warps of a k-step
       tc::mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < NIN; ++s) {
+      tc::mbar_init(&inFull[s], 1);
+      tc::mbar_init(&inEmpty[s], 4);   // the four producer warps that read a k-step
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&tfull[b], 1);
@@ -170,56 +209,90 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(FusedParams p) {
   const uint32_t tbase = *tmem_slot;
 
   if (warp == 0) {
-    // ---------------------------------------------------- phase tiles
+    // ---------------------------------------------------- phase tiles (A/B ring)
     if (lane == 0 && nk > 0) {
-      const char *Bsrc = reinterpret_cast<const char *>(p.B) + ((size_t)qc * p.nkb + kb0) * BSTAGE;
+      const char *Bsrc = reinterpret_cast<const char *>(p.B) + ((size_t)qc * p.nkb + kb0) * St::B;
       int issued = 0;
       for (int i = 0; i < nk; ++i) {
-        int s = i % NSTAGE, u = i / NSTAGE;
+        const int s = i % NSTAGE, u = i / NSTAGE;
         if (u > 0 && !tc::mbar_wait(&empty[s], (u - 1) & 1, err, 1)) break;
-        tc::mbar_arrive_expect_tx(&fullB[s], BSTAGE);
-        tc::bulk_g2s(sB + s * BSTAGE, Bsrc + (size_t)i * BSTAGE, BSTAGE, &fullB[s]);
+        tc::mbar_arrive_expect_tx(&full[s], St::B);
+        tc::bulk_g2s(stB(s), Bsrc + (size_t)i * St::B, St::B, &full[s]);
         issued = i + 1;
       }
       for (int i = max(0, issued - NSTAGE); i < issued; ++i) {   // nothing may still be landing
-        int s = i % NSTAGE, u = i / NSTAGE;
+        const int s = i % NSTAGE, u = i / NSTAGE;
         long long t0 = clock64();
-        while (!tc::mbar_try_wait(&fullB[s], u & 1) && clock64() - t0 < tc::kSpinLimit) {
+        while (!tc::mbar_try_wait(&full[s], u & 1) && clock64() - t0 < tc::kSpinLimit && !*err) {
+        }
+      }
+    }
+  } else if (warp == kInWarp) {
+    // ---------------------------------------------------- contraction inputs (input ring, TMA)
+    if (lane == 0 && nk > 0) {
+      const int tm = p.tM[j], tv = p.tV[j];
+      int issued = 0;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % NIN, u = i / NIN;
+        if (u > 0 && !tc::mbar_wait(&inEmpty[s], (u - 1) & 1, err, 7)) break;
+        const int x0 = 16 * (kb0 + i);
+        tc::mbar_arrive_expect_tx(&inFull[s], St::in);
+        if (MODE == 2)
+          tc::tma_load_3d(stM(s), &p.tmM, s0, 0, x0, &inFull[s]);
+        else
+          tc::tma_load_5d(stM(s), &p.tmM, 0, 0, bt0, x0, tm, &inFull[s]);
+        tc::tma_load_4d(stV(s), &p.tmV, 0, x0, tv, i0, &inFull[s]);
+        issued = i + 1;
+      }
+      for (int i = max(0, issued - NIN); i < issued; ++i) {   // nothing may still be landing
+        const int s = i % NIN, u = i / NIN;
+        long long t0 = clock64();
+        while (!tc::mbar_try_wait(&inFull[s], u & 1) && clock64() - t0 < tc::kSpinLimit) {
         }
       }
     }
   } else if (warp == 1) {
     // ---------------------------------------------------- MMA issue
     if (lane == 0 && nk > 0) {
-      // A: MN-major (row m = s*8 + noise*4 + spin), core matrices 8 k x 16 B: LBO (k) 128, SBO (m) 256
+      // A: MN-major (row m = s*8 + noise*4 + spin), core matrices 8 k x 16 B: the 16 row
+      // groups s lie 144 B apart (SBO; the 16 B of padding per group keep the producers'
+      // stores free of bank conflicts), the two 8-site k blocks 2304 B apart (LBO)
       constexpr uint32_t idesc = tc::idesc_f16(MT, 2 * NP) | (1u << 15);
-      const uint32_t aBase = tc::smem_u32(sA), bBase = tc::smem_u32(sB);
-      int i = 0;
+      // Everything between two k-steps' MMAs is on the tensor pipe's critical path (it
+      // queues few MMAs), so the loop does no division and builds no descriptor: the
+      // descriptors of stage 0 are offset by immediates (the start-address field is
+      // bytes / 16 and cannot carry out for shared-memory addresses).
+      const uint64_t dA0 = tc::smem_desc(tc::smem_u32(stA(0)), 2304, 144);
+      const uint64_t dB0 = tc::smem_desc(tc::smem_u32(stB(0)), 128, 256);
+      constexpr uint64_t kStageStep = St::ab >> 4, kATile = ATILE >> 4, kBHalf = (3 * NP * 32) >> 4,
+                         kBIm = (NP * 32) >> 4;
+      int i = 0, s = 0;
+      uint32_t ph = 0;   // phase of full[s] for k-step i
       bool ok = true;
       for (int c = 0; c < nchunks && ok; ++c) {
-        int b = c & 1, ub = c >> 1;
+        const int b = c & 1, ub = c >> 1;
+        // the chunk's accumulator buffer must have been drained (chunk c - 2)
         if (ub > 0 && !tc::mbar_wait(&tempty[b], (ub - 1) & 1, err, 2)) break;
-        tc::tc_fence_after();
         const uint32_t d = tbase + (uint32_t)(b * 2 * NP);
-        int iend = min(nk, (c + 1) * p.kd);
-        for (; i < iend; ++i) {
-          int s = i % NSTAGE, u = i / NSTAGE;
-          if (!tc::mbar_wait(&fullB[s], u & 1, err, 3) || !tc::mbar_wait(&fullA[s], u & 1, err, 4)) {
+        const int iend = min(nk, (c + 1) * p.kd);
+        for (uint32_t acc0 = 0; i < iend; ++i, acc0 = 1) {
+          if (!tc::mbar_wait(&full[s], ph, err, 3)) {
             ok = false;
             break;
           }
           tc::tc_fence_after();
-          uint32_t a = aBase + s * ASTAGE, bb = bBase + s * BSTAGE;
-          auto dA = [&](int t) { return tc::smem_desc(a + t * ATILE, 128, 256); };
-          auto dB = [&](int h, int row0) { return tc::smem_desc(bb + h * 3 * NP * 32 + row0 * 32, 128, 256); };
-          uint32_t acc0 = (i == c * p.kd) ? 0u : 1u;
-          tc::mma_f16(d, dA(0), dB(0, NP), idesc, acc0);   // Ur_h [Re|Im]_h
-          tc::mma_f16(d, dA(0), dB(1, NP), idesc, 1u);     // Ur_h [Re|Im]_l
-          tc::mma_f16(d, dA(1), dB(0, NP), idesc, 1u);     // Ur_l [Re|Im]_h
-          tc::mma_f16(d, dA(2), dB(0, 0), idesc, 1u);      // Ui_h [-Im|Re]_h
-          tc::mma_f16(d, dA(2), dB(1, 0), idesc, 1u);      // Ui_h [-Im|Re]_l
-          tc::mma_f16(d, dA(3), dB(0, 0), idesc, 1u);      // Ui_l [-Im|Re]_h
+          const uint64_t a = dA0 + s * kStageStep, bb = dB0 + s * kStageStep;
+          tc::mma_f16(d, a, bb + kBIm, idesc, acc0);                    // Ur_h [Re|Im]_h
+          tc::mma_f16(d, a, bb + kBHalf + kBIm, idesc, 1u);             // Ur_h [Re|Im]_l
+          tc::mma_f16(d, a + kATile, bb + kBIm, idesc, 1u);             // Ur_l [Re|Im]_h
+          tc::mma_f16(d, a + 2 * kATile, bb, idesc, 1u);                // Ui_h [-Im|Re]_h
+          tc::mma_f16(d, a + 2 * kATile, bb + kBHalf, idesc, 1u);       // Ui_h [-Im|Re]_l
+          tc::mma_f16(d, a + 3 * kATile, bb, idesc, 1u);                // Ui_l [-Im|Re]_h
           tc::mma_commit(&empty[s]);
+          if (++s == NSTAGE) {
+            s = 0;
+            ph ^= 1u;
+          }
         }
         tc::mma_commit(&tfull[b]);
       }
@@ -302,125 +375,93 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(FusedParams p) {
     }
   } else {
     // ---------------------------------------------------- producers
-    // Each producer warp owns 4 sites of every 32-site iteration (warps 0-3 fill the first
-    // k-step, warps 4-7 the second) and computes all 128 rows for them, so the warps only
-    // synchronise through the stage barriers.  Lane = (site x in 0..3, s pair slp in 0..7).
-    const int pw = warp - kProdWarp0;                    // 0..7
-    const int xl = lane & 3, slp = lane >> 2;
-    const float2 *S = static_cast<const float2 *>(p.slices[j].S);
-    const float2 *vec = static_cast<const float2 *>(p.slices[j].vec);
-    const int nit = (nk + 1) / 2;
-    float2 *Rw = R + pw * 2 * RBUF;                      // this warp's two gather buffers [72][4]
-    // gather: value v = lane + 32*jj of the warp's 4 x 72; jj < 6: the 48 propagator entries
-    // (colour c, s) of each site, jj >= 6: the 2 x 12 noise-vector entries.  Copies go
-    // global -> shared with cp.async (zero-filled out of range), one iteration ahead.
-    int goff[9], soff[9], xs[9];
-    bool live[9];
+    // Producer warp pw computes k-step kofs of every NPK k-steps for 4 of its 16 sites
+    // (quarter wq), all 128 rows (s, noise, spin): lane = (column sp in 0..7, site
+    // xq in 0..3) handles the columns s = sp and sp + 8 for 8 (noise, spin) rows.  A
+    // quarter-warp holds 8 consecutive columns of one site, so its 16-byte A-tile stores
+    // land 144 B apart (distinct banks) and its matrix reads are contiguous.
+    const int pw = warp - kProdWarp0;                    // 0 .. 4 NPK - 1
+    const int kofs = pw >> 2, wq = pw & 3;
+    const int sp = lane & 7, x = 4 * wq + (lane >> 3);   // column and site within the k-step
+    const int nit = (nk + NPK - 1) / NPK;
+    // matrix-box offsets of this lane's two columns (colour 0; colour c adds c*12 or c*16)
+    int mo[2];
 #pragma unroll
-    for (int jj = 0; jj < 9; ++jj) {
-      if (jj < 6) {
-        int v = lane + 32 * jj, x = v / 48, w = v % 48, c = w >> 4, sv = s0 + (w & 15);
-        xs[jj] = x;
-        goff[jj] = MODE == 2 ? x * MSTRIDE + c * SCOLS + sv : x * MSTRIDE + ((sv / 12) * 3 + c) * 12 + sv % 12;
-        soff[jj] = w * WSITES + x;
-        live[jj] = true;
-      } else {
-        int v = lane + 32 * (jj - 6), x = v / 24, ww = v % 24, noise = i0 + ww / 12;
-        xs[jj] = x;
-        live[jj] = noise < p.n_r;
-        goff[jj] = (live[jj] ? noise : 0) * (int)p.vec_stride + x * 12 + ww % 12;
-        soff[jj] = (48 + ww) * WSITES + x;
-      }
+    for (int jx = 0; jx < 2; ++jx) {
+      const int sv = s0 + sp + 8 * jx;
+      mo[jx] = MODE == 2 ? x * 48 + sp + 8 * jx : ((x * 2 + (sv / 12 - bt0)) * 3) * 12 + sv % 12;
     }
-    const int site_end = min(16 * kb1, p.V3);
-    auto issue = [&](int it) {
-      const int base = 16 * kb0 + PSITES * it + WSITES * pw;
-      const int lim = site_end - base;
-      float2 *Rb = Rw + (it & 1) * RBUF;
-      const float2 *Sb = S + (size_t)base * MSTRIDE, *Vb = vec + (size_t)base * 12;
-#pragma unroll
-      for (int jj = 0; jj < 9; ++jj) {
-        bool ok = live[jj] && xs[jj] < lim;
-        const float2 *src = ok ? (jj < 6 ? Sb : Vb) + goff[jj] : S;
-        tc::cp_async8(Rb + soff[jj], src, ok);
-      }
-      tc::cp_async_commit();
-    };
-    // (the gamma5 signs are per output row and are applied to the sums in the epilogue)
-    const int kofs = pw >> 2;                            // k-step of this warp within the iteration
-    const int kk = WSITES * (pw & 3) + xl;               // site within the k-step
-    if (nit > 0) issue(0);
     for (int it = 0; it < nit; ++it) {
-      if (it + 1 < nit) {
-        issue(it + 1);
-        tc::cp_async_wait<1>();   // this lane's copies for iteration it have landed
-      } else {
-        tc::cp_async_wait<0>();
+      const int kstep = NPK * it + kofs;
+      if (kstep >= nk) break;
+      const int si = kstep % NIN, ui = kstep / NIN;
+      {
+        // a wait that gives up (a loader stopped, or the limit ran out) ends the loop
+        int ok = 0;
+        if (lane == 0) ok = tc::mbar_wait(&inFull[si], ui & 1, err, 6) ? 1 : 0;
+        if (!__shfl_sync(0xffffffffu, ok, 0)) break;
       }
-      const int failed = __shfl_sync(0xffffffffu, lane == 0 ? *err : 0, 0);
-      if (failed) break;
-      __syncwarp();                // the warp's copies are visible to all its lanes
-      const int kstep = 2 * it + kofs;
-      if (kstep < nk) {
-        const int s = kstep % NSTAGE, u = kstep / NSTAGE;
-        if (u > 0) {
-          int ok = 1;
-          if (lane == 0) ok = tc::mbar_wait(&empty[s], (u - 1) & 1, err, 6) ? 1 : 0;
-          __syncwarp();
-        }
-        const float2 *Rc = Rw + (it & 1) * RBUF;
-        float2 acc[2][8];
+      const float2 *Ms = reinterpret_cast<const float2 *>(stM(si));
+      const float2 *Vs = reinterpret_cast<const float2 *>(stV(si)) + x * 12;
+      float2 acc[2][8];
 #pragma unroll
-        for (int jx = 0; jx < 2; ++jx)
+      for (int jx = 0; jx < 2; ++jx)
 #pragma unroll
-          for (int iv = 0; iv < 8; ++iv) acc[jx][iv] = make_float2(0.f, 0.f);
+        for (int iv = 0; iv < 8; ++iv) acc[jx][iv] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          float2 sv[2];
+      for (int c = 0; c < 3; ++c) {
+        float2 sv[2];
 #pragma unroll
-          for (int jx = 0; jx < 2; ++jx) sv[jx] = Rc[(c * 16 + 2 * slp + jx) * WSITES + xl];
+        for (int jx = 0; jx < 2; ++jx) sv[jx] = Ms[mo[jx] + c * (MODE == 2 ? 16 : 12)];
 #pragma unroll
-          for (int iv = 0; iv < 8; ++iv) {
-            const float2 pv = Rc[(48 + (iv >> 2) * 12 + (iv & 3) * 3 + c) * WSITES + xl];
+        for (int iv = 0; iv < 8; ++iv) {
+          const float2 pv = Vs[(iv >> 2) * 16 * 12 + (iv & 3) * 3 + c];   // noise iv/4, spin iv%4
 #pragma unroll
-            for (int jx = 0; jx < 2; ++jx) {
-              float2 &a = acc[jx][iv];
-              if (MODE == 0) {          // conj(psi) * S
-                a.x = fmaf(pv.x, sv[jx].x, fmaf(pv.y, sv[jx].y, a.x));
-                a.y = fmaf(pv.x, sv[jx].y, fmaf(-pv.y, sv[jx].x, a.y));
-              } else if (MODE == 1) {   // eta * conj(S)
-                a.x = fmaf(pv.x, sv[jx].x, fmaf(pv.y, sv[jx].y, a.x));
-                a.y = fmaf(pv.y, sv[jx].x, fmaf(-pv.x, sv[jx].y, a.y));
-              } else {                  // eta * D
-                a.x = fmaf(pv.x, sv[jx].x, fmaf(-pv.y, sv[jx].y, a.x));
-                a.y = fmaf(pv.x, sv[jx].y, fmaf(pv.y, sv[jx].x, a.y));
-              }
+          for (int jx = 0; jx < 2; ++jx) {
+            float2 &a = acc[jx][iv];
+            if (MODE == 0) {          // conj(psi) * S
+              a.x = fmaf(pv.x, sv[jx].x, fmaf(pv.y, sv[jx].y, a.x));
+              a.y = fmaf(pv.x, sv[jx].y, fmaf(-pv.y, sv[jx].x, a.y));
+            } else if (MODE == 1) {   // eta * conj(S)
+              a.x = fmaf(pv.x, sv[jx].x, fmaf(pv.y, sv[jx].y, a.x));
+              a.y = fmaf(pv.y, sv[jx].x, fmaf(-pv.x, sv[jx].y, a.y));
+            } else {                  // eta * D
+              a.x = fmaf(pv.x, sv[jx].x, fmaf(-pv.y, sv[jx].y, a.x));
+              a.y = fmaf(pv.x, sv[jx].y, fmaf(pv.y, sv[jx].x, a.y));
             }
           }
         }
-        char *a_st = sA + s * ASTAGE;
-#pragma unroll
-        for (int jx = 0; jx < 2; ++jx) {
-          uint32_t rh[4], rl[4], ih[4], il[4];
-#pragma unroll
-          for (int pr = 0; pr < 4; ++pr) {
-            split2(acc[jx][2 * pr].x, acc[jx][2 * pr + 1].x, rh[pr], rl[pr]);
-            split2(acc[jx][2 * pr].y, acc[jx][2 * pr + 1].y, ih[pr], il[pr]);
-          }
-          // MN-major tile: m-group = s (2*slp + jx), its 8 rows contiguous at k = kk
-          uint32_t off = (uint32_t)((2 * slp + jx) * 256 + (kk >> 3) * 128 + (kk & 7) * 16);
-          *reinterpret_cast<uint4 *>(a_st + 0 * ATILE + off) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
-          *reinterpret_cast<uint4 *>(a_st + 1 * ATILE + off) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
-          *reinterpret_cast<uint4 *>(a_st + 2 * ATILE + off) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
-          *reinterpret_cast<uint4 *>(a_st + 3 * ATILE + off) = make_uint4(il[0], il[1], il[2], il[3]);
-        }
-        tc::fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&fullA[s]);
       }
-      __syncwarp();                // all lanes are done reading this buffer before it is refilled
+      // the input stage is read: hand it back to the input loader
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&inEmpty[si]);
+      const int s = kstep % NSTAGE, u = kstep / NSTAGE;
+      if (u > 0) {
+        // the MMA must be done with this A stage (from NSTAGE k-steps ago)
+        int ok = 0;
+        if (lane == 0) ok = tc::mbar_wait(&empty[s], (u - 1) & 1, err, 8) ? 1 : 0;
+        if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+      }
+      char *a_st = stA(s);
+#pragma unroll
+      for (int jx = 0; jx < 2; ++jx) {
+        uint32_t rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+        for (int pr = 0; pr < 4; ++pr) {
+          split2(acc[jx][2 * pr].x, acc[jx][2 * pr + 1].x, rh[pr], rl[pr]);
+          split2(acc[jx][2 * pr].y, acc[jx][2 * pr + 1].y, ih[pr], il[pr]);
+        }
+        // row group s = sp + 8 jx, its 8 rows (noise, spin) contiguous at k = site x
+        const uint32_t off = (uint32_t)((sp + 8 * jx) * 144 + (x >> 3) * 2304 + (x & 7) * 16);
+        *reinterpret_cast<uint4 *>(a_st + 0 * ATILE + off) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+        *reinterpret_cast<uint4 *>(a_st + 1 * ATILE + off) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+        *reinterpret_cast<uint4 *>(a_st + 2 * ATILE + off) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+        *reinterpret_cast<uint4 *>(a_st + 3 * ATILE + off) = make_uint4(il[0], il[1], il[2], il[3]);
+      }
+      tc::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&full[s]);
     }
-    tc::cp_async_wait<0>();        // no copy may still be landing when the CTA retires
   }
   tc::tc_fence_before();
   __syncthreads();
@@ -456,22 +497,26 @@ __global__ void reduce_f64(const float2 *__restrict__ part, int nsplit, size_t p
   out[(size_t)j * out_stride + e] = make_double2((double)hx + (double)lx, (double)hy + (double)ly);
 }
 
-template <int NP>
+template <int MODE, int NP>
 constexpr size_t fused_smem() {
-  return (size_t)NSTAGE * (ASTAGE + 2 * 3 * NP * 32) + (size_t)8 * 2 * RBUF * 8 + (3 * NSTAGE + 5) * 8 + 16;
+  // rings + barriers + tensor-memory slot + up to 1023 B to align the rings
+  return (size_t)Stage<MODE, NP>::bytes + (2 * NSTAGE + 2 * NIN + 5) * 8 + 16 + 1024;
 }
 
 template <int MODE, int NP>
 int launch_fused_t(const FusedParams &p, int nt, cudaStream_t st) {
-  const size_t smem = std::max<size_t>(fused_smem<NP>(), 120 * 1024);   // one CTA per SM
+  constexpr size_t smem = fused_smem<MODE, NP>();
+  static_assert(smem <= 232448, "shared memory per CTA");
   static bool attr = false;
   if (!attr) {
     LHC_CHECK_CUDA(cudaFuncSetAttribute(fused_meson<float2, MODE, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
+                                        (int)std::max<size_t>(smem, 120 * 1024)));
     attr = true;
   }
   dim3 grid(p.nct, p.nsplit, nt * p.nqc);
-  fused_meson<float2, MODE, NP><<<grid, kThreads, smem, st>>>(p);
+  // at least 120 KB so that one CTA runs per SM (the tensor memory is allocated whole)
+  fused_meson<float2, MODE, NP><<<grid, kThreads, std::max<size_t>(smem, 120 * 1024), st>>>(p);
+  note_launch();
   return LHC_OK;
 }
 
@@ -594,6 +639,7 @@ static int get_phase_split(lhc_ctx ctx, int L, const int *k, int nq, const int r
   phase_split_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
       reinterpret_cast<__half *>(base), reinterpret_cast<const int *>(base + off_k), nq, Np, nqc, nkb, L, key.rx,
       key.ry, key.rz, sign, reinterpret_cast<const double2 *>(base + off_roots));
+  note_launch();
   LHC_CHECK_CUDA(cudaGetLastError());
   e.nq_pad = Np;
   ctx->phases[key] = e;
@@ -615,6 +661,63 @@ size_t mixed_call_bytes(Part part, int dtype, int V3, int n_r, int nt, int nq) {
   if (baryon) b += (size_t)V3 * 2304 * 8;
   b += nqc * nkb * 2 * 3 * QCHUNK * 32 + 4096;
   return b + 4 * 256;
+}
+
+// Tiled tensor map over complex64 data viewed as 8-byte elements (innermost dimension
+// first; strides in bytes for dimensions 1..rank-1).
+static int encode_map(CUtensorMap *m, int rank, const void *base, const uint64_t *dims, const uint64_t *strides,
+                      const uint32_t *box) {
+  cuuint64_t d[5], sb[4];
+  cuuint32_t b[5], es[5];
+  for (int i = 0; i < rank; ++i) {
+    d[i] = dims[i];
+    b[i] = box[i];
+    es[i] = 1;
+  }
+  for (int i = 0; i + 1 < rank; ++i) sb[i] = strides[i];
+  // the driver function is looked up through the runtime, so that the library itself
+  // loads on machines without a driver (and links no libcuda)
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      set_error("the driver does not provide cuTensorMapEncodeTiled");
+      return LHC_ECUDA;
+    }
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, (cuuint32_t)rank, const_cast<void *>(base), d, sb, b, es,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d) for a rank-%d map", (int)r, rank);
+    return LHC_ECUDA;
+  }
+  return LHC_OK;
+}
+
+// Time coordinates of slices that lie in one tensor at multiples of slice_bytes from the
+// lowest of them (slices wrap around the time extent, so the order is not monotonic).
+static int slice_coords(const void *const *ptrs, int nb, size_t slice_bytes, const char **base, int *coord,
+                        int *extent) {
+  const char *lo = static_cast<const char *>(ptrs[0]);
+  for (int j = 1; j < nb; ++j) lo = std::min(lo, static_cast<const char *>(ptrs[j]));
+  int hi = 0;
+  for (int j = 0; j < nb; ++j) {
+    const size_t d = static_cast<const char *>(ptrs[j]) - lo;
+    if (d % slice_bytes != 0 || d / slice_bytes > (size_t)1 << 30) {
+      set_error("slices of one call must lie in one tensor");
+      return LHC_EINVAL;
+    }
+    coord[j] = (int)(d / slice_bytes);
+    hi = std::max(hi, coord[j]);
+  }
+  *base = lo;
+  *extent = hi + 1;
+  return LHC_OK;
 }
 
 int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int nq, const int r[4], int sign,
@@ -678,20 +781,49 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
       ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT, (double)nb * V3 * ((baryon ? 288.0 : 144.0) + 12.0 * n_r) * 24);
       dim3 grid((unsigned)std::max(1, std::min(1024, (V3 * 144 + 255) / 256 / 4)), nb, (baryon ? 2 : 1) + n_r);
       narrow_c128<<<grid, 256, 0, st>>>(np);
-      for (int j = 0; j < nb; ++j)
-        fp.slices[j] = SlicePtrs{np.Sst + (size_t)j * V3 * 144, np.Vst + (size_t)j * V3 * 12};
-      fp.vec_stride = (size_t)nb * V3 * 12;
+      note_launch();
+    }
+    // tensor maps of the matrix operand and the vector of this chunk of slices
+    const char *Mbase, *Vbase;
+    int Tm, Tv;
+    size_t vstride_bytes;
+    if (narrow) {
+      Mbase = ws + off_s;
+      Vbase = ws + off_v;
+      for (int j = 0; j < nb; ++j) fp.tM[j] = fp.tV[j] = j;
+      Tm = Tv = nb;
+      vstride_bytes = (size_t)nb * V3 * 12 * sizeof(float2);
     } else {
-      for (int j = 0; j < nb; ++j) fp.slices[j] = SlicePtrs{jobs[jb + j].S, jobs[jb + j].vec};
-      fp.vec_stride = j0.vec_stride;
+      const void *mp[kMaxSlices], *vp[kMaxSlices];
+      for (int j = 0; j < nb; ++j) {
+        mp[j] = jobs[jb + j].S;
+        vp[j] = jobs[jb + j].vec;
+      }
+      LHC_TRY(slice_coords(mp, nb, (size_t)V3 * 144 * sizeof(float2), &Mbase, fp.tM, &Tm));
+      LHC_TRY(slice_coords(vp, nb, (size_t)V3 * 12 * sizeof(float2), &Vbase, fp.tV, &Tv));
+      vstride_bytes = j0.vec_stride * sizeof(float2);
     }
     if (baryon) {   // the matrix operand becomes the diquark of the (single) sink slice
-      const float2 *GA = static_cast<const float2 *>(fp.slices[0].S);
+      const float2 *GA = reinterpret_cast<const float2 *>(Mbase) + (size_t)fp.tM[0] * V3 * 144;
       const float2 *GB = narrow ? reinterpret_cast<const float2 *>(ws + off_sb) : static_cast<const float2 *>(j0.SB);
       float2 *D = reinterpret_cast<float2 *>(ws + off_d);
       ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT, (double)V3 * (288.0 + 2304.0) * 8);
       baryon_diquark<<<V3, 256, 0, st>>>(GA, GB, V3, D);
-      fp.slices[0].S = D;
+      note_launch();
+      const uint64_t dims[3] = {768, 3, (uint64_t)V3}, strides[2] = {768 * 8, 2304 * 8};
+      const uint32_t box[3] = {16, 3, 16};
+      LHC_TRY(encode_map(&fp.tmM, 3, D, dims, strides, box));
+    } else {
+      const uint64_t dims[5] = {12, 3, 4, (uint64_t)V3, (uint64_t)Tm};
+      const uint64_t strides[4] = {96, 288, 1152, (uint64_t)V3 * 1152};
+      const uint32_t box[5] = {12, 3, 2, 16, 1};
+      LHC_TRY(encode_map(&fp.tmM, 5, Mbase, dims, strides, box));
+    }
+    {
+      const uint64_t dims[4] = {12, (uint64_t)V3, (uint64_t)Tv, (uint64_t)n_r};
+      const uint64_t strides[3] = {96, (uint64_t)V3 * 96, vstride_bytes};
+      const uint32_t box[4] = {12, 16, 1, 2};
+      LHC_TRY(encode_map(&fp.tmV, 4, Vbase, dims, strides, box));
     }
     {
       ProfScope ps(ctx, st, LHC_KERNEL_FUSED, 8.0 * nb * (double)nq * ncols * V3);
@@ -706,6 +838,7 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
       ProfScope ps(ctx, st, LHC_KERNEL_REDUCE, (double)nb * nsplit * n_out * 8 + (double)nb * n_out * 16);
       reduce_f64<<<(unsigned)((n_out * nb + 255) / 256), 256, 0, st>>>(fp.partial, nsplit, n_out,
                                                                           jobs[jb].out, n_out, nb, n_out);
+      note_launch();
     }
   }
   LHC_CHECK_CUDA(cudaGetLastError());

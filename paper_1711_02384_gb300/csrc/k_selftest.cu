@@ -38,6 +38,7 @@ extern "C" int lhc_selftest_timeout(lhc_ctx ctx, int limit_us, void *stream) {
   long long cycles = (long long)limit_us * (long long)clk_khz / 1000;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   never_completed_wait<<<1, 32, 0, st>>>(ctx->dev_err, cycles);
+  lhc::note_launch();
   LHC_CHECK_CUDA(cudaGetLastError());
   return lhc_sync(ctx, stream);
 }

@@ -9,6 +9,8 @@
 
 namespace lhc {
 
+std::atomic<unsigned long long> g_launches{0};
+
 static thread_local char g_err[512] = "";
 
 void set_error(const char *fmt, ...) {
@@ -231,6 +233,8 @@ const char *lhc_strerror(int status) {
 const char *lhc_last_error(void) { return g_err; }
 
 int lhc_version(void) { return 100; }
+
+unsigned long long lhc_launch_count(void) { return lhc::g_launches.load(std::memory_order_relaxed); }
 
 int lhc_create(lhc_ctx *out, int device, size_t hbm_budget_bytes) {
   if (!out) return fail(LHC_EINVAL, "ctx pointer is NULL");
@@ -496,6 +500,8 @@ int common_checks(lhc_ctx ctx, const lhc_lattice *lat, const void *S, const void
   if (!ctx) return fail(LHC_EINVAL, "ctx is NULL");
   LHC_TRY(check_lattice(lat));
   if (!S || !vec || !out || !r || !k) return fail(LHC_EINVAL, "NULL buffer argument");
+  if (((uintptr_t)S | (uintptr_t)vec | (uintptr_t)out) & 15)
+    return fail(LHC_EINVAL, "propagator, vector and output buffers must be 16-byte aligned");
   if (n_r < 1 || n_r > 4096) return fail(LHC_EINVAL, "n_r=%d out of range", n_r);
   if (nq < 1 || nq > 65536) return fail(LHC_EINVAL, "nq=%d out of range", nq);
   if (prec != LHC_FP64 && prec != LHC_MIXED) return fail(LHC_EINVAL, "unknown precision %d", prec);
@@ -528,6 +534,7 @@ int lhc_spectator(lhc_ctx ctx, const lhc_lattice *lat, int kind, const void *S1_
   if (kind != LHC_MESON && kind != LHC_BARYON) return fail(LHC_EINVAL, "unknown kind %d", kind);
   if ((kind == LHC_MESON) != (GB == nullptr))
     return fail(LHC_EINVAL, "GB must be NULL for mesons and given for baryons");
+  if ((uintptr_t)GB & 15) return fail(LHC_EINVAL, "GB must be 16-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> g(ctx->mu);
   LHC_TRY(begin_call(ctx, st));

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <list>
@@ -14,6 +15,11 @@
 #include "lhc.h"
 
 namespace lhc {
+
+// ---------------------------------------------------------------- launch accounting
+// Every kernel launch site calls note_launch() right after the launch.
+extern std::atomic<unsigned long long> g_launches;
+inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------- errors
 void set_error(const char *fmt, ...);

@@ -40,6 +40,7 @@ struct Job {
   std::vector<int> k;   // copied momentum list
   int state = LHC_JOB_QUEUED;
   int status = LHC_OK;
+  std::string msg;      // error text of a failed job
   size_t need = 0;      // workspace upper bound
   int slot = -1;
   double t_submit = 0, t_start = 0, t_done = 0;
@@ -135,6 +136,7 @@ void worker_main(lhc_server_s *s) {
       Job *jb = sl.job;
       int st = lhc_sync(sl.sub, sl.stream);   // the stream is idle; reads the device error word
       jb->status = st;
+      if (st != LHC_OK) jb->msg = lhc_last_error();
       jb->state = st == LHC_OK ? LHC_JOB_DONE : LHC_JOB_FAILED;
       jb->t_done = now_s();
       sl.job = nullptr;
@@ -172,6 +174,7 @@ void worker_main(lhc_server_s *s) {
       lk.lock();
       if (st != LHC_OK) {
         pick->status = st;
+        pick->msg = lhc_last_error();
         pick->state = LHC_JOB_FAILED;
         pick->t_done = now_s();
         sl.job = nullptr;
@@ -245,8 +248,9 @@ int lhc_prop_register(lhc_ctx ctx, const void *dev_ptr, const lhc_lattice *lat, 
     lhc::set_error("lhc_prop_register: call lhc_serve_start first");
     return LHC_EINVAL;
   }
-  if (!dev_ptr || !lat || !handle || lat->L < 1 || lat->T < 1 || (lat->dtype != LHC_C128 && lat->dtype != LHC_C64)) {
-    lhc::set_error("lhc_prop_register: bad arguments");
+  if (!dev_ptr || !lat || !handle || lat->L < 1 || lat->T < 1 || (lat->dtype != LHC_C128 && lat->dtype != LHC_C64) ||
+      ((uintptr_t)dev_ptr & 15)) {
+    lhc::set_error("lhc_prop_register: bad arguments (NULL, bad lattice, or not 16-byte aligned)");
     return LHC_EINVAL;
   }
   cudaPointerAttributes a;
@@ -293,8 +297,9 @@ int lhc_submit(lhc_ctx ctx, const lhc_job *job, uint64_t *job_id) {
     return LHC_EINVAL;
   }
   if (!job || !job_id || job->type < LHC_JOB_INSERTION || job->type > LHC_JOB_THREEPT || job->n_r < 1 ||
-      job->nq < 1 || !job->k || (job->prec != LHC_FP64 && job->prec != LHC_MIXED)) {
-    lhc::set_error("lhc_submit: bad job description");
+      job->nq < 1 || !job->k || (job->prec != LHC_FP64 && job->prec != LHC_MIXED) ||
+      (((uintptr_t)job->psi | (uintptr_t)job->eta | (uintptr_t)job->out_ins | (uintptr_t)job->out_spec) & 15)) {
+    lhc::set_error("lhc_submit: bad job description (sizes, precision, or a buffer not 16-byte aligned)");
     return LHC_EINVAL;
   }
   std::unique_lock<std::mutex> lk(s->mu);
@@ -366,6 +371,8 @@ int lhc_wait(lhc_ctx ctx, uint64_t job_id, int timeout_ms) {
     return LHC_ETIMEOUT;
   }
   if (jb->state == LHC_JOB_CANCELED) return LHC_ECANCELED;
+  if (jb->status != LHC_OK)
+    lhc::set_error("job %llu failed: %s", (unsigned long long)job_id, jb->msg.c_str());
   return jb->status;
 }
 

@@ -68,6 +68,8 @@ def lib():
         L.lhc_last_error.restype = ctypes.c_char_p
         L.lhc_last_error.argtypes = []
         L.lhc_version.restype = ci
+        L.lhc_launch_count.restype = ctypes.c_ulonglong
+        L.lhc_launch_count.argtypes = []
         L.lhc_create.argtypes = [ctypes.POINTER(vp), ci, sz]
         L.lhc_destroy.argtypes = [vp]
         L.lhc_set_gamma5.argtypes = [vp, ip]
@@ -106,6 +108,11 @@ def lib():
 def _check(status):
     if status != OK:
         raise LhcError(status, lib().lhc_last_error().decode())
+
+
+def launch_count() -> int:
+    """Kernel launches this library has issued since it was loaded (graph replays excluded)."""
+    return int(lib().lhc_launch_count())
 
 
 def momenta(n2max: int, cmax: int = -1) -> np.ndarray:

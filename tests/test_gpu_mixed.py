@@ -100,6 +100,37 @@ def test_meson_24c48_sampled_slices(ctx):
     assert report("24c48 spec", CS.block_err(gs, ref, 1)) < CS.MIXED_TOL
 
 
+def test_noise_offset_beyond_int32(ctx):
+    """complex64 solutions whose noise offset (noise x T x V3 x 12 elements) passes 2^31
+    for the last noises: 16^3 x 1536 lattice, 32 noises, two insertion slices near the end
+    of the time extent; only those slices are filled (26 GB on the device).  Both
+    precisions against the oracle on the same complex64-rounded inputs."""
+    from oracle.momenta import momenta
+    from oracle import contractions as OC
+    from paper_1711_02384_gb300 import inputs
+    L, T, n_r, t0 = 16, 1536, 32, 1530
+    V3 = L ** 3
+    assert (n_r - 1) * T * V3 * 12 > 2 ** 31
+    k = momenta(2)
+    S_h = inputs.propagator(3200, L, T, slices=[t0, t0 + 1]).astype(np.complex64)
+    psi_h = inputs.solutions(3201, L, T, n_r, slices=[t0, t0 + 1]).astype(np.complex64)
+    S = torch.empty((T, V3, 12, 12), dtype=torch.complex64, device="cuda")
+    psi = torch.empty((n_r, T, V3, 12), dtype=torch.complex64, device="cuda")
+    try:
+        S[t0:t0 + 2] = dev(S_h)
+        psi[:, t0:t0 + 2] = dev(psi_h)
+        r = np.array([2, 5, 9, 0], dtype=np.int32)
+        gm = ctx.insertion(S, psi, t0, t0 + 1, r, k, prec="mixed").cpu().numpy()
+        gd = ctx.insertion(S, psi, t0, t0 + 1, r, k, prec="fp64").cpu().numpy()
+        ctx.sync()
+    finally:
+        del S, psi
+        torch.cuda.empty_cache()
+    ref = OC.insertion(S_h.astype(complex), psi_h.astype(complex), CS.g5_matrix(), r[:3], k, L)
+    assert report("ins noise offset > 2^31 (mixed)", CS.block_err(gm, ref, 2)) < CS.MIXED_TOL
+    assert report("ins noise offset > 2^31 (fp64)", CS.block_err(gd, ref, 2)) < CS.FP64_TOL
+
+
 @pytest.mark.parametrize("L,n_r,n2max,cmax,r,dtype", [
     (3, 3, 2, -1, (1, 2, 0, 0), np.complex128),   # odd n_r, source off the origin
     (4, 2, 3, 1, (0, 0, 0, 0), np.complex64),     # 27 momenta, complex64 storage
@@ -158,3 +189,24 @@ def test_baryon_32c_full_size_sampled_components(ctx):
         err = np.linalg.norm(got[:, i, col] - ref) / np.linalg.norm(ref)
         worst = max(worst, err)
     assert report("baryon 32^3 sampled components", worst) < CS.MIXED_TOL
+
+
+def test_misaligned_buffers_rejected(ctx):
+    """complex64 views that start 8 bytes into an allocation are refused with LHC_EINVAL
+    before any launch (the kernels copy 16-byte chunks)."""
+    from oracle.momenta import momenta
+    from paper_1711_02384_gb300 import lhc
+    L, T, n_r = 4, 2, 2
+    V3 = L ** 3
+    k = momenta(1)
+    S = torch.zeros(T * V3 * 144 + 1, dtype=torch.complex64, device="cuda")[1:].view(T, V3, 12, 12)
+    psi = torch.zeros((n_r, T, V3, 12), dtype=torch.complex64, device="cuda")
+    with pytest.raises(lhc.LhcError) as e:
+        ctx.insertion(S, psi, 0, 1, (0, 0, 0, 0), k, prec="mixed")
+    assert e.value.status == 1 and "aligned" in str(e.value)
+    eta = torch.zeros(n_r * V3 * 12 + 1, dtype=torch.complex64, device="cuda")[1:].view(n_r, V3, 12)
+    S_ok = torch.zeros((T, V3, 12, 12), dtype=torch.complex64, device="cuda")
+    with pytest.raises(lhc.LhcError) as e:
+        ctx.spectator(S_ok, eta, 0, (0, 0, 0, 0), k, prec="fp64")
+    assert e.value.status == 1
+    ctx.sync()
