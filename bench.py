@@ -257,10 +257,10 @@ def main():
         peak = 1.25     # FP64: 2 DFMA/clk/SM x 152 SMs x ~2.06 GHz (nominal GB300 FP64 rate)
         bound, punit, peak_src = "alu", "TFLOP/s", "nominal FP64 1.25 TFLOP/s"
     achieved = (kwork / (kms / 1e3)) / 1e12 if kms > 0 else None
-    # DRAM bytes per launch: ncu dram__bytes_read+write of the same kernel on the 2-slice
-    # 24^3 profile case (profiles/fused_meson_ins24_2slices.md), 2.28 bytes per unit,
-    # scaled to this workload's units per launch
-    traffic = 2.28 * upstep / kn if (args.prec == "mixed" and kn) else None
+    # DRAM bytes per launch: ncu dram__bytes_read + dram__bytes_write of the same kernel on
+    # the 2-slice 24^3 case (93.5 MB for 4.11e7 units: 2.27 bytes per unit, the compulsory
+    # input), scaled to this workload's units per launch
+    traffic = 2.27 * upstep / kn if (args.prec == "mixed" and kn) else None
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": punit,
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "kernel_ms_per_launch": kms / kn if kn else None, "launches_per_step": kn,
