@@ -43,7 +43,8 @@ constexpr int QCHUNK = 96;               // momenta per CTA (accumulator registe
 // (row groups 144 B apart, the two 8-site k blocks 2304 B apart)
 constexpr int ATILE = 2 * 16 * 144;
 constexpr int ASTAGE = 4 * ATILE;        // Ur hi, Ur lo, Ui hi, Ui lo
-constexpr int NSTAGE = 4;                // A/B ring (freed by the MMA)
+constexpr int NSTAGE = 4;                // A/B ring (freed by the MMA), used as two pairs of stages
+constexpr int NPAIR = NSTAGE / 2;
 constexpr int NIN = 6;                   // input ring (freed by the producers)
 constexpr int NPK = 3;                   // k-steps in flight in the producers (4 warps each)
 // warp roles: 0 phase-tile loader, 1 MMA issue, 2-9 drain, 10-21 producers, 22 input loader
@@ -160,10 +161,12 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
   // TMA destinations want 128-byte alignment: align the stage ring to 1024 explicitly
   char *smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + St::bytes);
-  // full[s]: the phase tile has landed (transaction bytes) and the four producer warps of
-  // the k-step have written the A tiles; empty[s]: the MMAs of the stage have completed
-  uint64_t *full = bars, *empty = bars + NSTAGE, *inFull = bars + 2 * NSTAGE, *inEmpty = bars + 2 * NSTAGE + NIN,
-           *tfull = bars + 2 * NSTAGE + 2 * NIN, *tempty = tfull + 2, *done = tfull + 4;
+  // The A/B stages go in pairs (two k-steps): full[pair] completes when both phase tiles
+  // have landed (transaction bytes) and the eight producer warps of the two k-steps have
+  // written their A tiles; empty[pair] when the pair's twelve MMAs have completed.  One
+  // wait and one commit per two k-steps keeps the MMA thread's gaps short.
+  uint64_t *full = bars, *empty = bars + NPAIR, *inFull = bars + 2 * NPAIR, *inEmpty = bars + 2 * NPAIR + NIN,
+           *tfull = bars + 2 * NPAIR + 2 * NIN, *tempty = tfull + 2, *done = tfull + 4;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
   auto stA = [&](int s) { return smem + s * St::ab; };
   auto stB = [&](int s) { return smem + s * St::ab + St::A; };
@@ -187,8 +190,8 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
   const int bt0 = s0 / 12;                                     // first bt block of the matrix box
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NSTAGE; ++s) {
-      tc::mbar_init(&full[s], 5);   // phase-tile loader + the four producer warps of a k-step
+    for (int s = 0; s < NPAIR; ++s) {
+      tc::mbar_init(&full[s], 10);   // two phase-tile arrivals + the eight producer warps
       tc::mbar_init(&empty[s], 1);
     }
     for (int s = 0; s < NIN; ++s) {
@@ -214,16 +217,16 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
       const char *Bsrc = reinterpret_cast<const char *>(p.B) + ((size_t)qc * p.nkb + kb0) * St::B;
       int issued = 0;
       for (int i = 0; i < nk; ++i) {
-        const int s = i % NSTAGE, u = i / NSTAGE;
-        if (u > 0 && !tc::mbar_wait(&empty[s], (u - 1) & 1, err, 1)) break;
-        tc::mbar_arrive_expect_tx(&full[s], St::B);
-        tc::bulk_g2s(stB(s), Bsrc + (size_t)i * St::B, St::B, &full[s]);
+        const int s = i % NSTAGE, pr = s >> 1, u = i / NSTAGE;
+        if (u > 0 && !tc::mbar_wait(&empty[pr], (u - 1) & 1, err, 1)) break;
+        tc::mbar_arrive_expect_tx(&full[pr], St::B);
+        tc::bulk_g2s(stB(s), Bsrc + (size_t)i * St::B, St::B, &full[pr]);
         issued = i + 1;
       }
-      for (int i = max(0, issued - NSTAGE); i < issued; ++i) {   // nothing may still be landing
-        const int s = i % NSTAGE, u = i / NSTAGE;
+      for (int i = max(0, issued - NSTAGE); i < issued; i += 2) {   // nothing may still be landing
+        const int pr = (i % NSTAGE) >> 1, u = i / NSTAGE;
         long long t0 = clock64();
-        while (!tc::mbar_try_wait(&full[s], u & 1) && clock64() - t0 < tc::kSpinLimit && !*err) {
+        while (!tc::mbar_try_wait(&full[pr], u & 1) && clock64() - t0 < tc::kSpinLimit && !*err) {
         }
       }
     }
@@ -266,8 +269,9 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
       const uint64_t dB0 = tc::smem_desc(tc::smem_u32(stB(0)), 128, 256);
       constexpr uint64_t kStageStep = St::ab >> 4, kATile = ATILE >> 4, kBHalf = (3 * NP * 32) >> 4,
                          kBIm = (NP * 32) >> 4;
-      int i = 0, s = 0;
-      uint32_t ph = 0;   // phase of full[s] for k-step i
+      // k-steps come in pairs (nk is even): stage pair pr holds stages 2 pr and 2 pr + 1
+      int i = 0, pr = 0;
+      uint32_t ph = 0;   // phase of full[pr] for the pair starting at k-step i
       bool ok = true;
       for (int c = 0; c < nchunks && ok; ++c) {
         const int b = c & 1, ub = c >> 1;
@@ -275,22 +279,25 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
         if (ub > 0 && !tc::mbar_wait(&tempty[b], (ub - 1) & 1, err, 2)) break;
         const uint32_t d = tbase + (uint32_t)(b * 2 * NP);
         const int iend = min(nk, (c + 1) * p.kd);
-        for (uint32_t acc0 = 0; i < iend; ++i, acc0 = 1) {
-          if (!tc::mbar_wait(&full[s], ph, err, 3)) {
+        for (uint32_t acc0 = 0; i < iend; i += 2, acc0 = 1) {
+          if (!tc::mbar_wait(&full[pr], ph, err, 3)) {
             ok = false;
             break;
           }
           tc::tc_fence_after();
-          const uint64_t a = dA0 + s * kStageStep, bb = dB0 + s * kStageStep;
-          tc::mma_f16(d, a, bb + kBIm, idesc, acc0);                    // Ur_h [Re|Im]_h
-          tc::mma_f16(d, a, bb + kBHalf + kBIm, idesc, 1u);             // Ur_h [Re|Im]_l
-          tc::mma_f16(d, a + kATile, bb + kBIm, idesc, 1u);             // Ur_l [Re|Im]_h
-          tc::mma_f16(d, a + 2 * kATile, bb, idesc, 1u);                // Ui_h [-Im|Re]_h
-          tc::mma_f16(d, a + 2 * kATile, bb + kBHalf, idesc, 1u);       // Ui_h [-Im|Re]_l
-          tc::mma_f16(d, a + 3 * kATile, bb, idesc, 1u);                // Ui_l [-Im|Re]_h
-          tc::mma_commit(&empty[s]);
-          if (++s == NSTAGE) {
-            s = 0;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint64_t a = dA0 + (2 * pr + h) * kStageStep, bb = dB0 + (2 * pr + h) * kStageStep;
+            tc::mma_f16(d, a, bb + kBIm, idesc, h ? 1u : acc0);           // Ur_h [Re|Im]_h
+            tc::mma_f16(d, a, bb + kBHalf + kBIm, idesc, 1u);             // Ur_h [Re|Im]_l
+            tc::mma_f16(d, a + kATile, bb + kBIm, idesc, 1u);             // Ur_l [Re|Im]_h
+            tc::mma_f16(d, a + 2 * kATile, bb, idesc, 1u);                // Ui_h [-Im|Re]_h
+            tc::mma_f16(d, a + 2 * kATile, bb + kBHalf, idesc, 1u);       // Ui_h [-Im|Re]_l
+            tc::mma_f16(d, a + 3 * kATile, bb, idesc, 1u);                // Ui_l [-Im|Re]_h
+          }
+          tc::mma_commit(&empty[pr]);
+          if (++pr == NPAIR) {
+            pr = 0;
             ph ^= 1u;
           }
         }
@@ -435,11 +442,11 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
       // the input stage is read: hand it back to the input loader
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&inEmpty[si]);
-      const int s = kstep % NSTAGE, u = kstep / NSTAGE;
+      const int s = kstep % NSTAGE, pr = s >> 1, u = kstep / NSTAGE;
       if (u > 0) {
         // the MMA must be done with this A stage (from NSTAGE k-steps ago)
         int ok = 0;
-        if (lane == 0) ok = tc::mbar_wait(&empty[s], (u - 1) & 1, err, 8) ? 1 : 0;
+        if (lane == 0) ok = tc::mbar_wait(&empty[pr], (u - 1) & 1, err, 8) ? 1 : 0;
         if (!__shfl_sync(0xffffffffu, ok, 0)) break;
       }
       char *a_st = stA(s);
@@ -460,7 +467,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
       }
       tc::fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&full[s]);
+      if (lane == 0) tc::mbar_arrive(&full[pr]);
     }
   }
   tc::tc_fence_before();
@@ -500,7 +507,7 @@ __global__ void reduce_f64(const float2 *__restrict__ part, int nsplit, size_t p
 template <int MODE, int NP>
 constexpr size_t fused_smem() {
   // rings + barriers + tensor-memory slot + up to 1023 B to align the rings
-  return (size_t)Stage<MODE, NP>::bytes + (2 * NSTAGE + 2 * NIN + 5) * 8 + 16 + 1024;
+  return (size_t)Stage<MODE, NP>::bytes + (2 * NPAIR + 2 * NIN + 5) * 8 + 16 + 1024;
 }
 
 template <int MODE, int NP>
@@ -655,7 +662,7 @@ size_t mixed_call_bytes(Part part, int dtype, int V3, int n_r, int nt, int nq) {
   const bool baryon = part == PART_SPEC_BARYON;
   const size_t ncols = (size_t)n_r * (baryon ? kBarCols : 192);
   const size_t ntl = (size_t)std::min(nt, kMaxSlices);
-  const size_t nkb = (V3 + KSTEP - 1) / KSTEP, nqc = (nq + QCHUNK - 1) / QCHUNK;
+  const size_t nkb = (V3 + 2 * KSTEP - 1) / (2 * KSTEP) * 2, nqc = (nq + QCHUNK - 1) / QCHUNK;
   size_t b = ntl * 8 * nq * ncols * sizeof(float2);
   if (dtype == LHC_C128) b += ntl * V3 * 144 * 8 + (baryon ? (size_t)V3 * 144 * 8 : 0) + (size_t)n_r * ntl * V3 * 12 * 8;
   if (baryon) b += (size_t)V3 * 2304 * 8;
@@ -727,7 +734,9 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
   const int V3 = j0.V3, n_r = j0.n_r;
   const int ncols = n_r * (baryon ? kBarCols : 192);
   const int nct = (baryon ? 48 : 3) * ((n_r + 1) / 2);
-  const int nkb = (V3 + KSTEP - 1) / KSTEP;
+  // site blocks, rounded up to an even number: the kernel consumes k-steps in pairs (the
+  // pad block's phases are zero and its sites lie past the slice, which TMA reads as zero)
+  const int nkb = ((V3 + 2 * KSTEP - 1) / (2 * KSTEP)) * 2;
   const int nqc = (nq + QCHUNK - 1) / QCHUNK;
   const int Np = ((std::min(nq, QCHUNK) + 15) / 16) * 16;
   const __half *phase = nullptr;
@@ -735,7 +744,7 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
 
   int nsplit = choose_nsplit(nct * nt * nqc, (nkb + 1) / 2, ctx->num_sms);
   int kd = 4;   // k-steps accumulated in tensor memory between drains (truncating accumulation)
-  if (const char *e = getenv("LHC_KD")) kd = std::max(1, atoi(e));
+  if (const char *e = getenv("LHC_KD")) kd = std::max(2, (atoi(e) + 1) / 2 * 2);   // even: k-steps come in pairs
   if (const char *e = getenv("LHC_NSPLIT")) nsplit = std::max(1, std::min((nkb + 1) / 2, atoi(e)));
 
   const int ntl = std::min(nt, kMaxSlices);   // slices per launch

@@ -210,3 +210,39 @@ def test_misaligned_buffers_rejected(ctx):
         ctx.spectator(S_ok, eta, 0, (0, 0, 0, 0), k, prec="fp64")
     assert e.value.status == 1
     ctx.sync()
+
+
+def test_complex128_staging_is_the_ieee_conversion(ctx):
+    """complex128 inputs are staged to complex64 (round to nearest even); the
+    mixed results must equal, bit for bit, those from the same inputs converted to
+    complex64 by torch (CUDA's IEEE conversion).  Magnitudes span 2^-12 .. 2^4 and a
+    quarter of the values sit exactly on a rounding tie."""
+    from oracle.momenta import momenta
+    g = torch.Generator(device="cuda")
+    g.manual_seed(77)
+    L, T, n_r = 6, 4, 3
+    V3 = L ** 3
+
+    def rough(shape):
+        x = torch.randn(shape + (2,), dtype=torch.float64, device="cuda", generator=g)
+        x = x * torch.exp2(torch.randint(-12, 5, shape + (2,), device="cuda", generator=g).double())
+        bits = x.view(torch.int64)
+        tie = torch.rand(shape + (2,), device="cuda", generator=g) < 0.25
+        bits = torch.where(tie, (bits & ~0x1FFFFFFF) | 0x10000000, bits)
+        return torch.view_as_complex(bits.view(torch.float64).contiguous())
+
+    S, SB = rough((T, V3, 12, 12)), rough((T, V3, 12, 12))
+    psi, eta = rough((n_r, T, V3, 12)), rough((n_r, V3, 12))
+    k = momenta(2)
+    r = (1, 0, 2, 0)
+    c64 = lambda t: t.to(torch.complex64)
+    a = ctx.insertion(S, psi, 0, 3, r, k, prec="mixed")
+    b = ctx.insertion(c64(S), c64(psi), 0, 3, r, k, prec="mixed")
+    assert torch.equal(a, b)
+    a = ctx.spectator(S, eta, 2, r, k, prec="mixed")
+    b = ctx.spectator(c64(S), c64(eta), 2, r, k, prec="mixed")
+    assert torch.equal(a, b)
+    a = ctx.spectator(S, eta, 1, r, k, prec="mixed", GB=SB)
+    b = ctx.spectator(c64(S), c64(eta), 1, r, k, prec="mixed", GB=c64(SB))
+    assert torch.equal(a, b)
+    ctx.sync()
