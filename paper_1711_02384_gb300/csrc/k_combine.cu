@@ -7,8 +7,10 @@
 //   baryon  Xs[g][p][i,b,c]  = sum Wsnk[a1p][a2p][bp] Wsrc[a1][a2][b] B[p][i][a1p,a1,a2p,a2,bp,c]
 //           Xi[t][g][q][i,b,c] = sum_{at,bt} Gins[at][bt] I[t][q][i][at,bt,b,c]
 // Precision: LHC_FP64 does everything in double.  LHC_MIXED does the Gamma contractions and
-// the 12-term spin-colour sum of each noise in FP32 and the sum over noises (the noise
-// average of Eq. 5) in FP64.
+// the 12-term spin-colour sum of each noise in FP32; the sum over noises (the noise
+// average of Eq. 5) is exact: each noise's term is added with Knuth's TwoSum into an
+// unevaluated FP32 pair hi + lo, rounded once to FP64 (no less accurate than FP64
+// accumulation, and it keeps GB300's slow FP64 pipe out of the inner loop).
 #include <type_traits>
 
 #include "lhc_internal.h"
@@ -42,6 +44,13 @@ template <typename R>
 __device__ __forceinline__ void stage(cplx<R> *dst, const double2 *src, int n) {
   for (int e = threadIdx.x; e < n; e += blockDim.x) dst[e] = ld<R>(src + e);
 }
+// The per-noise blocks of 192 values are staged 193 apart: consecutive tasks belong to
+// different noises, and a stride of 192 complex numbers would put them in one bank.
+constexpr int SROW = 193;
+template <typename R>
+__device__ __forceinline__ void stage_rows(cplx<R> *dst, const double2 *src, int n_r) {
+  for (int e = threadIdx.x; e < n_r * 192; e += blockDim.x) dst[(e / 192) * SROW + e % 192] = ld<R>(src + e);
+}
 
 // CTA per (t, q): Xi[t][g][q][i,al,a] = sum_b Gsrc[g][b][al] sum_{at,bt} Gins[g][at][bt] I[t][q][i][at,bt,b,a]
 template <typename R>
@@ -49,15 +58,15 @@ __global__ void comb_ins_meson(const double2 *__restrict__ I, int nq, int n_r, c
                                const double2 *__restrict__ Gsrc, int ng, cplx<R> *__restrict__ Xi) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   cplx<R> *sI = reinterpret_cast<cplx<R> *>(sm_raw);
-  cplx<R> *sGi = sI + n_r * 192, *sGc = sGi + ng * 16;
+  cplx<R> *sGi = sI + n_r * SROW, *sGc = sGi + ng * 16;
   const int tq = blockIdx.x, t = tq / nq, q = tq % nq;
-  stage(sI, I + (size_t)tq * n_r * 192, n_r * 192);
+  stage_rows(sI, I + (size_t)tq * n_r * 192, n_r);
   stage(sGi, Gins, ng * 16);
   stage(sGc, Gsrc, ng * 16);
   __syncthreads();
   for (int task = threadIdx.x; task < ng * n_r * 3; task += blockDim.x) {
     const int a = task % 3, i = (task / 3) % n_r, g = task / (3 * n_r);
-    const cplx<R> *v = sI + i * 192, *Gi = sGi + g * 16, *Gc = sGc + g * 16;
+    const cplx<R> *v = sI + i * SROW, *Gi = sGi + g * 16, *Gc = sGc + g * 16;
     cplx<R> T[4];
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
@@ -84,14 +93,14 @@ __global__ void comb_ins_baryon(const double2 *__restrict__ I, int nq, int n_r, 
                                 int ng, cplx<R> *__restrict__ Xi) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   cplx<R> *sI = reinterpret_cast<cplx<R> *>(sm_raw);
-  cplx<R> *sGi = sI + n_r * 192;
+  cplx<R> *sGi = sI + n_r * SROW;
   const int tq = blockIdx.x, t = tq / nq, q = tq % nq;
-  stage(sI, I + (size_t)tq * n_r * 192, n_r * 192);
+  stage_rows(sI, I + (size_t)tq * n_r * 192, n_r);
   stage(sGi, Gins, ng * 16);
   __syncthreads();
   for (int task = threadIdx.x; task < ng * n_r * 3; task += blockDim.x) {
     const int c = task % 3, i = (task / 3) % n_r, g = task / (3 * n_r);
-    const cplx<R> *v = sI + i * 192, *Gi = sGi + g * 16;
+    const cplx<R> *v = sI + i * SROW, *Gi = sGi + g * 16;
     cplx<R> *o = Xi + (((size_t)t * ng + g) * nq + q) * 12 * n_r + i * 12 + c;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
@@ -111,14 +120,14 @@ __global__ void comb_spec_meson(const double2 *__restrict__ S, int np, int n_r, 
                                 int ng, cplx<R> *__restrict__ Xs) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   cplx<R> *sS = reinterpret_cast<cplx<R> *>(sm_raw);
-  cplx<R> *sG = sS + n_r * 192;
+  cplx<R> *sG = sS + n_r * SROW;
   const int p = blockIdx.x;
-  stage(sS, S + (size_t)p * n_r * 192, n_r * 192);
+  stage_rows(sS, S + (size_t)p * n_r * 192, n_r);
   stage(sG, Gsnk, ng * 16);
   __syncthreads();
   for (int task = threadIdx.x; task < ng * n_r * 3; task += blockDim.x) {
     const int a = task % 3, i = (task / 3) % n_r, g = task / (3 * n_r);
-    const cplx<R> *s = sS + i * 192, *G = sG + g * 16;
+    const cplx<R> *s = sS + i * SROW, *G = sG + g * 16;
     cplx<R> *o = Xs + ((size_t)g * np + p) * 12 * n_r + i * 12 + a;
 #pragma unroll
     for (int al = 0; al < 4; ++al) {
@@ -163,9 +172,38 @@ __global__ void comb_spec_baryon(const double2 *__restrict__ B, int np, int n_r,
   for (int b = 0; b < 4; ++b) o[b * 3] = out[b];
 }
 
+// Sum over noises of the per-noise terms: in double for R = double; for R = float an
+// unevaluated pair hi + lo per component, each term added with Knuth's TwoSum (the pair
+// holds the sum exactly up to the rounding of lo), rounded once to double at the end.
+template <typename R>
+struct NoiseSum {
+  double x = 0.0, y = 0.0;
+  __device__ __forceinline__ void add(cplx<R> v) {
+    x += (double)v.x;
+    y += (double)v.y;
+  }
+  __device__ __forceinline__ double2 get(double scale) const { return make_double2(x * scale, y * scale); }
+};
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float v) {
+  const float s = hi + v, bp = s - hi;
+  lo += (hi - (s - bp)) + (v - bp);
+  hi = s;
+}
+template <>
+struct NoiseSum<float> {
+  float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f;
+  __device__ __forceinline__ void add(cplx<float> v) {
+    two_sum_acc(hx, lx, v.x);
+    two_sum_acc(hy, ly, v.y);
+  }
+  __device__ __forceinline__ double2 get(double scale) const {
+    return make_double2(((double)hx + (double)lx) * scale, ((double)hy + (double)ly) * scale);
+  }
+};
+
 // out[t][g][p][q] = (1/N) sum_i sum_{j<12} Xs[g][p][12i+j] Xi[t][g][q][12i+j]: a tiled complex
 // GEMM whose per-noise 12-term sums run in R (float or double) and whose sum over
-// noises runs in double.
+// noises is the NoiseSum above.
 constexpr int CTILE = 32;
 template <typename R>
 __global__ void __launch_bounds__(256) comb_gemm(const cplx<R> *__restrict__ Xs, const cplx<R> *__restrict__ Xi,
@@ -180,11 +218,7 @@ __global__ void __launch_bounds__(256) comb_gemm(const cplx<R> *__restrict__ Xs,
   const size_t K = (size_t)12 * n_r;
   const cplx<R> *A = Xs + ((size_t)g * np) * K;
   const cplx<R> *B = Xi + ((size_t)tg * nq) * K;
-  double2 acc[2][2];
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 2; ++b) acc[a][b] = make_double2(0.0, 0.0);
+  NoiseSum<R> acc[2][2];
   for (int i = 0; i < n_r; ++i) {
     for (int e = threadIdx.x; e < CTILE * 12; e += 256) {
       int r = e / 12, k = e % 12;
@@ -199,8 +233,7 @@ __global__ void __launch_bounds__(256) comb_gemm(const cplx<R> *__restrict__ Xs,
         cplx<R> pa{0, 0};
 #pragma unroll
         for (int k = 0; k < 12; ++k) cfma(pa, As[ty + 16 * a][k], Bs[tx + 16 * b][k]);
-        acc[a][b].x += (double)pa.x;
-        acc[a][b].y += (double)pa.y;
+        acc[a][b].add(pa);
       }
     __syncthreads();
   }
@@ -210,7 +243,7 @@ __global__ void __launch_bounds__(256) comb_gemm(const cplx<R> *__restrict__ Xs,
     for (int b = 0; b < 2; ++b) {
       int p = p0 + ty + 16 * a, q = q0 + tx + 16 * b;
       if (p < np && q < nq)
-        out[((size_t)tg * np + p) * nq + q] = make_double2(acc[a][b].x * inv_n, acc[a][b].y * inv_n);
+        out[((size_t)tg * np + p) * nq + q] = acc[a][b].get(inv_n);
     }
 }
 
@@ -222,7 +255,7 @@ int launch_combine(int kind, const double2 *spec, int np, const double2 *ins, in
                    double2 *out, cudaStream_t st) {
   cplx<R> *Xs = static_cast<cplx<R> *>(scratch);
   cplx<R> *Xi = Xs + (size_t)ng * np * 12 * n_r;
-  const size_t smem = ((size_t)n_r * 192 + 2 * ng * 16) * sizeof(cplx<R>);
+  const size_t smem = ((size_t)n_r * SROW + 2 * ng * 16) * sizeof(cplx<R>);
   if (smem > 200 * 1024) {
     set_error("combine block of %d noises and %d Gamma structures does not fit shared memory", n_r, ng);
     return LHC_EINVAL;

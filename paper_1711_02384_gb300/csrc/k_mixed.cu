@@ -2,11 +2,23 @@
 // fused kernel per call that performs the site contraction in FP32 and the momentum
 // projection on tcgen05 tensor cores, plus an FP64 cross-block reduction.
 //
-// GEMM view: out[q][col] = sum_x P[q][x] U[x][col], x over the sites of a timeslice.
-// A CTA owns one tile of 128 columns (2 noises x 4 "vector" spins x 16 "matrix"
-// indices s), one chunk of <= 96 momenta and one range of sites:
+// GEMM view: out[q][col] = sum_x P[q][x] U[x][col], x over the sites of a timeslice,
+// P[q][x] = exp(i sign phi_q(x)), phi_q(x) = 2 pi k_q.(x - r) / L.
 //
-//   warp 0      bulk-copies the phase tiles (FP16 hi/lo of [-Im | Re | Im], K-major) into
+// Momentum pairs.  phi_{-k} = -phi_k, so the phases of k and -k are complex conjugates.
+// The momenta are grouped into representatives k_rho (one per pair {k, -k}, or per
+// momentum whose partner is not requested), and the tensor cores compute only the two
+// real projections
+//   C_rho = sum_x cos(phi_rho(x)) U(x),   S_rho = sum_x sin(phi_rho(x)) U(x)   (U complex),
+// from which every requested momentum follows as out[q] = C_rho + i sigma_q S_rho with
+// sigma_q = sign * (+1 if k_q = k_rho, -1 if k_q = -k_rho).  A symmetric momentum set
+// (all |k|^2 <= n^2) therefore costs half the tensor-core work of the direct complex
+// projection; an asymmetric one costs the same.
+//
+// A CTA owns one tile of 128 columns (2 noises x 4 "vector" spins x 16 "matrix"
+// indices s), one chunk of NH <= 48 representatives and one range of sites:
+//
+//   warp 0      bulk-copies the phase tiles (FP16 hi/lo of [cos | sin], K-major) into
 //               the A/B ring, whose stages the MMA frees
 //   warp 22     loads the contraction inputs of each k-step with TMA tensor copies (the
 //               propagator or diquark box and the two noises' vector box) into the input
@@ -17,13 +29,15 @@
 //               inputs in FP32, split each value into fp16 hi + lo and write the four A
 //               tiles (Ur hi/lo, Ui hi/lo), MN-major
 //
-// Per k-step (16 sites) the accumulator D (128 x 2Np, FP32, tensor memory) receives
-//   Ur_h [Re|Im]_h + Ur_h [Re|Im]_l + Ur_l [Re|Im]_h + Ui_h [-Im|Re]_h + Ui_h [-Im|Re]_l
-//   + Ui_l [-Im|Re]_h,
-// so D[:, :Np] = Re(P U) and D[:, Np:] = Im(P U) with the lo*lo term dropped.  Tensor
-// memory accumulation truncates, so D is double-buffered and drained every KD k-steps;
-// each CTA writes FP32 partial sums that reduce_f64 adds exactly and rounds to FP64.
+// Per k-step (16 sites) the accumulator D (128 x 4NH, FP32, tensor memory) receives
+//   D[:, 0:2NH]   += Ur_h [cos|sin]_h + Ur_h [cos|sin]_l + Ur_l [cos|sin]_h
+//   D[:, 2NH:4NH] += Ui_h [cos|sin]_h + Ui_h [cos|sin]_l + Ui_l [cos|sin]_h
+// (the lo*lo term dropped), i.e. Re C, Re S, Im C, Im S.  Tensor memory accumulation
+// truncates, so D is double-buffered and drained every KD k-steps; each CTA writes FP32
+// partial sums of (Re C, Re S, Im C, Im S), and reduce_f64 adds the partials of all CTAs
+// exactly, rounds to FP64 and forms out[q] = C + i sigma_q S.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdlib>
 
@@ -38,7 +52,7 @@ namespace {
 
 constexpr int MT = 128;                  // GEMM M tile: output columns per CTA
 constexpr int KSTEP = 16;                // sites per MMA k-step
-constexpr int QCHUNK = 96;               // momenta per CTA (accumulator registers bound this)
+constexpr int RCHUNK = 48;               // momentum representatives per CTA (tensor memory bounds this)
 // one 128 x 16 fp16 operand tile, MN-major with 16 B of padding per 8-row group
 // (row groups 144 B apart, the two 8-site k blocks 2304 B apart)
 constexpr int ATILE = 2 * 16 * 144;
@@ -68,12 +82,14 @@ struct SlicePtrs {
 
 
 // ------------------------------------------------------------ phase table (FP16 split)
-// layout [qc][kb][hl][3*Np rows: -Im | Re | Im][16 sites], each (qc,kb,hl) block K-major
-__global__ void phase_split_kernel(__half *out, const int *k, int nq, int Np, int nqc, int nkb, int L,
-                                   int rx, int ry, int rz, int sign, const double2 *roots) {
+// layout [rc][kb][hl][2 NH rows: cos | sin][16 sites], each (rc, kb, hl) block K-major;
+// row n < NH holds cos(phi_rho), row NH + n sin(phi_rho) for rho = rc NH + n, with
+// phi_rho(x) = 2 pi ((k_rho.(x - r)) mod L) / L taken from the L-entry root table.
+__global__ void phase_cs_kernel(__half *out, const int *krep, int nrep, int NH, int nrc, int nkb, int L, int rx,
+                                int ry, int rz, const double2 *roots) {
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int rows = 3 * Np;
-  size_t total = (size_t)nqc * nkb * 2 * rows * KSTEP;
+  const int rows = 2 * NH;
+  size_t total = (size_t)nrc * nkb * 2 * rows * KSTEP;
   if (idx >= total) return;
   int kk = (int)(idx % KSTEP);
   size_t rest = idx / KSTEP;
@@ -82,25 +98,22 @@ __global__ void phase_split_kernel(__half *out, const int *k, int nq, int Np, in
   int hl = (int)(rest % 2);
   rest /= 2;
   int kb = (int)(rest % nkb);
-  int qc = (int)(rest / nkb);
-  int g = n / Np, qi = n % Np;
-  int q = qc * QCHUNK + qi;
-  int qend = min(nq, (qc + 1) * QCHUNK);
+  int rc = (int)(rest / nkb);
+  int g = n / NH, rho = rc * NH + n % NH;
   int V3 = L * L * L;
   int x = kb * KSTEP + kk;
   double v = 0.0;
-  if (q < qend && x < V3) {
+  if (rho < nrep && x < V3) {
     int cx = x % L, cy = (x / L) % L, cz = x / (L * L);
-    long long m = (long long)k[3 * q] * (cx - rx) + (long long)k[3 * q + 1] * (cy - ry) +
-                  (long long)k[3 * q + 2] * (cz - rz);
+    long long m = (long long)krep[3 * rho] * (cx - rx) + (long long)krep[3 * rho + 1] * (cy - ry) +
+                  (long long)krep[3 * rho + 2] * (cz - rz);
     m %= L;
     if (m < 0) m += L;
-    double re = roots[m].x, im = sign * roots[m].y;
-    v = g == 0 ? -im : (g == 1 ? re : im);
+    v = g == 0 ? roots[m].x : roots[m].y;
   }
   __half hi = __double2half(v);
   __half lo = __double2half(v - (double)__half2float(hi));
-  size_t block = ((size_t)qc * nkb + kb) * 2 + hl;
+  size_t block = ((size_t)rc * nkb + kb) * 2 + hl;
   char *base = reinterpret_cast<char *>(out) + block * (size_t)rows * 32;
   *reinterpret_cast<__half *>(base + kmajor_off(n, kk)) = hl ? lo : hi;
 }
@@ -121,9 +134,9 @@ struct FusedParams {
   CUtensorMap tmV;
   int tM[kMaxSlices], tV[kMaxSlices];   // per slice: time coordinate in tmM, tmV
   const __half *B;                      // phase table
-  float2 *partial;                      // [nt][nsplit][nq][ncols]
+  float4 *partial;                      // [nt][nsplit][nrc * NH][ncols]: (Re C, Re S, Im C, Im S)
   int *err;
-  int n_r, V3, nct, nkb, nqc, nq, ncols, nsplit, kd, g5mask;
+  int n_r, V3, nct, nkb, nrc, nrep, ncols, nsplit, kd, g5mask;
 };
 
 // fp16 hi/lo split of two floats, packed as half2 pairs
@@ -136,12 +149,12 @@ __device__ __forceinline__ void split2(float v0, float v1, uint32_t &hi, uint32_
 }
 
 // Shared memory: NSTAGE stages of the A tiles (Ur hi, Ur lo, Ui hi, Ui lo) and the phase
-// tile B, then NIN stages of the matrix box M and the vector box V.  Every region size is
-// a multiple of 1024 bytes.
-template <int MODE, int NP>
+// tile B (hi and lo of 2 NH rows x 16 sites), then NIN stages of the matrix box M and the
+// vector box V.  Every region size is a multiple of 1024 bytes.
+template <int MODE, int NH>
 struct Stage {
   static constexpr int A = ASTAGE;
-  static constexpr int B = 2 * 3 * NP * 32;
+  static constexpr int B = 2 * 2 * NH * 32;
   static constexpr int M = MODE == 2 ? 16 * 48 * 8 : 16 * 72 * 8;
   static constexpr int V = 2 * 16 * 12 * 8;
   static constexpr int ab = A + B;
@@ -149,10 +162,13 @@ struct Stage {
   static constexpr int bytes = NSTAGE * ab + NIN * in;
 };
 
-template <typename CT, int MODE, int NP>
+template <typename CT, int MODE, int NH>
 __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant__ FusedParams p) {
-  static_assert(NP % 16 == 0 && NP <= QCHUNK, "momentum chunk");
-  using St = Stage<MODE, NP>;
+  static_assert(NH % 8 == 0 && NH <= RCHUNK, "representative chunk");
+  using St = Stage<MODE, NH>;
+  // NP accumulator columns per half: [cos | sin] x NH representatives; half 0 takes the
+  // products with Ur, half 1 those with Ui.
+  constexpr int NP = 2 * NH;
   // tensor memory: D buffers [0, 2NP) and [2NP, 4NP); the rest holds NT columns of each
   // half's running sum, the remaining NR = NP - NT columns stay in registers
   constexpr int NT = ((kTmemCols - 4 * NP) / 2 / 16 * 16) < NP ? ((kTmemCols - 4 * NP) / 2 / 16 * 16) : NP;
@@ -168,6 +184,10 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
   uint64_t *full = bars, *empty = bars + NPAIR, *inFull = bars + 2 * NPAIR, *inEmpty = bars + 2 * NPAIR + NIN,
            *tfull = bars + 2 * NPAIR + 2 * NIN, *tempty = tfull + 2, *done = tfull + 4;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+  // Verdicts of waits that one leader thread performs for a group of warps, which block on
+  // a named barrier meanwhile: [0, 2) drain (by chunk parity), then per producer group
+  // (k-step offset) two slots for the input wait and two for the A-stage wait.
+  volatile int *verdict = reinterpret_cast<volatile int *>(tmem_slot + 1);
   auto stA = [&](int s) { return smem + s * St::ab; };
   auto stB = [&](int s) { return smem + s * St::ab + St::A; };
   auto stM = [&](int s) { return smem + NSTAGE * St::ab + s * St::in; };
@@ -175,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ct = blockIdx.x, split = blockIdx.y;
-  const int j = blockIdx.z / p.nqc, qc = blockIdx.z % p.nqc;
+  const int j = blockIdx.z / p.nrc, rc = blockIdx.z % p.nrc;
   // site range in k-steps; splits start on even k-steps so producer iterations align
   const int npair = (p.nkb + 1) / 2;
   const int kb0 = 2 * (int)((long long)npair * split / p.nsplit);
@@ -214,7 +234,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
   if (warp == 0) {
     // ---------------------------------------------------- phase tiles (A/B ring)
     if (lane == 0 && nk > 0) {
-      const char *Bsrc = reinterpret_cast<const char *>(p.B) + ((size_t)qc * p.nkb + kb0) * St::B;
+      const char *Bsrc = reinterpret_cast<const char *>(p.B) + ((size_t)rc * p.nkb + kb0) * St::B;
       int issued = 0;
       for (int i = 0; i < nk; ++i) {
         const int s = i % NSTAGE, pr = s >> 1, u = i / NSTAGE;
@@ -260,15 +280,14 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
       // A: MN-major (row m = s*8 + noise*4 + spin), core matrices 8 k x 16 B: the 16 row
       // groups s lie 144 B apart (SBO; the 16 B of padding per group keep the producers'
       // stores free of bank conflicts), the two 8-site k blocks 2304 B apart (LBO)
-      constexpr uint32_t idesc = tc::idesc_f16(MT, 2 * NP) | (1u << 15);
+      constexpr uint32_t idesc = tc::idesc_f16(MT, NP) | (1u << 15);
       // Everything between two k-steps' MMAs is on the tensor pipe's critical path (it
       // queues few MMAs), so the loop does no division and builds no descriptor: the
       // descriptors of stage 0 are offset by immediates (the start-address field is
       // bytes / 16 and cannot carry out for shared-memory addresses).
       const uint64_t dA0 = tc::smem_desc(tc::smem_u32(stA(0)), 2304, 144);
       const uint64_t dB0 = tc::smem_desc(tc::smem_u32(stB(0)), 128, 256);
-      constexpr uint64_t kStageStep = St::ab >> 4, kATile = ATILE >> 4, kBHalf = (3 * NP * 32) >> 4,
-                         kBIm = (NP * 32) >> 4;
+      constexpr uint64_t kStageStep = St::ab >> 4, kATile = ATILE >> 4, kBHalf = (NP * 32) >> 4;
       // k-steps come in pairs (nk is even): stage pair pr holds stages 2 pr and 2 pr + 1
       int i = 0, pr = 0;
       uint32_t ph = 0;   // phase of full[pr] for the pair starting at k-step i
@@ -288,12 +307,13 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const uint64_t a = dA0 + (2 * pr + h) * kStageStep, bb = dB0 + (2 * pr + h) * kStageStep;
-            tc::mma_f16(d, a, bb + kBIm, idesc, h ? 1u : acc0);           // Ur_h [Re|Im]_h
-            tc::mma_f16(d, a, bb + kBHalf + kBIm, idesc, 1u);             // Ur_h [Re|Im]_l
-            tc::mma_f16(d, a + kATile, bb + kBIm, idesc, 1u);             // Ur_l [Re|Im]_h
-            tc::mma_f16(d, a + 2 * kATile, bb, idesc, 1u);                // Ui_h [-Im|Re]_h
-            tc::mma_f16(d, a + 2 * kATile, bb + kBHalf, idesc, 1u);       // Ui_h [-Im|Re]_l
-            tc::mma_f16(d, a + 3 * kATile, bb, idesc, 1u);                // Ui_l [-Im|Re]_h
+            const uint32_t acc = h ? 1u : acc0;
+            tc::mma_f16(d, a, bb, idesc, acc);                            // Ur_h [cos|sin]_h
+            tc::mma_f16(d, a, bb + kBHalf, idesc, 1u);                    // Ur_h [cos|sin]_l
+            tc::mma_f16(d, a + kATile, bb, idesc, 1u);                    // Ur_l [cos|sin]_h
+            tc::mma_f16(d + NP, a + 2 * kATile, bb, idesc, acc);          // Ui_h [cos|sin]_h
+            tc::mma_f16(d + NP, a + 2 * kATile, bb + kBHalf, idesc, 1u);  // Ui_h [cos|sin]_l
+            tc::mma_f16(d + NP, a + 3 * kATile, bb, idesc, 1u);           // Ui_l [cos|sin]_h
           }
           tc::mma_commit(&empty[pr]);
           if (++pr == NPAIR) {
@@ -319,12 +339,12 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
     for (int n = 0; n < NR; ++n) acc[n] = 0.f;
     for (int c = 0; c < nchunks; ++c) {
       int b = c & 1, ub = c >> 1;
-      // one lane waits, the warp follows its verdict: the tensor-memory loads below are
-      // warp-collective and must never see a split warp
-      int ok = 0;
-      if (lane == 0) ok = tc::mbar_wait(&tfull[b], ub & 1, err, 5) ? 1 : 0;
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) break;
+      // one thread waits, the eight drain warps block on named barrier 1 and follow its
+      // verdict together (the tensor-memory loads below are warp-collective and must
+      // never see a split warp; every drain warp reaches the barrier in every chunk)
+      if (warp == kDrainWarp0 && lane == 0) verdict[b] = tc::mbar_wait(&tfull[b], ub & 1, err, 5) ? 1 : 0;
+      tc::named_bar_sync(1, 256);
+      if (!verdict[b]) break;
       tc::tc_fence_after();
       const uint32_t t = lane_base + (uint32_t)(b * 2 * NP + h * NP);
 #pragma unroll
@@ -361,24 +381,31 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
     const int smask = MODE != 1 ? (p.g5mask >> v)
                                 : ((p.g5mask >> v) ^ (p.g5mask >> (sidx / 12)) ^ (p.g5mask >> ((sidx % 12) / 3)));
     const float sgn = (smask & 1) ? -1.f : 1.f;
-    const int qend = min(p.nq - qc * QCHUNK, NP);
+    const int rend = min(p.nrep - rc * NH, NH);
     // tcgen05.ld is warp-collective: every lane executes it, only the stores are per lane
     const int failed = __shfl_sync(0xffffffffu, *err, 0);
     if (!failed && nk > 0) {
       const bool mine = noise < p.n_r;
-      float *out = reinterpret_cast<float *>(p.partial + ((size_t)j * p.nsplit + split) * p.nq * p.ncols);
-#pragma unroll
+      // column n of this half is (cos, sin) = (n / NH) of representative rc NH + n % NH;
+      // it goes to component 2 h + n / NH of the (Re C, Re S, Im C, Im S) quadruple
+      float *out = reinterpret_cast<float *>(p.partial + ((size_t)j * p.nsplit + split) * p.nrc * NH * p.ncols) +
+                   (size_t)rc * NH * p.ncols * 4 + (size_t)col * 4 + 2 * h;
+#pragma unroll 1
       for (int n0 = 0; n0 < NT; n0 += 16) {
         float r[16];
         tc::tmem_ld16(rsum + n0, r);
         tc::tmem_wait_ld();
 #pragma unroll
-        for (int e = 0; e < 16; ++e)
-          if (mine && n0 + e < qend) out[((size_t)(qc * QCHUNK + n0 + e) * p.ncols + col) * 2 + h] = sgn * r[e];
+        for (int e = 0; e < 16; ++e) {
+          const int n = n0 + e, rho = n % NH;
+          if (mine && rho < rend) out[(size_t)rho * p.ncols * 4 + n / NH] = sgn * r[e];
+        }
       }
 #pragma unroll
-      for (int n = 0; n < NR; ++n)
-        if (mine && NT + n < qend) out[((size_t)(qc * QCHUNK + NT + n) * p.ncols + col) * 2 + h] = sgn * acc[n];
+      for (int e = 0; e < NR; ++e) {
+        const int n = NT + e, rho = n % NH;
+        if (mine && rho < rend) out[(size_t)rho * p.ncols * 4 + n / NH] = sgn * acc[e];
+      }
     }
   } else {
     // ---------------------------------------------------- producers
@@ -402,12 +429,13 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
       const int kstep = NPK * it + kofs;
       if (kstep >= nk) break;
       const int si = kstep % NIN, ui = kstep / NIN;
-      {
-        // a wait that gives up (a loader stopped, or the limit ran out) ends the loop
-        int ok = 0;
-        if (lane == 0) ok = tc::mbar_wait(&inFull[si], ui & 1, err, 6) ? 1 : 0;
-        if (!__shfl_sync(0xffffffffu, ok, 0)) break;
-      }
+      // The first warp of the group waits for each barrier; the four warps block on the
+      // group's named barrier and follow its verdict together, so a wait that gives up (a
+      // loader stopped, or the limit ran out) ends the loop of all four at once.
+      volatile int *vin = verdict + 2 + 4 * kofs, *vempty = vin + 2;
+      if (wq == 0 && lane == 0) vin[it & 1] = tc::mbar_wait(&inFull[si], ui & 1, err, 6) ? 1 : 0;
+      tc::named_bar_sync(2 + kofs, 128);
+      if (!vin[it & 1]) break;
       const float2 *Ms = reinterpret_cast<const float2 *>(stM(si));
       const float2 *Vs = reinterpret_cast<const float2 *>(stV(si)) + x * 12;
       float2 acc[2][8];
@@ -445,9 +473,9 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
       const int s = kstep % NSTAGE, pr = s >> 1, u = kstep / NSTAGE;
       if (u > 0) {
         // the MMA must be done with this A stage (from NSTAGE k-steps ago)
-        int ok = 0;
-        if (lane == 0) ok = tc::mbar_wait(&empty[pr], (u - 1) & 1, err, 8) ? 1 : 0;
-        if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+        if (wq == 0 && lane == 0) vempty[it & 1] = tc::mbar_wait(&empty[pr], (u - 1) & 1, err, 8) ? 1 : 0;
+        tc::named_bar_sync(2 + kofs, 128);
+        if (!vempty[it & 1]) break;
       }
       char *a_st = stA(s);
 #pragma unroll
@@ -488,55 +516,72 @@ __device__ __forceinline__ void two_sum(float &hi, float &lo, float v) {
   lo += e;
 }
 
-__global__ void reduce_f64(const float2 *__restrict__ part, int nsplit, size_t per_split,
-                           double2 *__restrict__ out, size_t n_out, int nt, size_t out_stride) {
+// One thread per (slice j, representative rho, column): the four sums (Re C, Re S, Im C,
+// Im S) over the site splits are each added exactly (TwoSum pairs) and rounded once to
+// FP64; then every requested momentum q of rho (rep_q[rep_first[rho] ..], entry 2 q + 1
+// when k_q = -k_rho) receives out[j][q][col] = C + i sigma_q S with
+// sigma_q = sign * (+1 or -1), i.e. Re = Re C - sigma Im S, Im = Im C + sigma Re S.
+__global__ void reduce_f64(const float4 *__restrict__ part, int nsplit, size_t per_split,
+                           const int *__restrict__ rep_first, const int *__restrict__ rep_q, int nrep, int sign,
+                           int ncols, double2 *__restrict__ out, int nt, size_t out_stride) {
+  const size_t n_in = (size_t)nrep * ncols;
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n_out * nt) return;
-  int j = (int)(idx / n_out);
-  size_t e = idx % n_out;
-  const float2 *pj = part + (size_t)j * nsplit * per_split + e;
-  float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f;
+  if (idx >= n_in * nt) return;
+  const int j = (int)(idx / n_in);
+  const size_t e = idx % n_in;
+  const int rho = (int)(e / ncols), col = (int)(e % ncols);
+  const float4 *pj = part + (size_t)j * nsplit * per_split + e;
+  float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
   for (int s = 0; s < nsplit; ++s) {
-    float2 v = pj[(size_t)s * per_split];
-    two_sum(hx, lx, v.x);
-    two_sum(hy, ly, v.y);
+    const float4 v = pj[(size_t)s * per_split];
+    two_sum(h[0], l[0], v.x);
+    two_sum(h[1], l[1], v.y);
+    two_sum(h[2], l[2], v.z);
+    two_sum(h[3], l[3], v.w);
   }
-  out[(size_t)j * out_stride + e] = make_double2((double)hx + (double)lx, (double)hy + (double)ly);
+  const double cr = (double)h[0] + (double)l[0], sr = (double)h[1] + (double)l[1];
+  const double ci = (double)h[2] + (double)l[2], si = (double)h[3] + (double)l[3];
+  double2 *oj = out + (size_t)j * out_stride + col;
+  for (int u = __ldg(rep_first + rho), u1 = __ldg(rep_first + rho + 1); u < u1; ++u) {
+    const int qe = __ldg(rep_q + u);
+    const double sigma = (qe & 1) ? -(double)sign : (double)sign;
+    oj[(size_t)(qe >> 1) * ncols] = make_double2(cr - sigma * si, ci + sigma * sr);
+  }
 }
 
-template <int MODE, int NP>
+template <int MODE, int NH>
 constexpr size_t fused_smem() {
   // rings + barriers + tensor-memory slot + up to 1023 B to align the rings
-  return (size_t)Stage<MODE, NP>::bytes + (2 * NPAIR + 2 * NIN + 5) * 8 + 16 + 1024;
+  return (size_t)Stage<MODE, NH>::bytes + (2 * NPAIR + 2 * NIN + 5) * 8 + 16 + 4 * (2 + 4 * NPK) + 1024;
 }
 
-template <int MODE, int NP>
+template <int MODE, int NH>
 int launch_fused_t(const FusedParams &p, int nt, cudaStream_t st) {
-  constexpr size_t smem = fused_smem<MODE, NP>();
+  constexpr size_t smem = fused_smem<MODE, NH>();
   static_assert(smem <= 232448, "shared memory per CTA");
   static bool attr = false;
   if (!attr) {
-    LHC_CHECK_CUDA(cudaFuncSetAttribute(fused_meson<float2, MODE, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    LHC_CHECK_CUDA(cudaFuncSetAttribute(fused_meson<float2, MODE, NH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)std::max<size_t>(smem, 120 * 1024)));
     attr = true;
   }
-  dim3 grid(p.nct, p.nsplit, nt * p.nqc);
+  dim3 grid(p.nct, p.nsplit, nt * p.nrc);
   // at least 120 KB so that one CTA runs per SM (the tensor memory is allocated whole)
-  fused_meson<float2, MODE, NP><<<grid, kThreads, std::max<size_t>(smem, 120 * 1024), st>>>(p);
+  fused_meson<float2, MODE, NH><<<grid, kThreads, std::max<size_t>(smem, 120 * 1024), st>>>(p);
   note_launch();
   return LHC_OK;
 }
 
 template <int MODE>
-int launch_fused_np(int Np, const FusedParams &p, int nt, cudaStream_t st) {
-  switch (Np) {
+int launch_fused_nh(int NH, const FusedParams &p, int nt, cudaStream_t st) {
+  switch (NH) {
+    case 8: return launch_fused_t<MODE, 8>(p, nt, st);
     case 16: return launch_fused_t<MODE, 16>(p, nt, st);
+    case 24: return launch_fused_t<MODE, 24>(p, nt, st);
     case 32: return launch_fused_t<MODE, 32>(p, nt, st);
+    case 40: return launch_fused_t<MODE, 40>(p, nt, st);
     case 48: return launch_fused_t<MODE, 48>(p, nt, st);
-    case 64: return launch_fused_t<MODE, 64>(p, nt, st);
-    case 80: return launch_fused_t<MODE, 80>(p, nt, st);
-    case 96: return launch_fused_t<MODE, 96>(p, nt, st);
-    default: set_error("unsupported momentum chunk %d", Np); return LHC_EINVAL;
+    default: set_error("unsupported representative chunk %d", NH); return LHC_EINVAL;
   }
 }
 
@@ -566,29 +611,45 @@ struct NarrowParams {
   int nb, V3;
 };
 
-__global__ void narrow_c128(NarrowParams p) {
-  // part 0: propagator, then (baryon) the second propagator, then noise i
-  const int j = blockIdx.y, nprop = p.SB ? 2 : 1, part = blockIdx.z;
+// One block per chunk of 1024 complex numbers of one part (propagator slices first, then
+// the second baryon propagator, then the noise vectors noise-major); every thread issues
+// its four 16-byte loads before converting, so each SM keeps many loads in flight.
+constexpr int kNarrowChunk = 1024;
+__global__ void __launch_bounds__(256) narrow_c128(NarrowParams p) {
+  const size_t nS = (size_t)p.V3 * 144, nV = (size_t)p.V3 * 12;
+  const size_t cS = (nS + kNarrowChunk - 1) / kNarrowChunk, cV = (nV + kNarrowChunk - 1) / kNarrowChunk;
+  size_t b = blockIdx.x;
   const double2 *src;
   float2 *dst;
   size_t n;
-  if (part == 0) {
+  if (b < (size_t)p.nb * cS) {
+    const int j = (int)(b / cS);
     src = static_cast<const double2 *>(p.slices[j].S);
-    dst = p.Sst + (size_t)j * p.V3 * 144;
-    n = (size_t)p.V3 * 144;
-  } else if (part < nprop) {
+    dst = p.Sst + (size_t)j * nS;
+    n = nS;
+    b %= cS;
+  } else if (p.SB && b < (size_t)(p.nb + 1) * cS) {
     src = static_cast<const double2 *>(p.SB);
     dst = p.SBst;
-    n = (size_t)p.V3 * 144;
+    n = nS;
+    b -= (size_t)p.nb * cS;
   } else {
-    src = static_cast<const double2 *>(p.slices[j].vec) + (size_t)(part - nprop) * p.vec_stride;
-    dst = p.Vst + ((size_t)(part - nprop) * p.nb + j) * p.V3 * 12;
-    n = (size_t)p.V3 * 12;
+    b -= (size_t)(p.nb + (p.SB ? 1 : 0)) * cS;
+    const size_t iv = b / cV;   // noise * nb + slice
+    const int i = (int)(iv / p.nb), j = (int)(iv % p.nb);
+    src = static_cast<const double2 *>(p.slices[j].vec) + (size_t)i * p.vec_stride;
+    dst = p.Vst + iv * nV;
+    n = nV;
+    b %= cV;
   }
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    double2 v = __ldg(src + e);
-    dst[e] = make_float2((float)v.x, (float)v.y);
-  }
+  const size_t e0 = b * kNarrowChunk + threadIdx.x;
+  double2 v[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    if (e0 + u * 256 < n) v[u] = __ldcs(src + e0 + u * 256);
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    if (e0 + u * 256 < n) dst[e0 + u * 256] = make_float2((float)v[u].x, (float)v[u].y);
 }
 
 // Noise-independent baryon diquark, FP32: D[x][c'][(alpha, c)] with
@@ -621,37 +682,94 @@ __global__ void __launch_bounds__(256) baryon_diquark(const float2 *__restrict__
 
 }  // namespace
 
-static int get_phase_split(lhc_ctx ctx, int L, const int *k, int nq, const int r[4], int sign, int Np, int nqc,
-                           int nkb, cudaStream_t st, const __half **out) {
-  PhaseKey key{L, nq, sign, 1, ((r[0] % L) + L) % L, ((r[1] % L) + L) % L, ((r[2] % L) + L) % L, hash_k(k, nq)};
+// Representatives of a momentum list: one k_rho per pair {k, -k} (the lexicographically
+// larger of the two), in order of first appearance.  The momenta of representative rho
+// are q_list[first[rho] .. first[rho + 1]), each entry 2 q + (1 if k_q = -k_rho).
+struct MomentumReps {
+  std::vector<int> k;       // [nrep][3]
+  std::vector<int> first;   // [nrep + 1]
+  std::vector<int> q_list;  // [nq]
+  int nrep() const { return (int)k.size() / 3; }
+};
+
+static MomentumReps momentum_reps(const int *k, int nq) {
+  MomentumReps m;
+  std::map<std::array<int, 3>, int> index;
+  std::vector<int> map(nq);
+  for (int q = 0; q < nq; ++q) {
+    const std::array<int, 3> a{k[3 * q], k[3 * q + 1], k[3 * q + 2]}, b{-a[0], -a[1], -a[2]};
+    const bool neg = b > a;
+    const std::array<int, 3> &c = neg ? b : a;
+    auto it = index.find(c);
+    int rho;
+    if (it == index.end()) {
+      rho = (int)index.size();
+      index.emplace(c, rho);
+      m.k.insert(m.k.end(), c.begin(), c.end());
+    } else {
+      rho = it->second;
+    }
+    map[q] = 2 * rho + (neg ? 1 : 0);
+  }
+  const int nrep = m.nrep();
+  m.first.assign(nrep + 1, 0);
+  for (int q = 0; q < nq; ++q) ++m.first[(map[q] >> 1) + 1];
+  for (int r = 0; r < nrep; ++r) m.first[r + 1] += m.first[r];
+  m.q_list.resize(nq);
+  std::vector<int> fill(m.first.begin(), m.first.end() - 1);
+  for (int q = 0; q < nq; ++q) m.q_list[fill[map[q] >> 1]++] = 2 * q + (map[q] & 1);
+  return m;
+}
+
+// Chunks of representatives per CTA: as few chunks as the tensor memory allows, balanced,
+// each a multiple of 8 representatives (the accumulator width 2 NH is a multiple of 16).
+static void rep_chunks(int nrep, int *nrc, int *NH) {
+  *nrc = (nrep + RCHUNK - 1) / RCHUNK;
+  *NH = ((nrep + *nrc - 1) / *nrc + 7) / 8 * 8;
+}
+
+// Phase table (cos | sin of the representatives, FP16 hi/lo) and the device copy of the
+// momentum map, cached per (L, momentum list, source position); the sign of the phase
+// does not enter the table, so insertion and spectator share it.
+static int get_phase_cs(lhc_ctx ctx, int L, const int *k, int nq, const int r[4], const MomentumReps &reps, int NH,
+                        int nrc, int nkb, cudaStream_t st, const __half **table, const int **rmap) {
+  PhaseKey key{L, nq, 0, 2, ((r[0] % L) + L) % L, ((r[1] % L) + L) % L, ((r[2] % L) + L) % L, hash_k(k, nq)};
+  const int nrep = reps.nrep();
+  const size_t tbytes = (size_t)nrc * nkb * 2 * 2 * NH * 32;
+  // rmap: first[nrep + 1] followed by q_list[nq]
+  const size_t off_map = (tbytes + 255) & ~(size_t)255;
   auto it = ctx->phases.find(key);
   if (it != ctx->phases.end()) {
     ctx->phase_lru.remove(key);
     ctx->phase_lru.push_front(key);
-    *out = static_cast<const __half *>(it->second.buf.p);
+    *table = static_cast<const __half *>(it->second.buf.p);
+    *rmap = reinterpret_cast<const int *>(static_cast<const char *>(it->second.buf.p) + off_map);
     return LHC_OK;
   }
-  size_t tbytes = (size_t)nqc * nkb * 2 * 3 * Np * 32;
-  size_t off_k = (tbytes + 255) & ~(size_t)255;
-  size_t off_roots = (off_k + (size_t)12 * nq + 255) & ~(size_t)255;
+  const size_t off_k = (off_map + sizeof(int) * (size_t)(nrep + 1 + nq) + 255) & ~(size_t)255;
+  const size_t off_roots = (off_k + (size_t)12 * nrep + 255) & ~(size_t)255;
   PhaseEntry e;
   LHC_TRY(dev_alloc(ctx, e.buf, off_roots + (size_t)L * sizeof(double2)));
   std::vector<double2> roots(L);
   const double two_pi = 6.283185307179586476925286766559;
   for (int m = 0; m < L; ++m) roots[m] = make_double2(std::cos(two_pi * m / L), std::sin(two_pi * m / L));
   char *base = static_cast<char *>(e.buf.p);
-  LHC_CHECK_CUDA(cudaMemcpy(base + off_k, k, (size_t)12 * nq, cudaMemcpyHostToDevice));
+  LHC_CHECK_CUDA(cudaMemcpy(base + off_map, reps.first.data(), sizeof(int) * (size_t)(nrep + 1), cudaMemcpyHostToDevice));
+  LHC_CHECK_CUDA(cudaMemcpy(base + off_map + sizeof(int) * (size_t)(nrep + 1), reps.q_list.data(),
+                            sizeof(int) * (size_t)nq, cudaMemcpyHostToDevice));
+  LHC_CHECK_CUDA(cudaMemcpy(base + off_k, reps.k.data(), (size_t)12 * nrep, cudaMemcpyHostToDevice));
   LHC_CHECK_CUDA(cudaMemcpy(base + off_roots, roots.data(), (size_t)L * sizeof(double2), cudaMemcpyHostToDevice));
-  size_t total = (size_t)nqc * nkb * 2 * 3 * Np * KSTEP;
-  phase_split_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
-      reinterpret_cast<__half *>(base), reinterpret_cast<const int *>(base + off_k), nq, Np, nqc, nkb, L, key.rx,
-      key.ry, key.rz, sign, reinterpret_cast<const double2 *>(base + off_roots));
+  const size_t total = (size_t)nrc * nkb * 2 * 2 * NH * KSTEP;
+  phase_cs_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+      reinterpret_cast<__half *>(base), reinterpret_cast<const int *>(base + off_k), nrep, NH, nrc, nkb, L, key.rx,
+      key.ry, key.rz, reinterpret_cast<const double2 *>(base + off_roots));
   note_launch();
   LHC_CHECK_CUDA(cudaGetLastError());
-  e.nq_pad = Np;
+  e.nq_pad = nrc * NH;
   ctx->phases[key] = e;
   ctx->phase_lru.push_front(key);
-  *out = reinterpret_cast<const __half *>(base);
+  *table = reinterpret_cast<const __half *>(base);
+  *rmap = reinterpret_cast<const int *>(base + off_map);
   return LHC_OK;
 }
 
@@ -662,11 +780,13 @@ size_t mixed_call_bytes(Part part, int dtype, int V3, int n_r, int nt, int nq) {
   const bool baryon = part == PART_SPEC_BARYON;
   const size_t ncols = (size_t)n_r * (baryon ? kBarCols : 192);
   const size_t ntl = (size_t)std::min(nt, kMaxSlices);
-  const size_t nkb = (V3 + 2 * KSTEP - 1) / (2 * KSTEP) * 2, nqc = (nq + QCHUNK - 1) / QCHUNK;
-  size_t b = ntl * 8 * nq * ncols * sizeof(float2);
+  // at most nq representatives: at most ceil(nq / RCHUNK) chunks of at most RCHUNK
+  const size_t nrep_pad = (size_t)(nq + RCHUNK - 1) / RCHUNK * RCHUNK;
+  const size_t nkb = (V3 + 2 * KSTEP - 1) / (2 * KSTEP) * 2;
+  size_t b = ntl * 8 * nrep_pad * ncols * sizeof(float4);
   if (dtype == LHC_C128) b += ntl * V3 * 144 * 8 + (baryon ? (size_t)V3 * 144 * 8 : 0) + (size_t)n_r * ntl * V3 * 12 * 8;
   if (baryon) b += (size_t)V3 * 2304 * 8;
-  b += nqc * nkb * 2 * 3 * QCHUNK * 32 + 4096;
+  b += nkb * 2 * 2 * nrep_pad * 32 + 4 * (size_t)(2 * nq + 1) + 12 * (size_t)nq + 4096;
   return b + 4 * 256;
 }
 
@@ -737,19 +857,22 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
   // site blocks, rounded up to an even number: the kernel consumes k-steps in pairs (the
   // pad block's phases are zero and its sites lie past the slice, which TMA reads as zero)
   const int nkb = ((V3 + 2 * KSTEP - 1) / (2 * KSTEP)) * 2;
-  const int nqc = (nq + QCHUNK - 1) / QCHUNK;
-  const int Np = ((std::min(nq, QCHUNK) + 15) / 16) * 16;
+  const MomentumReps reps = momentum_reps(k, nq);
+  int nrc, NH;
+  rep_chunks(reps.nrep(), &nrc, &NH);
   const __half *phase = nullptr;
-  LHC_TRY(get_phase_split(ctx, j0.L, k, nq, r, sign, Np, nqc, nkb, st, &phase));
+  const int *rmap = nullptr;
+  LHC_TRY(get_phase_cs(ctx, j0.L, k, nq, r, reps, NH, nrc, nkb, st, &phase, &rmap));
 
-  int nsplit = choose_nsplit(nct * nt * nqc, (nkb + 1) / 2, ctx->num_sms);
+  int nsplit = choose_nsplit(nct * nt * nrc, (nkb + 1) / 2, ctx->num_sms);
   int kd = 4;   // k-steps accumulated in tensor memory between drains (truncating accumulation)
   if (const char *e = getenv("LHC_KD")) kd = std::max(2, (atoi(e) + 1) / 2 * 2);   // even: k-steps come in pairs
   if (const char *e = getenv("LHC_NSPLIT")) nsplit = std::max(1, std::min((nkb + 1) / 2, atoi(e)));
 
   const int ntl = std::min(nt, kMaxSlices);   // slices per launch
   const bool narrow = j0.dtype == LHC_C128;
-  size_t p_bytes = (size_t)ntl * nsplit * nq * ncols * sizeof(float2);
+  const size_t per_split = (size_t)nrc * NH * ncols;   // float4 partials per slice and split
+  size_t p_bytes = (size_t)ntl * nsplit * per_split * sizeof(float4);
   size_t s_bytes = narrow ? (size_t)ntl * V3 * 144 * sizeof(float2) : 0;
   size_t sb_bytes = narrow && baryon ? (size_t)V3 * 144 * sizeof(float2) : 0;
   size_t v_bytes = narrow ? (size_t)n_r * ntl * V3 * 12 * sizeof(float2) : 0;
@@ -762,14 +885,14 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
 
   FusedParams fp;
   fp.B = phase;
-  fp.partial = reinterpret_cast<float2 *>(ws);
+  fp.partial = reinterpret_cast<float4 *>(ws);
   fp.err = ctx->dev_err;
   fp.n_r = n_r;
   fp.V3 = V3;
   fp.nct = nct;
   fp.nkb = nkb;
-  fp.nqc = nqc;
-  fp.nq = nq;
+  fp.nrc = nrc;
+  fp.nrep = reps.nrep();
   fp.ncols = ncols;
   fp.nsplit = nsplit;
   fp.kd = kd;
@@ -788,8 +911,10 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
       np.nb = nb;
       np.V3 = V3;
       ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT, (double)nb * V3 * ((baryon ? 288.0 : 144.0) + 12.0 * n_r) * 24);
-      dim3 grid((unsigned)std::max(1, std::min(1024, (V3 * 144 + 255) / 256 / 4)), nb, (baryon ? 2 : 1) + n_r);
-      narrow_c128<<<grid, 256, 0, st>>>(np);
+      const size_t cS = ((size_t)V3 * 144 + kNarrowChunk - 1) / kNarrowChunk;
+      const size_t cV = ((size_t)V3 * 12 + kNarrowChunk - 1) / kNarrowChunk;
+      const size_t blocks = (size_t)(nb + (baryon ? 1 : 0)) * cS + (size_t)n_r * nb * cV;
+      narrow_c128<<<(unsigned)blocks, 256, 0, st>>>(np);
       note_launch();
     }
     // tensor maps of the matrix operand and the vector of this chunk of slices
@@ -837,16 +962,18 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
     {
       ProfScope ps(ctx, st, LHC_KERNEL_FUSED, 8.0 * nb * (double)nq * ncols * V3);
       if (j0.part == PART_INS)
-        LHC_TRY(launch_fused_np<0>(Np, fp, nb, st));
+        LHC_TRY(launch_fused_nh<0>(NH, fp, nb, st));
       else if (j0.part == PART_SPEC_MESON)
-        LHC_TRY(launch_fused_np<1>(Np, fp, nb, st));
+        LHC_TRY(launch_fused_nh<1>(NH, fp, nb, st));
       else
-        LHC_TRY(launch_fused_np<2>(Np, fp, nb, st));
+        LHC_TRY(launch_fused_nh<2>(NH, fp, nb, st));
     }
     {
-      ProfScope ps(ctx, st, LHC_KERNEL_REDUCE, (double)nb * nsplit * n_out * 8 + (double)nb * n_out * 16);
-      reduce_f64<<<(unsigned)((n_out * nb + 255) / 256), 256, 0, st>>>(fp.partial, nsplit, n_out,
-                                                                          jobs[jb].out, n_out, nb, n_out);
+      const size_t n_in = (size_t)reps.nrep() * ncols;
+      ProfScope ps(ctx, st, LHC_KERNEL_REDUCE, (double)nb * nsplit * n_in * 16 + (double)nb * n_out * 16);
+      reduce_f64<<<(unsigned)((n_in * nb + 255) / 256), 256, 0, st>>>(fp.partial, nsplit, per_split, rmap,
+                                                                         rmap + reps.nrep() + 1, reps.nrep(), sign,
+                                                                         ncols, jobs[jb].out, nb, n_out);
       note_launch();
     }
   }

@@ -61,18 +61,27 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t pari
 
 // Bounded wait for phase `parity` of `bar`.  Returns false (and raises *err) on timeout;
 // once *err is set by anyone, waits give up.  Each try suspends the thread for up to
-// 20 us; the clock and the error word are looked at between tries.
+// 20 us; the clock and the error word are looked at every 8 tries, which keeps a waiting
+// thread's instructions few (every mbarrier arrival in the CTA can end a suspension).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *err, int code) {
   if (mbar_try_wait(bar, parity)) return true;
   long long t0 = clock64();
-  for (;;) {
+  for (uint32_t n = 1;; ++n) {
     if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
-    if (*err) return false;
-    if (clock64() - t0 > kSpinLimit) {
-      atomicExch((int *)err, code);
-      return false;
+    if ((n & 7u) == 0u) {
+      if (*err) return false;
+      if (clock64() - t0 > kSpinLimit) {
+        atomicExch((int *)err, code);
+        return false;
+      }
     }
   }
+}
+
+// Named barrier `id` (1..15) over `nthreads` threads (a multiple of 32, whole warps).
+// Warps blocked here issue nothing; every participating warp must arrive.
+__device__ __forceinline__ void named_bar_sync(uint32_t id, uint32_t nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 // cp.async.bulk global -> shared (this CTA), completion counted on `bar` in bytes.

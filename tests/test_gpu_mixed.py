@@ -62,6 +62,32 @@ def test_edges(ctx, L, n_r, n2max, r, dtype):
     assert report(f"spec L={L}", CS.block_err(gs, c.ref_spectator_meson(3), 1)) < CS.MIXED_TOL
 
 
+def _klists():
+    from oracle.momenta import momenta
+    rng = np.random.default_rng(77)
+    full = momenta(4)
+    half = np.array([k for k in full if tuple(k) > tuple(-k)])       # no partner requested
+    mixed = full[rng.permutation(len(full))][:40]                    # shuffled, pairs broken
+    mixed = np.concatenate([mixed, mixed[:5], -mixed[5:9]])          # duplicates and partners
+    modL = np.array([[2, 0, 0], [-2, 0, 0], [2, 2, 0], [-2, 2, 0], [0, -2, 2], [1, 0, 0], [-1, 0, 0]])
+    big = np.concatenate([momenta(18), np.array([[9, 0, 0], [0, 0, -9]])])   # 173 representatives: 4 chunks
+    return [("unpaired", half), ("shuffled", mixed), ("k=-k mod L", modL), ("four chunks", big)]
+
+
+@pytest.mark.parametrize("name,k", _klists(), ids=lambda v: v if isinstance(v, str) else "")
+def test_momentum_lists(ctx, name, k):
+    """The projection groups the momenta into pairs {k, -k} and forms both from the same
+    cos and sin sums: momentum lists with unpaired momenta, broken pairs, duplicates,
+    an arbitrary order, momenta whose negatives coincide modulo L (L = 4), and more
+    representatives than one chunk, all against the oracle."""
+    c = CS.Case(4, 4, 2, k, seed=1450, r=(3, 1, 2, 0))
+    gi = ctx.insertion(dev(c.S), dev(c.psi), 0, 2, c.r, c.k, prec="mixed").cpu().numpy()
+    gs = ctx.spectator(dev(c.S), dev(c.eta(2)), 2, c.r, c.k, prec="mixed").cpu().numpy()
+    ctx.sync()
+    assert report(f"ins {name}", CS.block_err(gi, c.ref_insertion(0, 2), 2)) < CS.MIXED_TOL
+    assert report(f"spec {name}", CS.block_err(gs, c.ref_spectator_meson(2), 1)) < CS.MIXED_TOL
+
+
 def test_other_gamma5(ctx):
     from oracle.momenta import momenta
     c = CS.Case(4, 4, 2, momenta(2), seed=1500, r=(1, 1, 1, 0))
