@@ -266,6 +266,40 @@ int lhc_profile_read(lhc_ctx ctx, int kernel, double *total_ms, long long *launc
  * counted again).  Never fails; reading it costs one atomic load. */
 unsigned long long lhc_launch_count(void);
 
+/* ---- Launch-shape autotuning of the LHC_MIXED path.  The paper has no counterpart:
+ * its kernels were tuned by hand for one machine.
+ *
+ * The fused kernel's launch shape has two parameters: how many momentum
+ * representatives (one per pair k, -k) one CTA projects (8..48, a multiple of 8), and
+ * into how many site ranges each slice is split.  Without tuning a heuristic picks
+ * them: the widest chunks, and splits that fill whole waves of one CTA per SM.
+ *
+ * With mode LHC_TUNE_ON, the first LHC_MIXED call of every new shape (part, dtype, L^3,
+ * n_r, slices per launch, representatives) times up to 30 candidate shapes on its own
+ * inputs. It synchronizes its stream meanwhile, and the fastest shape is kept for every
+ * later call of that shape in the process, from any context. Calls whose stream is
+ * being captured into a CUDA graph never tune, so tune before capturing. A tuned
+ * call's results equal those of any other shape within the mixed path's error bound:
+ * the site split changes the summation order. Calls of the same shape always use the
+ * same launch shape, so they are bitwise reproducible.
+ *
+ * path (may be NULL) names a text file. Entries already in it are loaded now, and the
+ * whole table is rewritten after each new entry, one line per shape:
+ *   part dtype V3 n_r nt nrep  NH nsplit  microseconds
+ * Returns LHC_EINVAL for an unknown mode or a malformed file. */
+typedef enum { LHC_TUNE_OFF = 0, LHC_TUNE_ON = 1 } lhc_tune_mode;
+int lhc_set_tuning(lhc_ctx ctx, int mode, const char *path);
+
+/* The process-wide launch-shape table: writes min(count, cap) entries as int[cap][8]
+ * (part, dtype, V3, n_r, nt, nrep, NH, nsplit; part 0 insertion, 1 meson spectator,
+ * 2 baryon spectator) and the number of entries to *count. */
+int lhc_tuning_table(int *entries, int cap, int *count);
+
+/* Loads the entries of a table file into the process-wide table without touching a
+ * GPU; *count = entries read (0 when the file does not exist).  LHC_EINVAL on a
+ * malformed line, which leaves the lines before it loaded. */
+int lhc_tuning_load(const char *path, int *count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,6 +13,7 @@
 // accumulation, and it keeps GB300's slow FP64 pipe out of the inner loop).
 #include <type_traits>
 
+#include "conv.cuh"
 #include "lhc_internal.h"
 
 namespace lhc {
@@ -26,7 +27,10 @@ struct cplx {
 template <typename R>
 __device__ __forceinline__ cplx<R> ld(const double2 *p) {
   double2 v = *p;
-  return {(R)v.x, (R)v.y};
+  if constexpr (std::is_same<R, float>::value)
+    return {f64_to_f32_rne(v.x), f64_to_f32_rne(v.y)};   // integer conversion, off the FP64 pipe
+  else
+    return {v.x, v.y};
 }
 template <typename R>
 __device__ __forceinline__ void cfma(cplx<R> &acc, cplx<R> a, cplx<R> b) {
@@ -182,7 +186,7 @@ struct NoiseSum {
     x += (double)v.x;
     y += (double)v.y;
   }
-  __device__ __forceinline__ double2 get(double scale) const { return make_double2(x * scale, y * scale); }
+  __device__ __forceinline__ double2 get(double scale, float) const { return make_double2(x * scale, y * scale); }
 };
 __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float v) {
   const float s = hi + v, bp = s - hi;
@@ -196,54 +200,82 @@ struct NoiseSum<float> {
     two_sum_acc(hx, lx, v.x);
     two_sum_acc(hy, ly, v.y);
   }
-  __device__ __forceinline__ double2 get(double scale) const {
-    return make_double2(((double)hx + (double)lx) * scale, ((double)hy + (double)ly) * scale);
+  // (hi + lo) * scale rounded once to FP64; a power-of-two scale (1/N for N = 2^m) is
+  // applied to hi and lo in FP32 without error (barring underflow), which leaves one
+  // FP64 addition per component
+  __device__ __forceinline__ double2 get(double scale, float scale_pow2) const {
+    if (scale_pow2 != 0.f)
+      return make_double2(f32_to_f64(hx * scale_pow2) + f32_to_f64(lx * scale_pow2),
+                          f32_to_f64(hy * scale_pow2) + f32_to_f64(ly * scale_pow2));
+    return make_double2((f32_to_f64(hx) + f32_to_f64(lx)) * scale, (f32_to_f64(hy) + f32_to_f64(ly)) * scale);
   }
 };
 
 // out[t][g][p][q] = (1/N) sum_i sum_{j<12} Xs[g][p][12i+j] Xi[t][g][q][12i+j]: a tiled complex
 // GEMM whose per-noise 12-term sums run in R (float or double) and whose sum over
-// noises is the NoiseSum above.
-constexpr int CTILE = 32;
+// noises is the NoiseSum above.  A CTA computes a TP x TQ tile of (p, q) for one (t, g);
+// thread (ty, tx) of 16 x 16 holds p = p0 + ty + 16 a (a < 2) and q = q0 + tx + 16 b
+// (b < 3).  KN noises (12 KN values of K) are staged per pass (4 in FP32, 2 in FP64: the
+// static shared memory stays below 48 KB); rows are padded by one element so that the
+// 16 q rows a warp reads fall into distinct banks.
+constexpr int TP = 32, TQ = 48;
 template <typename R>
 __global__ void __launch_bounds__(256) comb_gemm(const cplx<R> *__restrict__ Xs, const cplx<R> *__restrict__ Xi,
-                                                 int np, int nq, int n_r, int ng, double inv_n,
+                                                 int np, int nq, int n_r, int ng, double inv_n, float inv_n_pow2,
                                                  double2 *__restrict__ out) {
-  __shared__ cplx<R> As[CTILE][13];
-  __shared__ cplx<R> Bs[CTILE][13];
+  constexpr int KN = sizeof(R) == 4 ? 4 : 2, KW = 12 * KN + 1;
+  __shared__ cplx<R> As[TP * KW];
+  __shared__ cplx<R> Bs[TQ * KW];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int q0 = blockIdx.x * CTILE, p0 = blockIdx.y * CTILE;
+  const int q0 = blockIdx.x * TQ, p0 = blockIdx.y * TP;
   const int tg = blockIdx.z;   // t * ng + g
   const int g = tg % ng;
   const size_t K = (size_t)12 * n_r;
   const cplx<R> *A = Xs + ((size_t)g * np) * K;
   const cplx<R> *B = Xi + ((size_t)tg * nq) * K;
-  NoiseSum<R> acc[2][2];
-  for (int i = 0; i < n_r; ++i) {
-    for (int e = threadIdx.x; e < CTILE * 12; e += 256) {
-      int r = e / 12, k = e % 12;
-      As[r][k] = (p0 + r < np) ? A[(size_t)(p0 + r) * K + 12 * i + k] : cplx<R>{0, 0};
-      Bs[r][k] = (q0 + r < nq) ? B[(size_t)(q0 + r) * K + 12 * i + k] : cplx<R>{0, 0};
+  NoiseSum<R> acc[2][3];
+  for (int i0 = 0; i0 < n_r; i0 += KN) {
+    const int kw = 12 * min(KN, n_r - i0);
+    for (int e = threadIdx.x; e < TP * 12 * KN; e += 256) {
+      const int r = e / (12 * KN), k = e % (12 * KN);
+      As[r * KW + k] = (p0 + r < np && k < kw) ? A[(size_t)(p0 + r) * K + 12 * i0 + k] : cplx<R>{0, 0};
+    }
+    for (int e = threadIdx.x; e < TQ * 12 * KN; e += 256) {
+      const int r = e / (12 * KN), k = e % (12 * KN);
+      Bs[r * KW + k] = (q0 + r < nq && k < kw) ? B[(size_t)(q0 + r) * K + 12 * i0 + k] : cplx<R>{0, 0};
     }
     __syncthreads();
+    for (int ii = 0; ii < kw / 12; ++ii) {
+      cplx<R> pa[2][3];
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+      for (int a = 0; a < 2; ++a)
 #pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        cplx<R> pa{0, 0};
+        for (int b = 0; b < 3; ++b) pa[a][b] = cplx<R>{0, 0};
+      const cplx<R> *ar = As + ty * KW + 12 * ii, *br = Bs + tx * KW + 12 * ii;
 #pragma unroll
-        for (int k = 0; k < 12; ++k) cfma(pa, As[ty + 16 * a][k], Bs[tx + 16 * b][k]);
-        acc[a][b].add(pa);
+      for (int k = 0; k < 12; ++k) {
+        const cplx<R> a0 = ar[k], a1 = ar[16 * KW + k];
+        const cplx<R> b0 = br[k], b1 = br[16 * KW + k], b2 = br[32 * KW + k];
+        cfma(pa[0][0], a0, b0);
+        cfma(pa[0][1], a0, b1);
+        cfma(pa[0][2], a0, b2);
+        cfma(pa[1][0], a1, b0);
+        cfma(pa[1][1], a1, b1);
+        cfma(pa[1][2], a1, b2);
       }
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) acc[a][b].add(pa[a][b]);
+    }
     __syncthreads();
   }
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      int p = p0 + ty + 16 * a, q = q0 + tx + 16 * b;
-      if (p < np && q < nq)
-        out[((size_t)tg * np + p) * nq + q] = acc[a][b].get(inv_n);
+    for (int b = 0; b < 3; ++b) {
+      const int p = p0 + ty + 16 * a, q = q0 + tx + 16 * b;
+      if (p < np && q < nq) out[((size_t)tg * np + p) * nq + q] = acc[a][b].get(inv_n, inv_n_pow2);
     }
 }
 
@@ -281,8 +313,9 @@ int launch_combine(int kind, const double2 *spec, int np, const double2 *ins, in
     comb_ins_baryon<R><<<nt * nq, 256, smem, st>>>(ins, nq, n_r, ins_g, ng, Xi);
     note_launch();
   }
-  dim3 grid((nq + CTILE - 1) / CTILE, (np + CTILE - 1) / CTILE, nt * ng);
-  comb_gemm<R><<<grid, 256, 0, st>>>(Xs, Xi, np, nq, n_r, ng, 1.0 / n_r, out);
+  dim3 grid((nq + TQ - 1) / TQ, (np + TP - 1) / TP, nt * ng);
+  const float inv_pow2 = (n_r & (n_r - 1)) == 0 ? 1.0f / (float)n_r : 0.0f;   // exact for N = 2^m
+  comb_gemm<R><<<grid, 256, 0, st>>>(Xs, Xi, np, nq, n_r, ng, 1.0 / n_r, inv_pow2, out);
   note_launch();
   return LHC_OK;
 }

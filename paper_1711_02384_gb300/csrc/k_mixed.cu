@@ -44,6 +44,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include "conv.cuh"
 #include "lhc_internal.h"
 #include "tc_ptx.cuh"
 
@@ -57,7 +58,7 @@ constexpr int RCHUNK = 48;               // momentum representatives per CTA (te
 // (row groups 144 B apart, the two 8-site k blocks 2304 B apart)
 constexpr int ATILE = 2 * 16 * 144;
 constexpr int ASTAGE = 4 * ATILE;        // Ur hi, Ur lo, Ui hi, Ui lo
-constexpr int NSTAGE = 4;                // A/B ring (freed by the MMA), used as two pairs of stages
+constexpr int NSTAGE = 6;                // A/B ring (freed by the MMA), used as pairs of stages
 constexpr int NPAIR = NSTAGE / 2;
 constexpr int NIN = 6;                   // input ring (freed by the producers)
 constexpr int NPK = 3;                   // k-steps in flight in the producers (4 warps each)
@@ -136,8 +137,26 @@ struct FusedParams {
   const __half *B;                      // phase table
   float4 *partial;                      // [nt][nsplit][nrc * NH][ncols]: (Re C, Re S, Im C, Im S)
   int *err;
+  // per slice of the launch: the largest |re| or |im| of the matrix operand and of the
+  // vector operand (as float bits), from which the CTA picks its power-of-two scale
+  const unsigned *maxM, *maxV;
+  int maxM_per_slice;                   // 1: maxM[j]; 0: maxM[0] for every slice (diquark)
   int n_r, V3, nct, nkb, nrc, nrep, ncols, nsplit, kd, g5mask;
 };
+
+// Power-of-two scale of the contracted values before their FP16 split.  Every value is a
+// sum over 3 colours of (vector x matrix) products, so |re|, |im| <= 6 mV mM with mV, mM
+// the largest real or imaginary parts of the operands.  The scale 2^e puts that bound at
+// 2^14: far below the FP16 maximum (65504), and typical values, which lie well below the
+// bound, keep their lo parts (2^-11 of the value) out of the FP16 subnormal range.  The
+// drain multiplies the sums by 2^-e, which is exact.
+__device__ __forceinline__ int split_scale_exp(unsigned mM_bits, unsigned mV_bits) {
+  const float b = 6.f * __uint_as_float(mM_bits) * __uint_as_float(mV_bits);
+  if (!(b > 0.f) || !(b < 3.0e38f)) return 0;
+  int x;
+  frexpf(b, &x);   // b = f 2^x, f in [0.5, 1): b <= 2^x
+  return max(-100, min(100, 14 - x));
+}
 
 // fp16 hi/lo split of two floats, packed as half2 pairs
 __device__ __forceinline__ void split2(float v0, float v1, uint32_t &hi, uint32_t &lo) {
@@ -196,6 +215,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ct = blockIdx.x, split = blockIdx.y;
   const int j = blockIdx.z / p.nrc, rc = blockIdx.z % p.nrc;
+  const int sc_e = split_scale_exp(p.maxM[p.maxM_per_slice ? j : 0], p.maxV[j]);
   // site range in k-steps; splits start on even k-steps so producer iterations align
   const int npair = (p.nkb + 1) / 2;
   const int kb0 = 2 * (int)((long long)npair * split / p.nsplit);
@@ -380,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
     // linear, so they act on the finished sums
     const int smask = MODE != 1 ? (p.g5mask >> v)
                                 : ((p.g5mask >> v) ^ (p.g5mask >> (sidx / 12)) ^ (p.g5mask >> ((sidx % 12) / 3)));
-    const float sgn = (smask & 1) ? -1.f : 1.f;
+    const float sgn = ldexpf((smask & 1) ? -1.f : 1.f, -sc_e);   // the sign and the inverse split scale
     const int rend = min(p.nrep - rc * NH, NH);
     // tcgen05.ld is warp-collective: every lane executes it, only the stores are per lane
     const int failed = __shfl_sync(0xffffffffu, *err, 0);
@@ -418,6 +438,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
     const int kofs = pw >> 2, wq = pw & 3;
     const int sp = lane & 7, x = 4 * wq + (lane >> 3);   // column and site within the k-step
     const int nit = (nk + NPK - 1) / NPK;
+    const float sc = ldexpf(1.f, sc_e);
     // matrix-box offsets of this lane's two columns (colour 0; colour c adds c*12 or c*16)
     int mo[2];
 #pragma unroll
@@ -447,7 +468,10 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
       for (int c = 0; c < 3; ++c) {
         float2 sv[2];
 #pragma unroll
-        for (int jx = 0; jx < 2; ++jx) sv[jx] = Ms[mo[jx] + c * (MODE == 2 ? 16 : 12)];
+        for (int jx = 0; jx < 2; ++jx) {
+          const float2 m = Ms[mo[jx] + c * (MODE == 2 ? 16 : 12)];
+          sv[jx] = make_float2(m.x * sc, m.y * sc);   // the split scale, folded into the matrix value
+        }
 #pragma unroll
         for (int iv = 0; iv < 8; ++iv) {
           const float2 pv = Vs[(iv >> 2) * 16 * 12 + (iv & 3) * 3 + c];   // noise iv/4, spin iv%4
@@ -517,10 +541,12 @@ __device__ __forceinline__ void two_sum(float &hi, float &lo, float v) {
 }
 
 // One thread per (slice j, representative rho, column): the four sums (Re C, Re S, Im C,
-// Im S) over the site splits are each added exactly (TwoSum pairs) and rounded once to
-// FP64; then every requested momentum q of rho (rep_q[rep_first[rho] ..], entry 2 q + 1
-// when k_q = -k_rho) receives out[j][q][col] = C + i sigma_q S with
-// sigma_q = sign * (+1 or -1), i.e. Re = Re C - sigma Im S, Im = Im C + sigma Re S.
+// Im S) over the site splits are each kept exactly as an unevaluated FP32 pair (TwoSum).
+// Every requested momentum q of rho (rep_q[rep_first[rho] ..], entry 2 q + 1 when
+// k_q = -k_rho) receives out[j][q][col] = C + i sigma_q S with sigma_q = sign * (+1 or
+// -1): Re = Re C - sigma Im S and Im = Im C + sigma Re S are formed as FP32 pairs too
+// (TwoSum of the leading parts, the trailing parts added), and each pair is rounded once
+// to FP64 with one FP64 addition; the FP64 pipe of GB300 does nothing else here.
 __global__ void reduce_f64(const float4 *__restrict__ part, int nsplit, size_t per_split,
                            const int *__restrict__ rep_first, const int *__restrict__ rep_q, int nrep, int sign,
                            int ncols, double2 *__restrict__ out, int nt, size_t out_stride) {
@@ -539,13 +565,15 @@ __global__ void reduce_f64(const float4 *__restrict__ part, int nsplit, size_t p
     two_sum(h[2], l[2], v.z);
     two_sum(h[3], l[3], v.w);
   }
-  const double cr = (double)h[0] + (double)l[0], sr = (double)h[1] + (double)l[1];
-  const double ci = (double)h[2] + (double)l[2], si = (double)h[3] + (double)l[3];
   double2 *oj = out + (size_t)j * out_stride + col;
   for (int u = __ldg(rep_first + rho), u1 = __ldg(rep_first + rho + 1); u < u1; ++u) {
     const int qe = __ldg(rep_q + u);
-    const double sigma = (qe & 1) ? -(double)sign : (double)sign;
-    oj[(size_t)(qe >> 1) * ncols] = make_double2(cr - sigma * si, ci + sigma * sr);
+    const float sg = (qe & 1) ? -(float)sign : (float)sign;
+    // Re = (h0 + l0) - sg (h3 + l3), Im = (h2 + l2) + sg (h1 + l1): sg = +-1 is exact
+    float rh = h[0], rl = l[0] - sg * l[3], ih = h[2], il = l[2] + sg * l[1];
+    two_sum(rh, rl, -sg * h[3]);
+    two_sum(ih, il, sg * h[1]);
+    oj[(size_t)(qe >> 1) * ncols] = make_double2(f32_to_f64(rh) + f32_to_f64(rl), f32_to_f64(ih) + f32_to_f64(il));
   }
 }
 
@@ -608,12 +636,31 @@ struct NarrowParams {
   const void *SB;      // baryon: second propagator slice (one slice), else nullptr
   size_t vec_stride;   // source elements between noises
   float2 *Sst, *SBst, *Vst;
+  unsigned *maxS, *maxV;   // per slice: largest |re| or |im| of the propagator and of the vectors
   int nb, V3;
 };
 
+// Largest |re| or |im| over a block's values, folded into *m with an atomic max on the
+// float bits (non-negative floats order like their bit patterns).
+__device__ __forceinline__ void block_max_to(unsigned *m, float v) {
+  __shared__ float wmax[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0 && m) atomicMax(m, __float_as_uint(v));
+  }
+}
+
 // One block per chunk of 1024 complex numbers of one part (propagator slices first, then
 // the second baryon propagator, then the noise vectors noise-major); every thread issues
-// its four 16-byte loads before converting, so each SM keeps many loads in flight.
+// its four 16-byte loads before converting, so each SM keeps many loads in flight.  The
+// conversion is the integer one (f64_to_f32_rne): with the hardware conversion this
+// copy is bound by the FP64 pipe.
 constexpr int kNarrowChunk = 1024;
 __global__ void __launch_bounds__(256) narrow_c128(NarrowParams p) {
   const size_t nS = (size_t)p.V3 * 144, nV = (size_t)p.V3 * 12;
@@ -622,17 +669,20 @@ __global__ void __launch_bounds__(256) narrow_c128(NarrowParams p) {
   const double2 *src;
   float2 *dst;
   size_t n;
+  unsigned *mx;
   if (b < (size_t)p.nb * cS) {
     const int j = (int)(b / cS);
     src = static_cast<const double2 *>(p.slices[j].S);
     dst = p.Sst + (size_t)j * nS;
     n = nS;
     b %= cS;
+    mx = p.maxS + j;
   } else if (p.SB && b < (size_t)(p.nb + 1) * cS) {
     src = static_cast<const double2 *>(p.SB);
     dst = p.SBst;
     n = nS;
     b -= (size_t)p.nb * cS;
+    mx = nullptr;   // the baryon's matrix operand is the diquark, bounded separately
   } else {
     b -= (size_t)(p.nb + (p.SB ? 1 : 0)) * cS;
     const size_t iv = b / cV;   // noise * nb + slice
@@ -641,15 +691,64 @@ __global__ void __launch_bounds__(256) narrow_c128(NarrowParams p) {
     dst = p.Vst + iv * nV;
     n = nV;
     b %= cV;
+    mx = p.maxV + j;
   }
   const size_t e0 = b * kNarrowChunk + threadIdx.x;
   double2 v[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
     if (e0 + u * 256 < n) v[u] = __ldcs(src + e0 + u * 256);
+  float m = 0.f;
 #pragma unroll
   for (int u = 0; u < 4; ++u)
-    if (e0 + u * 256 < n) dst[e0 + u * 256] = make_float2((float)v[u].x, (float)v[u].y);
+    if (e0 + u * 256 < n) {
+      const float2 w = make_float2(f64_to_f32_rne(v[u].x), f64_to_f32_rne(v[u].y));
+      dst[e0 + u * 256] = w;
+      m = fmaxf(m, fmaxf(fabsf(w.x), fabsf(w.y)));
+    }
+  block_max_to(mx, m);
+}
+
+// The same per-slice maxima for complex64 inputs, which are read in place (no copy).
+struct MaxParams {
+  SlicePtrs slices[kMaxSlices];
+  size_t vec_stride;
+  unsigned *maxS, *maxV;
+  int nb, V3, n_r, with_S;
+};
+
+__global__ void __launch_bounds__(256) max_c64(MaxParams p) {
+  const size_t nS = (size_t)p.V3 * 144, nV = (size_t)p.V3 * 12;
+  const size_t cS = (nS + kNarrowChunk - 1) / kNarrowChunk, cV = (nV + kNarrowChunk - 1) / kNarrowChunk;
+  size_t b = blockIdx.x;
+  const float4 *src;   // two complex64 per float4 (sizes are multiples of 2 complex numbers)
+  size_t n;
+  unsigned *mx;
+  const size_t nSb = p.with_S ? (size_t)p.nb * cS : 0;
+  if (b < nSb) {
+    const int j = (int)(b / cS);
+    src = static_cast<const float4 *>(p.slices[j].S);
+    n = nS / 2;
+    b %= cS;
+    mx = p.maxS + j;
+  } else {
+    b -= nSb;
+    const size_t iv = b / cV;
+    const int i = (int)(iv / p.nb), j = (int)(iv % p.nb);
+    src = reinterpret_cast<const float4 *>(static_cast<const float2 *>(p.slices[j].vec) + (size_t)i * p.vec_stride);
+    n = nV / 2;
+    b %= cV;
+    mx = p.maxV + j;
+  }
+  const size_t e0 = b * (kNarrowChunk / 2) + threadIdx.x;
+  float m = 0.f;
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+    if (e0 + u * 256 < n) {
+      const float4 w = __ldcs(src + e0 + u * 256);
+      m = fmaxf(m, fmaxf(fmaxf(fabsf(w.x), fabsf(w.y)), fmaxf(fabsf(w.z), fabsf(w.w))));
+    }
+  block_max_to(mx, m);
 }
 
 // Noise-independent baryon diquark, FP32: D[x][c'][(alpha, c)] with
@@ -658,7 +757,7 @@ __global__ void __launch_bounds__(256) narrow_c128(NarrowParams p) {
 // GA[p,u]GB[q,v] - GA[p,v]GB[q,u] - GA[q,u]GB[p,v] + GA[q,v]GB[p,u].
 // One CTA per site: the two 12x12 propagators are staged in shared memory.
 __global__ void __launch_bounds__(256) baryon_diquark(const float2 *__restrict__ GA, const float2 *__restrict__ GB,
-                                                      int V3, float2 *__restrict__ D) {
+                                                      int V3, float2 *__restrict__ D, unsigned *maxD) {
   __shared__ float2 a[144], bm[144];
   const int x = blockIdx.x;
   for (int e = threadIdx.x; e < 144; e += 256) {
@@ -667,6 +766,7 @@ __global__ void __launch_bounds__(256) baryon_diquark(const float2 *__restrict__
   }
   __syncthreads();
   float2 *out = D + (size_t)x * 2304;
+  float m = 0.f;   // largest |re| or |im| of D (the bound of the fused kernel's split scale)
   for (int e = threadIdx.x; e < 2304; e += 256) {
     const int cp = e / 768, sidx = e % 768, c = sidx % 3, al = sidx / 3;
     const int a2 = al & 3, a2p = (al >> 2) & 3, a1 = (al >> 4) & 3, a1p = al >> 6;
@@ -676,8 +776,11 @@ __global__ void __launch_bounds__(256) baryon_diquark(const float2 *__restrict__
     auto mul = [](float2 x1, float2 y1) { return make_float2(x1.x * y1.x - x1.y * y1.y, x1.x * y1.y + x1.y * y1.x); };
     float2 t1 = mul(A(pp, u), B(qq, v)), t2 = mul(A(pp, v), B(qq, u)), t3 = mul(A(qq, u), B(pp, v)),
            t4 = mul(A(qq, v), B(pp, u));
-    out[e] = make_float2(t1.x - t2.x - t3.x + t4.x, t1.y - t2.y - t3.y + t4.y);
+    const float2 d = make_float2(t1.x - t2.x - t3.x + t4.x, t1.y - t2.y - t3.y + t4.y);
+    out[e] = d;
+    m = fmaxf(m, fmaxf(fabsf(d.x), fabsf(d.y)));
   }
+  block_max_to(maxD, m);
 }
 
 }  // namespace
@@ -729,11 +832,12 @@ static void rep_chunks(int nrep, int *nrc, int *NH) {
 }
 
 // Phase table (cos | sin of the representatives, FP16 hi/lo) and the device copy of the
-// momentum map, cached per (L, momentum list, source position); the sign of the phase
-// does not enter the table, so insertion and spectator share it.
+// momentum map, cached per (L, momentum list, source position, chunk width NH, which the
+// key carries in its sign field); the sign of the phase does not enter the table, so
+// insertion and spectator share it.
 static int get_phase_cs(lhc_ctx ctx, int L, const int *k, int nq, const int r[4], const MomentumReps &reps, int NH,
                         int nrc, int nkb, cudaStream_t st, const __half **table, const int **rmap) {
-  PhaseKey key{L, nq, 0, 2, ((r[0] % L) + L) % L, ((r[1] % L) + L) % L, ((r[2] % L) + L) % L, hash_k(k, nq)};
+  PhaseKey key{L, nq, NH, 2, ((r[0] % L) + L) % L, ((r[1] % L) + L) % L, ((r[2] % L) + L) % L, hash_k(k, nq)};
   const int nrep = reps.nrep();
   const size_t tbytes = (size_t)nrc * nkb * 2 * 2 * NH * 32;
   // rmap: first[nrep + 1] followed by q_list[nq]
@@ -787,6 +891,7 @@ size_t mixed_call_bytes(Part part, int dtype, int V3, int n_r, int nt, int nq) {
   if (dtype == LHC_C128) b += ntl * V3 * 144 * 8 + (baryon ? (size_t)V3 * 144 * 8 : 0) + (size_t)n_r * ntl * V3 * 12 * 8;
   if (baryon) b += (size_t)V3 * 2304 * 8;
   b += nkb * 2 * 2 * nrep_pad * 32 + 4 * (size_t)(2 * nq + 1) + 12 * (size_t)nq + 4096;
+  b += (2 * kMaxSlices + 1) * sizeof(unsigned) + 256;   // operand maxima of the split scale
   return b + 4 * 256;
 }
 
@@ -847,8 +952,10 @@ static int slice_coords(const void *const *ptrs, int nb, size_t slice_bytes, con
   return LHC_OK;
 }
 
-int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int nq, const int r[4], int sign,
-                   cudaStream_t st) {
+// One mixed-precision call with a given launch shape: NH representatives per CTA (a
+// multiple of 8, at most RCHUNK) and nsplit site ranges per slice.
+static int run_mixed_shape(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int nq, const int r[4],
+                           int sign, cudaStream_t st, const MomentumReps &reps, int NH, int nsplit) {
   const SliceJob &j0 = jobs[0];
   const bool baryon = j0.part == PART_SPEC_BARYON;
   const int V3 = j0.V3, n_r = j0.n_r;
@@ -857,17 +964,13 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
   // site blocks, rounded up to an even number: the kernel consumes k-steps in pairs (the
   // pad block's phases are zero and its sites lie past the slice, which TMA reads as zero)
   const int nkb = ((V3 + 2 * KSTEP - 1) / (2 * KSTEP)) * 2;
-  const MomentumReps reps = momentum_reps(k, nq);
-  int nrc, NH;
-  rep_chunks(reps.nrep(), &nrc, &NH);
+  const int nrc = (reps.nrep() + NH - 1) / NH;
   const __half *phase = nullptr;
   const int *rmap = nullptr;
   LHC_TRY(get_phase_cs(ctx, j0.L, k, nq, r, reps, NH, nrc, nkb, st, &phase, &rmap));
 
-  int nsplit = choose_nsplit(nct * nt * nrc, (nkb + 1) / 2, ctx->num_sms);
-  int kd = 4;   // k-steps accumulated in tensor memory between drains (truncating accumulation)
+  int kd = 6;   // k-steps accumulated in tensor memory between drains (truncating accumulation)
   if (const char *e = getenv("LHC_KD")) kd = std::max(2, (atoi(e) + 1) / 2 * 2);   // even: k-steps come in pairs
-  if (const char *e = getenv("LHC_NSPLIT")) nsplit = std::max(1, std::min((nkb + 1) / 2, atoi(e)));
 
   const int ntl = std::min(nt, kMaxSlices);   // slices per launch
   const bool narrow = j0.dtype == LHC_C128;
@@ -879,9 +982,11 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
   size_t d_bytes = baryon ? (size_t)V3 * 2304 * sizeof(float2) : 0;   // diquark (one sink slice)
   auto al256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
   size_t off_s = al256(p_bytes), off_sb = off_s + al256(s_bytes), off_v = off_sb + al256(sb_bytes),
-         off_d = off_v + al256(v_bytes);
-  LHC_TRY(ensure(ctx, ctx->ws, off_d + d_bytes));
+         off_d = off_v + al256(v_bytes), off_m = off_d + al256(d_bytes);
+  const size_t m_bytes = (2 * kMaxSlices + 1) * sizeof(unsigned);   // maxS, maxV per slice, maxD
+  LHC_TRY(ensure(ctx, ctx->ws, off_m + m_bytes));
   char *ws = static_cast<char *>(ctx->ws.p);
+  unsigned *maxS = reinterpret_cast<unsigned *>(ws + off_m), *maxV = maxS + kMaxSlices, *maxD = maxV + kMaxSlices;
 
   FusedParams fp;
   fp.B = phase;
@@ -897,9 +1002,14 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
   fp.nsplit = nsplit;
   fp.kd = kd;
   fp.g5mask = j0.g5mask;
+  fp.maxM = baryon ? maxD : maxS;
+  fp.maxM_per_slice = baryon ? 0 : 1;
+  fp.maxV = maxV;
   const size_t n_out = (size_t)nq * ncols;
   for (int jb = 0; jb < nt; jb += kMaxSlices) {
     const int nb = std::min(kMaxSlices, nt - jb);
+    // the operand maxima of this chunk of slices (for the split scale) start at zero
+    LHC_CHECK_CUDA(cudaMemsetAsync(maxS, 0, m_bytes, st));
     if (narrow) {
       NarrowParams np;
       for (int j = 0; j < nb; ++j) np.slices[j] = SlicePtrs{jobs[jb + j].S, jobs[jb + j].vec};
@@ -908,6 +1018,8 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
       np.Sst = reinterpret_cast<float2 *>(ws + off_s);
       np.SBst = reinterpret_cast<float2 *>(ws + off_sb);
       np.Vst = reinterpret_cast<float2 *>(ws + off_v);
+      np.maxS = maxS;
+      np.maxV = maxV;
       np.nb = nb;
       np.V3 = V3;
       ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT, (double)nb * V3 * ((baryon ? 288.0 : 144.0) + 12.0 * n_r) * 24);
@@ -915,6 +1027,23 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
       const size_t cV = ((size_t)V3 * 12 + kNarrowChunk - 1) / kNarrowChunk;
       const size_t blocks = (size_t)(nb + (baryon ? 1 : 0)) * cS + (size_t)n_r * nb * cV;
       narrow_c128<<<(unsigned)blocks, 256, 0, st>>>(np);
+      note_launch();
+    } else {
+      // complex64 inputs are read in place; one read-only pass finds their maxima
+      MaxParams mp;
+      for (int j = 0; j < nb; ++j) mp.slices[j] = SlicePtrs{jobs[jb + j].S, jobs[jb + j].vec};
+      mp.vec_stride = j0.vec_stride;
+      mp.maxS = maxS;
+      mp.maxV = maxV;
+      mp.nb = nb;
+      mp.V3 = V3;
+      mp.n_r = n_r;
+      mp.with_S = baryon ? 0 : 1;   // the baryon's matrix operand is the diquark
+      ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT, (double)nb * V3 * ((baryon ? 0.0 : 144.0) + 12.0 * n_r) * 8);
+      const size_t cS = ((size_t)V3 * 144 + kNarrowChunk - 1) / kNarrowChunk;
+      const size_t cV = ((size_t)V3 * 12 + kNarrowChunk - 1) / kNarrowChunk;
+      const size_t blocks = (size_t)(baryon ? 0 : nb) * cS + (size_t)n_r * nb * cV;
+      max_c64<<<(unsigned)blocks, 256, 0, st>>>(mp);
       note_launch();
     }
     // tensor maps of the matrix operand and the vector of this chunk of slices
@@ -942,7 +1071,7 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
       const float2 *GB = narrow ? reinterpret_cast<const float2 *>(ws + off_sb) : static_cast<const float2 *>(j0.SB);
       float2 *D = reinterpret_cast<float2 *>(ws + off_d);
       ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT, (double)V3 * (288.0 + 2304.0) * 8);
-      baryon_diquark<<<V3, 256, 0, st>>>(GA, GB, V3, D);
+      baryon_diquark<<<V3, 256, 0, st>>>(GA, GB, V3, D, maxD);
       note_launch();
       const uint64_t dims[3] = {768, 3, (uint64_t)V3}, strides[2] = {768 * 8, 2304 * 8};
       const uint32_t box[3] = {16, 3, 16};
@@ -979,6 +1108,95 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
   }
   LHC_CHECK_CUDA(cudaGetLastError());
   return LHC_OK;
+}
+
+// Candidate launch shapes of the autotuner: the distinct chunk widths NH that split the
+// representatives evenly (at least 16 unless fewer are needed; at most three, widest
+// first) and site splits from 1 to 16 that leave every split at least two k-step pairs.
+static void tune_candidates(int nrep, int npairs, std::vector<std::pair<int, int>> *out) {
+  std::vector<int> widths;
+  for (int w = RCHUNK; w >= 8 && (int)widths.size() < 3; w -= 8) {
+    const int nrc = (nrep + w - 1) / w, nh = ((nrep + nrc - 1) / nrc + 7) / 8 * 8;
+    if (nh < 16 && nrep > 8 && !widths.empty()) break;
+    if (std::find(widths.begin(), widths.end(), nh) == widths.end()) widths.push_back(nh);
+  }
+  static const int kSplits[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16};
+  for (int nh : widths)
+    for (int ns : kSplits)
+      if (ns == 1 || ns <= npairs / 2) out->emplace_back(nh, ns);
+}
+
+// Times every candidate shape on this call's own inputs (each run rewrites the outputs;
+// the last run uses the chosen shape) and stores the fastest.  Runs only outside stream
+// capture: it synchronizes the stream.
+static int autotune(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int nq, const int r[4], int sign,
+                    cudaStream_t st, const MomentumReps &reps, const TuneKey &key, TuneChoice *best) {
+  const int nkb = ((jobs[0].V3 + 2 * KSTEP - 1) / (2 * KSTEP)) * 2;
+  std::vector<std::pair<int, int>> cand;
+  tune_candidates(reps.nrep(), (nkb + 1) / 2, &cand);
+  cudaEvent_t e0, e1;
+  LHC_CHECK_CUDA(cudaEventCreate(&e0));
+  LHC_CHECK_CUDA(cudaEventCreate(&e1));
+  best->us = -1.f;
+  int status = LHC_OK;
+  for (const auto &c : cand) {
+    int s = run_mixed_shape(ctx, jobs, nt, k, nq, r, sign, st, reps, c.first, c.second);   // warm-up
+    if (s == LHC_EBUDGET || s == LHC_ENOMEM) continue;   // this shape does not fit: skip it
+    if (s != LHC_OK) {
+      status = s;
+      break;
+    }
+    cudaEventRecord(e0, st);
+    for (int rep = 0; rep < 2 && s == LHC_OK; ++rep) s = run_mixed_shape(ctx, jobs, nt, k, nq, r, sign, st, reps, c.first, c.second);
+    cudaEventRecord(e1, st);
+    if (s != LHC_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+      status = s != LHC_OK ? s : LHC_ECUDA;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const float us = ms * 500.f;   // per run
+    if (best->us < 0.f || us < best->us) *best = TuneChoice{c.first, c.second, us};
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (status != LHC_OK) return status;
+  if (best->us < 0.f) {
+    set_error("no launch shape of this call fits the memory budget");
+    return LHC_EBUDGET;
+  }
+  tune_store(key, *best);
+  return LHC_OK;
+}
+
+int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int nq, const int r[4], int sign,
+                   cudaStream_t st) {
+  const SliceJob &j0 = jobs[0];
+  const bool baryon = j0.part == PART_SPEC_BARYON;
+  const MomentumReps reps = momentum_reps(k, nq);
+  const int nkb = ((j0.V3 + 2 * KSTEP - 1) / (2 * KSTEP)) * 2;
+  const int nct = (baryon ? 48 : 3) * ((j0.n_r + 1) / 2);
+  // launch shape: the tuned one for this shape if known (or tuned now), else the heuristic
+  // (widest chunks; site splits that fill whole waves of one CTA per SM)
+  int nrc, NH;
+  rep_chunks(reps.nrep(), &nrc, &NH);
+  int nsplit = choose_nsplit(nct * nt * nrc, (nkb + 1) / 2, ctx->num_sms);
+  const TuneKey key{(int)j0.part, j0.dtype, j0.V3, j0.n_r, std::min(nt, kMaxSlices), reps.nrep()};
+  TuneChoice ch;
+  if (tune_lookup(key, &ch)) {
+    NH = ch.NH;
+    nsplit = ch.nsplit;
+  } else if (ctx->tune_mode == LHC_TUNE_ON) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    LHC_CHECK_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (cs == cudaStreamCaptureStatusNone) {
+      LHC_TRY(autotune(ctx, jobs, nt, k, nq, r, sign, st, reps, key, &ch));
+      NH = ch.NH;
+      nsplit = ch.nsplit;
+    }
+  }
+  if (const char *e = getenv("LHC_NSPLIT")) nsplit = std::max(1, std::min((nkb + 1) / 2, atoi(e)));
+  return run_mixed_shape(ctx, jobs, nt, k, nq, r, sign, st, reps, NH, nsplit);
 }
 
 }  // namespace lhc

@@ -108,6 +108,7 @@ struct lhc_ctx_s {
   int num_sms = 0;
   bool prof_on = false;
   int *dev_err = nullptr;                 // sticky device error word (bounded waits that gave up)
+  int tune_mode = 0;                      // lhc_tune_mode: time launch shapes of new shapes
   std::vector<lhc::ProfRecord> prof;
 };
 
@@ -134,6 +135,18 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
                    cudaStream_t st);
 
 size_t mixed_call_bytes(Part part, int dtype, int V3, int n_r, int nt, int nq);
+
+// launch-shape table of the mixed path (lhc_tune.cu): process-wide, guarded by a mutex
+struct TuneKey {
+  int part, dtype, V3, n_r, nt, nrep;   // nt: slices per launch
+  bool operator<(const TuneKey &o) const;
+};
+struct TuneChoice {
+  int NH, nsplit;   // representatives per CTA, site splits per slice
+  float us;         // measured time of one call with this shape
+};
+bool tune_lookup(const TuneKey &key, TuneChoice *out);
+void tune_store(const TuneKey &key, const TuneChoice &c);   // and rewrites the table file, if one is set
 
 // combine (k_combine.cu)
 int run_combine(lhc_ctx ctx, int kind, const double2 *spec, int np, const double2 *ins, int nq,

@@ -238,11 +238,45 @@ def test_misaligned_buffers_rejected(ctx):
     ctx.sync()
 
 
+@pytest.mark.parametrize("name,fs,fv", [
+    ("tiny", 1e-9, 1e-6),          # products near 1e-15: the unscaled FP16 split would flush them
+    ("huge", 3e3, 1e3),            # products near 1e7 (1e10 for the baryon): beyond FP16
+    ("decaying", None, 1.0),       # slice t scaled by exp(-0.9 |t|): 5 orders over the range
+])
+def test_dynamic_range(ctx, name, fs, fv):
+    """The FP16 split of the contracted values is scaled per slice by a power of two
+    bounded by the operands' maxima, so inputs far from unit magnitude keep the 1e-6
+    per-correlator bound: insertion over slices of different magnitude, meson and baryon
+    spectators, against the oracle."""
+    from oracle.momenta import momenta
+    from oracle import contractions as OC
+    c = CS.Case(4, 8, 2, momenta(2), seed=1700, r=(1, 2, 3, 0))
+    if fs is None:
+        w = np.exp(-0.9 * np.arange(8))
+        S, SB = c.S * w[:, None, None, None], c.SB * w[:, None, None, None]
+    else:
+        S, SB = c.S * fs, c.SB * fs
+    psi, eta = c.psi * fv, c.eta(6) * fv
+    g5 = CS.g5_matrix()
+    gi = ctx.insertion(dev(S), dev(psi), 0, 6, c.r, c.k, prec="mixed").cpu().numpy()
+    gs = ctx.spectator(dev(S), dev(eta), 6, c.r, c.k, prec="mixed").cpu().numpy()
+    gb = ctx.spectator(dev(S), dev(eta), 6, c.r, c.k, prec="mixed", GB=dev(SB)).cpu().numpy()
+    ctx.sync()
+    ri = OC.insertion(S[0:7], psi[:, 0:7], g5, c.r[:3], c.k, 4)
+    rs = OC.spectator_meson(S[6], eta, g5, c.r[:3], c.k, 4)
+    rb = OC.spectator_baryon(S[6], SB[6], eta, g5, c.r[:3], c.k, 4)
+    assert report(f"ins {name}", CS.block_err(gi, ri, 2)) < CS.MIXED_TOL
+    assert report(f"spec {name}", CS.block_err(gs, rs, 1)) < CS.MIXED_TOL
+    assert report(f"baryon {name}", CS.block_err(gb, rb, 1)) < CS.MIXED_TOL
+
+
 def test_complex128_staging_is_the_ieee_conversion(ctx):
     """complex128 inputs are staged to complex64 (round to nearest even); the
     mixed results must equal, bit for bit, those from the same inputs converted to
-    complex64 by torch (CUDA's IEEE conversion).  Magnitudes span 2^-12 .. 2^4 and a
-    quarter of the values sit exactly on a rounding tie."""
+    complex64 on the host by numpy (IEEE 754).  Magnitudes span 2^-12 .. 2^4, a quarter
+    of the values sit exactly on a rounding tie, and a few are zero or round to binary32
+    subnormals.  The results must also be finite: the baryon's products of three such
+    inputs exceed the FP16 range unless the split is scaled."""
     from oracle.momenta import momenta
     g = torch.Generator(device="cuda")
     g.manual_seed(77)
@@ -255,13 +289,20 @@ def test_complex128_staging_is_the_ieee_conversion(ctx):
         bits = x.view(torch.int64)
         tie = torch.rand(shape + (2,), device="cuda", generator=g) < 0.25
         bits = torch.where(tie, (bits & ~0x1FFFFFFF) | 0x10000000, bits)
-        return torch.view_as_complex(bits.view(torch.float64).contiguous())
+        x = bits.view(torch.float64)
+        # exact zeros and values whose binary32 result is subnormal (the conversion's
+        # other branch)
+        u = torch.rand(shape + (2,), device="cuda", generator=g)
+        x = torch.where(u < 0.02, torch.zeros_like(x), torch.where(u > 0.98, x * 2.0 ** -135, x))
+        return torch.view_as_complex(x.contiguous())
 
     S, SB = rough((T, V3, 12, 12)), rough((T, V3, 12, 12))
     psi, eta = rough((n_r, T, V3, 12)), rough((n_r, V3, 12))
     k = momenta(2)
     r = (1, 0, 2, 0)
-    c64 = lambda t: t.to(torch.complex64)
+    # the reference conversion is numpy's on the host: IEEE round to nearest even with
+    # gradual underflow
+    c64 = lambda t: torch.from_numpy(t.cpu().numpy().astype(np.complex64)).cuda()
     a = ctx.insertion(S, psi, 0, 3, r, k, prec="mixed")
     b = ctx.insertion(c64(S), c64(psi), 0, 3, r, k, prec="mixed")
     assert torch.equal(a, b)
@@ -271,4 +312,5 @@ def test_complex128_staging_is_the_ieee_conversion(ctx):
     a = ctx.spectator(S, eta, 1, r, k, prec="mixed", GB=SB)
     b = ctx.spectator(c64(S), c64(eta), 1, r, k, prec="mixed", GB=c64(SB))
     assert torch.equal(a, b)
+    assert bool(torch.isfinite(torch.view_as_real(a)).all())
     ctx.sync()
