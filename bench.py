@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the heuristic launch shapes instead of autotuning them during warm-up")
     ap.add_argument("--workload", default="meson24",
                     choices=["meson24", "baryon32", "batched", "serve", "mom1"],
                     help="meson24: the headline line; the others measure the further benchmark rows")
@@ -202,6 +204,7 @@ def main():
     etas = [torch.from_numpy(e).to(dev) for e in etas_h]
     G = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (g16, g4, gsrc)]
     ctx = lhc.Context(local)
+    ctx.set_tuning(not args.no_tune)   # new shapes are tuned in the first warm-up step
     st = torch.cuda.current_stream(dev)
 
     outs_ins = [torch.empty((tf + 1, nq, N_R, 192), dtype=torch.complex128, device=dev) for tf in TFS]
@@ -324,7 +327,11 @@ def main():
             "dtype": "f32+f16x2->f32 (mixed)" if args.prec == "mixed" else "f64",
             "data": "synthetic (seeded Philox Gaussian propagators/solutions, Z2xZ2 noise)",
             "config": {"workload": WORKLOAD, "precision": args.prec, "parallelism": f"replicas x{world}",
-                       "l2": "inputs (2.1 GB per step) larger than L2", "units_per_step": upstep},
+                       "l2": "inputs (2.1 GB per step) larger than L2", "units_per_step": upstep,
+                       "launch_shapes": "heuristic" if args.no_tune or args.prec != "mixed" else
+                       "autotuned in warm-up: " + "; ".join(
+                           f"part {r[0]} nt {r[4]}: NH {r[6]} x {r[5]} reps, {r[7]} splits"
+                           for r in lhc.tuning_table() if r[2] == L ** 3 and r[3] == N_R)},
             "clocks": clk, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": n_launches, "kernels": kernels,
         }))

@@ -266,6 +266,35 @@ int lhc_profile_read(lhc_ctx ctx, int kernel, double *total_ms, long long *launc
  * counted again).  Never fails; reading it costs one atomic load. */
 unsigned long long lhc_launch_count(void);
 
+/* ---- Free-field Wilson-Dirac operator and solver: inputs for end-to-end checks.
+ *
+ * The paper computes propagators and solutions on gauge configurations with a
+ * multigrid solver (Sec. 3). With unit gauge links the Wilson-Dirac operator
+ * (Wilson parameter 1, bare mass m) is
+ *   (D psi)(x) = (m + 4) psi(x)
+ *                - 1/2 sum_mu [ (1 - gamma_mu) psi(x + mu) + (1 + gamma_mu) psi(x - mu) ],
+ * colour-diagonal and periodic in all four directions (mu = x, y, z, t). Its inverse
+ * has a closed form, so point-to-all propagators G(x, r) (Eq. 1) and solutions
+ * s_i = D^{-1} eta_i (Eq. 5) made with it let the whole path be checked against an
+ * independent momentum-space evaluation.
+ *
+ * Fields are complex128 device arrays [nrhs][T][L^3][12] (spin*3 + colour), lat->dtype
+ * = LHC_C128. gammas: host double[4][4][4][2], gamma_mu[s][s'] (re, im) for
+ * mu = x, y, z, t. They must be Hermitian, and with gamma5 = g1 g2 g3 g4 diagonal, as
+ * in the default chiral basis, the results feed the other calls directly.
+ * Asynchronous on `stream`. Returns LHC_EINVAL for host fields or bad shapes. */
+/* out = D in (dagger = 0) or D^dagger in (dagger != 0: gamma_mu -> -gamma_mu). */
+int lhc_wilson_apply(lhc_ctx ctx, const lhc_lattice *lat, double mass, const double *gammas, int dagger,
+                     const void *in, void *out, int nrhs, void *stream);
+/* sol = D^{-1} src for nrhs right-hand sides: conjugate gradients on
+ * D^dagger D sol = D^dagger src, in FP64, until |D^dagger r| <= tol |D^dagger src| for
+ * every right-hand side or maxiter iterations. Synchronizes `stream` once per
+ * iteration; allocates its three work fields from the context's budget.
+ * *iters = iterations, *relres = max over right-hand sides of |src - D sol| / |src|
+ * (either may be NULL). */
+int lhc_wilson_solve(lhc_ctx ctx, const lhc_lattice *lat, double mass, const double *gammas, const void *src,
+                     void *sol, int nrhs, double tol, int maxiter, int *iters, double *relres, void *stream);
+
 /* ---- Launch-shape autotuning of the LHC_MIXED path.  The paper has no counterpart:
  * its kernels were tuned by hand for one machine.
  *

@@ -11,6 +11,7 @@
 // average of Eq. 5) is exact: each noise's term is added with Knuth's TwoSum into an
 // unevaluated FP32 pair hi + lo, rounded once to FP64 (no less accurate than FP64
 // accumulation, and it keeps GB300's slow FP64 pipe out of the inner loop).
+#include <algorithm>
 #include <type_traits>
 
 #include "conv.cuh"
@@ -57,20 +58,24 @@ __device__ __forceinline__ void stage_rows(cplx<R> *dst, const double2 *src, int
 }
 
 // CTA per (t, q): Xi[t][g][q][i,al,a] = sum_b Gsrc[g][b][al] sum_{at,bt} Gins[g][at][bt] I[t][q][i][at,bt,b,a]
+// The noises of the block are staged nch at a time (as many as fit the shared memory the
+// host grants), after the Gamma matrices.
 template <typename R>
-__global__ void comb_ins_meson(const double2 *__restrict__ I, int nq, int n_r, const double2 *__restrict__ Gins,
+__global__ void comb_ins_meson(const double2 *__restrict__ I, int nq, int n_r, int nch, const double2 *__restrict__ Gins,
                                const double2 *__restrict__ Gsrc, int ng, cplx<R> *__restrict__ Xi) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  cplx<R> *sI = reinterpret_cast<cplx<R> *>(sm_raw);
-  cplx<R> *sGi = sI + n_r * SROW, *sGc = sGi + ng * 16;
+  cplx<R> *sGi = reinterpret_cast<cplx<R> *>(sm_raw), *sGc = sGi + ng * 16, *sI = sGc + ng * 16;
   const int tq = blockIdx.x, t = tq / nq, q = tq % nq;
-  stage_rows(sI, I + (size_t)tq * n_r * 192, n_r);
   stage(sGi, Gins, ng * 16);
   stage(sGc, Gsrc, ng * 16);
+  for (int i0 = 0; i0 < n_r; i0 += nch) {
+  const int nc = min(nch, n_r - i0);
   __syncthreads();
-  for (int task = threadIdx.x; task < ng * n_r * 3; task += blockDim.x) {
-    const int a = task % 3, i = (task / 3) % n_r, g = task / (3 * n_r);
-    const cplx<R> *v = sI + i * SROW, *Gi = sGi + g * 16, *Gc = sGc + g * 16;
+  stage_rows(sI, I + ((size_t)tq * n_r + i0) * 192, nc);
+  __syncthreads();
+  for (int task = threadIdx.x; task < ng * nc * 3; task += blockDim.x) {
+    const int a = task % 3, ii = (task / 3) % nc, g = task / (3 * nc), i = i0 + ii;
+    const cplx<R> *v = sI + ii * SROW, *Gi = sGi + g * 16, *Gc = sGc + g * 16;
     cplx<R> T[4];
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
@@ -89,22 +94,25 @@ __global__ void comb_ins_meson(const double2 *__restrict__ I, int nq, int n_r, c
       o[al * 3] = acc;
     }
   }
+  }
 }
 
 // CTA per (t, q): Xi[t][g][q][i,b,c] = sum_{at,bt} Gins[g][at][bt] I[t][q][i][at,bt,b,c]
 template <typename R>
-__global__ void comb_ins_baryon(const double2 *__restrict__ I, int nq, int n_r, const double2 *__restrict__ Gins,
+__global__ void comb_ins_baryon(const double2 *__restrict__ I, int nq, int n_r, int nch, const double2 *__restrict__ Gins,
                                 int ng, cplx<R> *__restrict__ Xi) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  cplx<R> *sI = reinterpret_cast<cplx<R> *>(sm_raw);
-  cplx<R> *sGi = sI + n_r * SROW;
+  cplx<R> *sGi = reinterpret_cast<cplx<R> *>(sm_raw), *sI = sGi + 2 * ng * 16;
   const int tq = blockIdx.x, t = tq / nq, q = tq % nq;
-  stage_rows(sI, I + (size_t)tq * n_r * 192, n_r);
   stage(sGi, Gins, ng * 16);
+  for (int i0 = 0; i0 < n_r; i0 += nch) {
+  const int nc = min(nch, n_r - i0);
   __syncthreads();
-  for (int task = threadIdx.x; task < ng * n_r * 3; task += blockDim.x) {
-    const int c = task % 3, i = (task / 3) % n_r, g = task / (3 * n_r);
-    const cplx<R> *v = sI + i * SROW, *Gi = sGi + g * 16;
+  stage_rows(sI, I + ((size_t)tq * n_r + i0) * 192, nc);
+  __syncthreads();
+  for (int task = threadIdx.x; task < ng * nc * 3; task += blockDim.x) {
+    const int c = task % 3, ii = (task / 3) % nc, g = task / (3 * nc), i = i0 + ii;
+    const cplx<R> *v = sI + ii * SROW, *Gi = sGi + g * 16;
     cplx<R> *o = Xi + (((size_t)t * ng + g) * nq + q) * 12 * n_r + i * 12 + c;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
@@ -116,22 +124,25 @@ __global__ void comb_ins_baryon(const double2 *__restrict__ I, int nq, int n_r, 
       o[b * 3] = acc;
     }
   }
+  }
 }
 
 // CTA per p: Xs[g][p][i,al,a] = sum_{ap,bp} Gsnk[g][ap][bp] S[p][i][bp,ap,al,a]
 template <typename R>
-__global__ void comb_spec_meson(const double2 *__restrict__ S, int np, int n_r, const double2 *__restrict__ Gsnk,
+__global__ void comb_spec_meson(const double2 *__restrict__ S, int np, int n_r, int nch, const double2 *__restrict__ Gsnk,
                                 int ng, cplx<R> *__restrict__ Xs) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  cplx<R> *sS = reinterpret_cast<cplx<R> *>(sm_raw);
-  cplx<R> *sG = sS + n_r * SROW;
+  cplx<R> *sG = reinterpret_cast<cplx<R> *>(sm_raw), *sS = sG + 2 * ng * 16;
   const int p = blockIdx.x;
-  stage_rows(sS, S + (size_t)p * n_r * 192, n_r);
   stage(sG, Gsnk, ng * 16);
+  for (int i0 = 0; i0 < n_r; i0 += nch) {
+  const int nc = min(nch, n_r - i0);
   __syncthreads();
-  for (int task = threadIdx.x; task < ng * n_r * 3; task += blockDim.x) {
-    const int a = task % 3, i = (task / 3) % n_r, g = task / (3 * n_r);
-    const cplx<R> *s = sS + i * SROW, *G = sG + g * 16;
+  stage_rows(sS, S + ((size_t)p * n_r + i0) * 192, nc);
+  __syncthreads();
+  for (int task = threadIdx.x; task < ng * nc * 3; task += blockDim.x) {
+    const int a = task % 3, ii = (task / 3) % nc, g = task / (3 * nc), i = i0 + ii;
+    const cplx<R> *s = sS + ii * SROW, *G = sG + g * 16;
     cplx<R> *o = Xs + ((size_t)g * np + p) * 12 * n_r + i * 12 + a;
 #pragma unroll
     for (int al = 0; al < 4; ++al) {
@@ -142,6 +153,7 @@ __global__ void comb_spec_meson(const double2 *__restrict__ S, int np, int n_r, 
         for (int bp = 0; bp < 4; ++bp) cfma(acc, G[ap * 4 + bp], s[bp * 48 + ap * 12 + al * 3 + a]);
       o[al * 3] = acc;
     }
+  }
   }
 }
 
@@ -287,11 +299,15 @@ int launch_combine(int kind, const double2 *spec, int np, const double2 *ins, in
                    double2 *out, cudaStream_t st) {
   cplx<R> *Xs = static_cast<cplx<R> *>(scratch);
   cplx<R> *Xi = Xs + (size_t)ng * np * 12 * n_r;
-  const size_t smem = ((size_t)n_r * SROW + 2 * ng * 16) * sizeof(cplx<R>);
-  if (smem > 200 * 1024) {
-    set_error("combine block of %d noises and %d Gamma structures does not fit shared memory", n_r, ng);
+  // noises staged per pass: as many as fit 96 KB next to the Gamma matrices (two CTAs
+  // per SM), at least one
+  const size_t g_bytes = (size_t)2 * ng * 16 * sizeof(cplx<R>), row = (size_t)SROW * sizeof(cplx<R>);
+  if (g_bytes + row > 200 * 1024) {
+    set_error("combine: %d Gamma structures do not fit shared memory", ng);
     return LHC_EINVAL;
   }
+  const int nch = (int)std::min<size_t>((size_t)n_r, g_bytes + row <= 96 * 1024 ? (96 * 1024 - g_bytes) / row : 1);
+  const size_t smem = g_bytes + (size_t)nch * row;
   if (smem > 48 * 1024) {
     static bool attr[4] = {false, false, false, false};
     if (!attr[0]) {
@@ -302,15 +318,15 @@ int launch_combine(int kind, const double2 *spec, int np, const double2 *ins, in
     }
   }
   if (kind == LHC_MESON) {
-    comb_spec_meson<R><<<np, 256, smem, st>>>(spec, np, n_r, snk, ng, Xs);
+    comb_spec_meson<R><<<np, 256, smem, st>>>(spec, np, n_r, nch, snk, ng, Xs);
     note_launch();
-    comb_ins_meson<R><<<nt * nq, 256, smem, st>>>(ins, nq, n_r, ins_g, src, ng, Xi);
+    comb_ins_meson<R><<<nt * nq, 256, smem, st>>>(ins, nq, n_r, nch, ins_g, src, ng, Xi);
     note_launch();
   } else {
     size_t ns = (size_t)ng * np * n_r * 3;
     comb_spec_baryon<R><<<blocks(ns, 128), 128, 0, st>>>(spec, np, n_r, snk, src, ng, Xs);
     note_launch();
-    comb_ins_baryon<R><<<nt * nq, 256, smem, st>>>(ins, nq, n_r, ins_g, ng, Xi);
+    comb_ins_baryon<R><<<nt * nq, 256, smem, st>>>(ins, nq, n_r, nch, ins_g, ng, Xi);
     note_launch();
   }
   dim3 grid((nq + TQ - 1) / TQ, (np + TP - 1) / TP, nt * ng);

@@ -95,7 +95,14 @@ def lib():
         L.lhc_profile.argtypes = [vp, ci]
         L.lhc_profile_read.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
-        for name in ("lhc_create", "lhc_destroy", "lhc_set_gamma5", "lhc_momenta", "lhc_insertion",
+        L.lhc_wilson_apply.argtypes = [vp, lp, ctypes.c_double, vp, ci, vp, vp, ci, vp]
+        L.lhc_wilson_solve.argtypes = [vp, lp, ctypes.c_double, vp, vp, vp, ci, ctypes.c_double, ci, ip,
+                                       ctypes.POINTER(ctypes.c_double), vp]
+        L.lhc_set_tuning.argtypes = [vp, ci, ctypes.c_char_p]
+        L.lhc_tuning_table.argtypes = [ip, ci, ip]
+        L.lhc_tuning_load.argtypes = [ctypes.c_char_p, ip]
+        for name in ("lhc_wilson_apply", "lhc_wilson_solve", "lhc_set_tuning", "lhc_tuning_table", "lhc_tuning_load",
+                     "lhc_create", "lhc_destroy", "lhc_set_gamma5", "lhc_momenta", "lhc_insertion",
                      "lhc_spectator", "lhc_combine", "lhc_profile", "lhc_profile_read", "lhc_sync", "lhc_release_workspace",
                      "lhc_selftest_timeout", "lhc_serve_start", "lhc_serve_stop", "lhc_prop_register",
                      "lhc_prop_release", "lhc_submit", "lhc_poll", "lhc_wait", "lhc_cancel", "lhc_job_times",
@@ -113,6 +120,26 @@ def _check(status):
 def launch_count() -> int:
     """Kernel launches this library has issued since it was loaded (graph replays excluded)."""
     return int(lib().lhc_launch_count())
+
+
+TUNE_OFF, TUNE_ON = 0, 1
+
+
+def tuning_table() -> np.ndarray:
+    """The process-wide launch-shape table: int [n][8] rows (part, dtype, V3, n_r, nt,
+    nrep, NH, nsplit)."""
+    n = ctypes.c_int(0)
+    _check(lib().lhc_tuning_table(None, 0, ctypes.byref(n)))
+    t = np.zeros((max(n.value, 1), 8), dtype=np.int32)
+    _check(lib().lhc_tuning_table(t.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), n.value, ctypes.byref(n)))
+    return t[:n.value]
+
+
+def tuning_load(path: str) -> int:
+    """Load a launch-shape table file into the process-wide table (no GPU needed)."""
+    n = ctypes.c_int(0)
+    _check(lib().lhc_tuning_load(str(path).encode(), ctypes.byref(n)))
+    return n.value
 
 
 def momenta(n2max: int, cmax: int = -1) -> np.ndarray:
@@ -208,6 +235,44 @@ class Context:
         ms, n, w = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
         _check(lib().lhc_profile_read(self._h, kernel, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)))
         return ms.value, n.value, w.value
+
+    def set_tuning(self, enable: bool, path=None):
+        """Autotune the launch shape of each new mixed-precision shape on its first call
+        (which then synchronizes its stream); path: optional table file, loaded now and
+        rewritten after each new entry."""
+        _check(lib().lhc_set_tuning(self._h, TUNE_ON if enable else TUNE_OFF,
+                                    None if path is None else str(path).encode()))
+
+    def _wilson_args(self, field, gammas):
+        if field.dtype != torch.complex128 or not field.is_cuda or field.dim() != 4 or field.shape[-1] != 12:
+            raise ValueError("fields are complex128 CUDA tensors [nrhs][T][L^3][12]")
+        nrhs, T, V3 = field.shape[0], field.shape[1], field.shape[2]
+        L = round(V3 ** (1 / 3))
+        if L ** 3 != V3:
+            raise ValueError("L^3 sites per timeslice expected")
+        g = np.ascontiguousarray(np.asarray(gammas, dtype=np.complex128).reshape(4, 4, 4))
+        return Lattice(L, T, C128), nrhs, g
+
+    def wilson_apply(self, field, mass, gammas, dagger=False, out=None, stream=None):
+        """D field (or D^dagger field) for the free (unit-link) Wilson-Dirac operator."""
+        lat, nrhs, g = self._wilson_args(field, gammas)
+        field = field.contiguous()
+        out = torch.empty_like(field) if out is None else out
+        _check(lib().lhc_wilson_apply(self._h, ctypes.byref(lat), float(mass), g.ctypes.data, 1 if dagger else 0,
+                                      _ptr(field), _ptr(out), nrhs, _stream(field, stream)))
+        return out
+
+    def wilson_solve(self, src, mass, gammas, tol=1e-12, maxiter=2000, stream=None):
+        """D^{-1} src (free Wilson-Dirac operator, CG on the normal equations);
+        returns (solution, iterations, max relative residual |src - D sol| / |src|)."""
+        lat, nrhs, g = self._wilson_args(src, gammas)
+        src = src.contiguous()
+        sol = torch.empty_like(src)
+        it, res = ctypes.c_int(0), ctypes.c_double(0.0)
+        _check(lib().lhc_wilson_solve(self._h, ctypes.byref(lat), float(mass), g.ctypes.data, _ptr(src), _ptr(sol),
+                                      nrhs, float(tol), int(maxiter), ctypes.byref(it), ctypes.byref(res),
+                                      _stream(src, stream)))
+        return sol, it.value, res.value
 
     def set_gamma5(self, g5):
         self._g5, p = _ints(g5, 4)
