@@ -26,11 +26,18 @@
  *
  * Memory: every buffer argument may be device memory or host memory (pinned or
  * pageable), and must be 16-byte aligned (the kernels move complex64 data in 16-byte
- * copies); misaligned buffers return LHC_EINVAL.  Host buffers are staged through the context's workspace; a call
- * that touches any host buffer synchronizes its stream before it returns.  With
- * only device buffers a call is asynchronous on `stream` (a cudaStream_t; NULL =
- * legacy default stream).  The caller owns every buffer it passes; the library
- * never frees them.  The library owns its workspace and its cached phase tables,
+ * copies); misaligned buffers return LHC_EINVAL.  Every call is asynchronous on `stream`
+ * (a cudaStream_t; NULL = legacy default stream), with device or host buffers alike.
+ * Host buffers are staged through two device slots that alternate between calls: the
+ * input copies run on a copy stream of the context and overlap the kernels of the
+ * previous call, and the output copy runs on a second copy stream that `stream` waits
+ * for.  So once `stream` (or the device) is synchronized after a call, its host output
+ * is written and its host inputs have been read; until then the caller must not change
+ * the inputs or read the output.  A later call may take an earlier call's host output
+ * as its input: the library tracks host ranges that output copies in flight will write
+ * and orders the copies.  Pinned host memory gives overlap; pageable memory is copied
+ * synchronously by CUDA.  The caller owns every buffer it passes; the library never
+ * frees them.  The library owns its workspace and its cached phase tables,
  * both counted against the context's HBM budget.
  *
  * Errors: every call returns an lhc_status; nothing is thrown across the ABI.

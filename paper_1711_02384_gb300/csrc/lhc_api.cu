@@ -195,6 +195,110 @@ struct CtxSync {
 static std::map<lhc_ctx, CtxSync> g_sync;
 static std::mutex g_sync_mu;
 
+// ---------------------------------------------------------------- host staging
+// A call with host buffers takes the next of kStageSlots staging slots.  Its input
+// copies run on the slot's H2D stream as soon as the slot is free (the call kStageSlots
+// back has finished with it) and any output copy in flight into the same host memory has
+// landed; the caller's stream waits for them, runs the kernels, and the D2H stream
+// copies the output back, which the caller's stream waits for in turn.  So the copies of
+// one call overlap the kernels of the ones before, and a stream or device synchronize
+// still covers all.
+static int stage_streams(lhc_ctx ctx) {
+  if (ctx->d2h) return LHC_OK;
+  for (int s = 0; s < lhc_ctx_s::kStageSlots; ++s) {
+    LHC_CHECK_CUDA(cudaStreamCreateWithFlags(&ctx->h2d[s], cudaStreamNonBlocking));
+    LHC_CHECK_CUDA(cudaEventCreateWithFlags(&ctx->slot_free[s], cudaEventDisableTiming));
+    LHC_CHECK_CUDA(cudaEventCreateWithFlags(&ctx->in_ready[s], cudaEventDisableTiming));
+  }
+  LHC_CHECK_CUDA(cudaEventCreateWithFlags(&ctx->comp_done, cudaEventDisableTiming));
+  LHC_CHECK_CUDA(cudaStreamCreateWithFlags(&ctx->d2h, cudaStreamNonBlocking));
+  return LHC_OK;
+}
+
+// Takes a staging slot of at least `bytes`; *base is its device address.
+static int stage_begin(lhc_ctx ctx, size_t bytes, int *slot, char **base) {
+  LHC_TRY(stage_streams(ctx));
+  const int s = ctx->next_slot;
+  ctx->next_slot = (s + 1) % lhc_ctx_s::kStageSlots;
+  if (ctx->slot_used[s]) LHC_CHECK_CUDA(cudaStreamWaitEvent(ctx->h2d[s], ctx->slot_free[s], 0));
+  LHC_TRY(ensure(ctx, ctx->stage[s], bytes));   // growing synchronizes the device first
+  *slot = s;
+  *base = static_cast<char *>(ctx->stage[s].p);
+  return LHC_OK;
+}
+
+// Host -> slot copy on the slot's H2D stream, after any output copy still writing that
+// memory.
+static int stage_in(lhc_ctx ctx, int slot, void *dst, const void *src, size_t bytes) {
+  const char *a = static_cast<const char *>(src);
+  for (auto it = ctx->pending_out.begin(); it != ctx->pending_out.end();) {
+    if (cudaEventQuery(it->ev) == cudaSuccess) {   // landed: forget it
+      ctx->event_pool.push_back(it->ev);
+      it = ctx->pending_out.erase(it);
+      continue;
+    }
+    cudaGetLastError();   // cudaErrorNotReady is not an error here
+    if (a < it->p + it->n && it->p < a + bytes) LHC_CHECK_CUDA(cudaStreamWaitEvent(ctx->h2d[slot], it->ev, 0));
+    ++it;
+  }
+  LHC_CHECK_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->h2d[slot]));
+  return LHC_OK;
+}
+
+// The kernels on `st` may start once the inputs have landed.
+static int stage_ready(lhc_ctx ctx, int slot, cudaStream_t st) {
+  LHC_CHECK_CUDA(cudaEventRecord(ctx->in_ready[slot], ctx->h2d[slot]));
+  LHC_CHECK_CUDA(cudaStreamWaitEvent(st, ctx->in_ready[slot], 0));
+  return LHC_OK;
+}
+
+// After the kernels: copy the output back (if it is host memory) and release the slot.
+static int stage_end(lhc_ctx ctx, int slot, cudaStream_t st, void *host_out, const void *dev_out, size_t bytes) {
+  if (host_out) {
+    LHC_CHECK_CUDA(cudaEventRecord(ctx->comp_done, st));
+    LHC_CHECK_CUDA(cudaStreamWaitEvent(ctx->d2h, ctx->comp_done, 0));
+    LHC_CHECK_CUDA(cudaMemcpyAsync(host_out, dev_out, bytes, cudaMemcpyDeviceToHost, ctx->d2h));
+    LHC_CHECK_CUDA(cudaEventRecord(ctx->slot_free[slot], ctx->d2h));
+    LHC_CHECK_CUDA(cudaStreamWaitEvent(st, ctx->slot_free[slot], 0));   // the caller's stream covers the copy
+    cudaEvent_t ev;
+    if (ctx->event_pool.empty()) {
+      LHC_CHECK_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    } else {
+      ev = ctx->event_pool.back();
+      ctx->event_pool.pop_back();
+    }
+    LHC_CHECK_CUDA(cudaEventRecord(ev, ctx->d2h));
+    ctx->pending_out.push_back({static_cast<const char *>(host_out), bytes, ev});
+  } else {
+    LHC_CHECK_CUDA(cudaEventRecord(ctx->slot_free[slot], st));
+  }
+  ctx->slot_used[slot] = true;
+  return LHC_OK;
+}
+
+static void stage_release(lhc_ctx ctx) {
+  for (int s = 0; s < lhc_ctx_s::kStageSlots; ++s) dev_free(ctx, ctx->stage[s]);
+}
+
+static void stage_destroy(lhc_ctx ctx) {
+  stage_release(ctx);
+  for (auto &po : ctx->pending_out) cudaEventDestroy(po.ev);
+  for (auto ev : ctx->event_pool) cudaEventDestroy(ev);
+  ctx->pending_out.clear();
+  ctx->event_pool.clear();
+  if (ctx->d2h) {
+    for (int s = 0; s < lhc_ctx_s::kStageSlots; ++s) {
+      cudaStreamDestroy(ctx->h2d[s]);
+      cudaEventDestroy(ctx->slot_free[s]);
+      cudaEventDestroy(ctx->in_ready[s]);
+      ctx->h2d[s] = nullptr;
+    }
+    cudaStreamDestroy(ctx->d2h);
+    cudaEventDestroy(ctx->comp_done);
+    ctx->d2h = nullptr;
+  }
+}
+
 static int begin_call(lhc_ctx ctx, cudaStream_t st) {
   LHC_CHECK_CUDA(cudaSetDevice(ctx->device));
   std::lock_guard<std::mutex> g(g_sync_mu);
@@ -271,7 +375,7 @@ int lhc_destroy(lhc_ctx ctx) {
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   dev_free(ctx, ctx->ws);
-  dev_free(ctx, ctx->stage);
+  stage_destroy(ctx);
   if (ctx->dev_err) cudaFree(ctx->dev_err);
   for (auto &kv : ctx->phases) dev_free(ctx, kv.second.buf);
   for (auto &r : ctx->prof) {
@@ -296,7 +400,7 @@ int lhc_release_workspace(lhc_ctx ctx) {
   LHC_CHECK_CUDA(cudaSetDevice(ctx->device));
   LHC_CHECK_CUDA(cudaDeviceSynchronize());
   dev_free(ctx, ctx->ws);
-  dev_free(ctx, ctx->stage);
+  stage_release(ctx);
   for (auto &kv : ctx->phases) dev_free(ctx, kv.second.buf);
   ctx->phases.clear();
   ctx->phase_lru.clear();
@@ -425,22 +529,25 @@ int run_part(lhc_ctx ctx, const PartCall &c, cudaStream_t st) {
   size_t bV = hV ? (size_t)c.n_r * nvt * vec_slice * es : 0;
   size_t bO = hO ? out_bytes : 0;
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  if (any_host) LHC_TRY(ensure(ctx, ctx->stage, al(bS) + al(bSB) + al(bV) + al(bO)));
-  char *sp = static_cast<char *>(ctx->stage.p);
+  int slot = -1;
+  char *sp = nullptr;
+  if (any_host) LHC_TRY(stage_begin(ctx, al(bS) + al(bSB) + al(bV) + al(bO), &slot, &sp));
   const char *S = static_cast<const char *>(c.S), *SB = static_cast<const char *>(c.SB),
              *V = static_cast<const char *>(c.vec);
   size_t S_tstride = slice_elems * es;   // bytes between slices
+  // the call's slices t0 .. t0+nt-1 (mod T) as runs of consecutive t: one copy per run
+  std::vector<std::pair<int, int>> runs;   // (first j, length)
+  for (int j = 0; j < c.nt;) {
+    const int t = (c.t0 + j) % T, len = std::min(c.nt - j, T - t);
+    runs.emplace_back(j, len);
+    j += len;
+  }
   if (hS || hSB) {
-    // copy the needed slices into [nt][V3][144]
-    for (int j = 0; j < c.nt; ++j) {
-      int t = (c.t0 + j) % T;
-      if (hS)
-        LHC_CHECK_CUDA(cudaMemcpyAsync(sp + j * slice_elems * es, S + (size_t)t * slice_elems * es,
-                                       slice_elems * es, cudaMemcpyHostToDevice, st));
-      if (hSB)
-        LHC_CHECK_CUDA(cudaMemcpyAsync(sp + al(bS) + j * slice_elems * es,
-                                       SB + (size_t)t * slice_elems * es, slice_elems * es,
-                                       cudaMemcpyHostToDevice, st));
+    // the needed slices, as [nt][V3][144]
+    for (const auto &rn : runs) {
+      const size_t t = (size_t)((c.t0 + rn.first) % T), n = (size_t)rn.second * S_tstride;
+      if (hS) LHC_TRY(stage_in(ctx, slot, sp + rn.first * S_tstride, S + t * S_tstride, n));
+      if (hSB) LHC_TRY(stage_in(ctx, slot, sp + al(bS) + rn.first * S_tstride, SB + t * S_tstride, n));
     }
   }
   const char *Sd = hS ? sp : S;
@@ -451,19 +558,23 @@ int run_part(lhc_ctx ctx, const PartCall &c, cudaStream_t st) {
   bool v_staged = false;
   if (hV) {
     char *dst = sp + al(bS) + al(bSB);
-    for (int i = 0; i < c.n_r; ++i)
-      for (size_t j = 0; j < nvt; ++j) {
-        size_t t = c.vec_has_time ? (size_t)((c.t0 + (int)j) % T) : 0;
-        size_t src_off = c.vec_has_time ? ((size_t)i * T + t) * vec_slice : (size_t)i * vec_slice;
-        LHC_CHECK_CUDA(cudaMemcpyAsync(dst + (i * nvt + j) * vec_slice * es, V + src_off * es,
-                                       vec_slice * es, cudaMemcpyHostToDevice, st));
-      }
+    if (!c.vec_has_time) {   // eta: [n_r][V3][12], one block
+      LHC_TRY(stage_in(ctx, slot, dst, V, (size_t)c.n_r * vec_slice * es));
+    } else {   // psi: per noise, the runs of slices
+      for (int i = 0; i < c.n_r; ++i)
+        for (const auto &rn : runs) {
+          const size_t t = (size_t)((c.t0 + rn.first) % T);
+          LHC_TRY(stage_in(ctx, slot, dst + ((size_t)i * nvt + rn.first) * vec_slice * es,
+                           V + ((size_t)i * T + t) * vec_slice * es, (size_t)rn.second * vec_slice * es));
+        }
+    }
     Vd = dst;
     v_noise_stride = nvt * vec_slice;
     v_staged = true;
   }
   double2 *Od = hO ? reinterpret_cast<double2 *>(sp + al(bS) + al(bSB) + al(bV))
                    : static_cast<double2 *>(c.out);
+  if (any_host) LHC_TRY(stage_ready(ctx, slot, st));
 
   const double2 *phase = nullptr;
   if (c.prec == LHC_FP64) LHC_TRY(get_phase_f64(ctx, L, c.k, c.nq, c.r, c.sign, st, &phase));
@@ -488,10 +599,7 @@ int run_part(lhc_ctx ctx, const PartCall &c, cudaStream_t st) {
     if (c.prec == LHC_FP64) LHC_TRY(run_slice_f64(ctx, job, phase, st));
   }
   if (c.prec == LHC_MIXED) LHC_TRY(run_part_mixed(ctx, jobs.data(), c.nt, c.k, c.nq, c.r, c.sign, st));
-  if (hO) {
-    LHC_CHECK_CUDA(cudaMemcpyAsync(c.out, Od, out_bytes, cudaMemcpyDeviceToHost, st));
-  }
-  if (any_host) LHC_CHECK_CUDA(cudaStreamSynchronize(st));
+  if (any_host) LHC_TRY(stage_end(ctx, slot, st, hO ? c.out : nullptr, Od, out_bytes));
   return LHC_OK;
 }
 
@@ -571,40 +679,28 @@ int lhc_combine(lhc_ctx ctx, int kind, const void *spec, int np, const void *ins
     any |= host[j];
     if (host[j]) need += al(bytes[j]);
   }
-  int s = LHC_OK;
+  int s = LHC_OK, slot = -1;
   const void *dev[6];
-  if (any) s = ensure(ctx, ctx->stage, need);
+  char *sp = nullptr;
+  if (any) s = stage_begin(ctx, need, &slot, &sp);
   if (s == LHC_OK) {
-    char *sp = static_cast<char *>(ctx->stage.p);
     size_t off = 0;
-    for (int j = 0; j < 6; ++j) {
+    for (int j = 0; j < 6 && s == LHC_OK; ++j) {
       if (host[j]) {
         dev[j] = sp + off;
-        if (j < 5) {
-          cudaError_t e = cudaMemcpyAsync(sp + off, ptr[j], bytes[j], cudaMemcpyHostToDevice, st);
-          if (e != cudaSuccess) {
-            s = fail(LHC_ECUDA, "staging copy: %s", cudaGetErrorString(e));
-            break;
-          }
-        }
+        if (j < 5) s = stage_in(ctx, slot, sp + off, ptr[j], bytes[j]);
         off += al(bytes[j]);
       } else {
         dev[j] = ptr[j];
       }
     }
   }
+  if (s == LHC_OK && any) s = stage_ready(ctx, slot, st);
   if (s == LHC_OK)
     s = run_combine(ctx, kind, (const double2 *)dev[0], np, (const double2 *)dev[1], nq, n_r, nt,
                     (const double2 *)dev[2], (const double2 *)dev[3], (const double2 *)dev[4], ng, prec,
                     (double2 *)dev[5], st);
-  if (s == LHC_OK && host[5]) {
-    cudaError_t e = cudaMemcpyAsync(out, dev[5], b_out, cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) s = fail(LHC_ECUDA, "output copy: %s", cudaGetErrorString(e));
-  }
-  if (s == LHC_OK && any) {
-    cudaError_t e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) s = fail(LHC_ECUDA, "stream sync: %s", cudaGetErrorString(e));
-  }
+  if (s == LHC_OK && any) s = stage_end(ctx, slot, st, host[5] ? out : nullptr, dev[5], b_out);
   int e2 = end_call(ctx, st);
   return s != LHC_OK ? s : e2;
 }

@@ -102,7 +102,24 @@ struct lhc_ctx_s {
   int g5[4] = {1, 1, -1, -1};
   std::mutex mu;
   lhc::DevBuf ws;                         // general workspace (grown on demand)
-  lhc::DevBuf stage;                      // host-staging buffer
+  // Host-buffer staging: kStageSlots device slots used by successive calls in turn, each
+  // with its own H2D copy stream (a call's copies wait for nothing but its own slot and
+  // its own host dependencies), one D2H copy stream, and the host ranges that output
+  // copies still in flight will write (a later call reading such a range waits for
+  // that copy).
+  static constexpr int kStageSlots = 4;
+  lhc::DevBuf stage[kStageSlots];
+  cudaStream_t h2d[kStageSlots] = {}, d2h = nullptr;
+  cudaEvent_t slot_free[kStageSlots] = {}, in_ready[kStageSlots] = {}, comp_done = nullptr;
+  bool slot_used[kStageSlots] = {};
+  int next_slot = 0;
+  struct PendingOut {
+    const char *p;
+    size_t n;
+    cudaEvent_t ev;
+  };
+  std::vector<PendingOut> pending_out;
+  std::vector<cudaEvent_t> event_pool;
   std::map<lhc::PhaseKey, lhc::PhaseEntry> phases;
   std::list<lhc::PhaseKey> phase_lru;     // front = most recent
   int num_sms = 0;
