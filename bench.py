@@ -127,6 +127,24 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+# --------------------------------------------------------------------------- replicas
+
+def max_over_ranks(x, world, device="cpu"):
+    """The largest x over the ranks of the job: the slowest replica's time is the job's."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_step, steps, world, ms):
+    """Whole-job throughput: the units every replica processed over the slowest one's time."""
+    return units_per_step * steps * world / (ms / 1e3)
+
+
 # --------------------------------------------------------------------------- reference arm / cpu baseline
 
 def oracle_sample(S, psis, etas, k):
@@ -237,12 +255,9 @@ def main():
     clk = clocks.stop()
     n_launches = lhc.launch_count() - n_launch0
     ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     upstep = units_per_step(nq)
-    value = upstep * args.steps * world / (ms / 1e3)
+    value = job_value(upstep, args.steps, world, ms)
 
     # dominant kernel: timed with CUDA events on its own stream by the library
     kern = lhc.KERNEL_FUSED if args.prec == "mixed" else lhc.KERNEL_PROJECT

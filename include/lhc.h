@@ -273,6 +273,24 @@ int lhc_profile_read(lhc_ctx ctx, int kernel, double *total_ms, long long *launc
  * counted again).  Never fails; reading it costs one atomic load. */
 unsigned long long lhc_launch_count(void);
 
+/* Open-source-spin combine (meson): Eq. 8 with the source Gamma left open,
+ *
+ *   out[t][gs][gi][p][q][al*4 + be]
+ *     = (1/N) sum_i sum_a Shat_i[gs](p)[al*3 + a] Ihat_i[t][gi](q)[be*3 + a],
+ *   Shat_i[gs] = sum_{ap,bp} Gsnk[gs][ap][bp] spec_i[(bp*4 + ap)*12 + al*3 + a],
+ *   Ihat_i[gi] = sum_{at,bt} Gins[gi][at][bt] ins_i[(at*4 + bt)*12 + be*3 + a],
+ *
+ * the quantities of lhc_combine before Gamma_src is applied. For any source structure,
+ *   C = sum_{al,be} Gsrc[be][al] out[...][al*4 + be]
+ * equals lhc_combine's result. So one call serves every (Gamma_snk, Gamma_ins) pair of
+ * the two lists and, after a 4x4 contraction per (p, q), every Gamma_src: with
+ * 16-entry lists that is the whole 16 x 16 x 16 sweep over the Dirac basis (Sec. 3).
+ * spec: [np][n_r][192], ins: [nt][nq][n_r][192], snk: [ngs][4][4], ins_g: [ngi][4][4];
+ * out: complex128 [nt][ngs][ngi][np][nq][16]; nt*ngs*ngi <= 65535. Device buffers only
+ * (LHC_EINVAL otherwise). prec as for lhc_combine. */
+int lhc_combine_open(lhc_ctx ctx, const void *spec, int np, const void *ins, int nq, int n_r, int nt,
+                     const void *snk, int ngs, const void *ins_g, int ngi, int prec, void *out, void *stream);
+
 /* ---- Free-field Wilson-Dirac operator and solver: inputs for end-to-end checks.
  *
  * The paper computes propagators and solutions on gauge configurations with a

@@ -7,10 +7,10 @@
 //   baryon  Xs[g][p][i,b,c]  = sum Wsnk[a1p][a2p][bp] Wsrc[a1][a2][b] B[p][i][a1p,a1,a2p,a2,bp,c]
 //           Xi[t][g][q][i,b,c] = sum_{at,bt} Gins[at][bt] I[t][q][i][at,bt,b,c]
 // Precision: LHC_FP64 does everything in double.  LHC_MIXED does the Gamma contractions and
-// the 12-term spin-colour sum of each noise in FP32; the sum over noises (the noise
-// average of Eq. 5) is exact: each noise's term is added with Knuth's TwoSum into an
+// the spin-colour sums of each pair of noises in FP32; the sum over those (the noise
+// average of Eq. 5) is exact: each pair's term is added with Knuth's TwoSum into an
 // unevaluated FP32 pair hi + lo, rounded once to FP64 (no less accurate than FP64
-// accumulation, and it keeps GB300's slow FP64 pipe out of the inner loop).
+// accumulation of those terms, and it keeps GB300's slow FP64 pipe out of the inner loop).
 #include <algorithm>
 #include <type_traits>
 
@@ -224,8 +224,8 @@ struct NoiseSum<float> {
 };
 
 // out[t][g][p][q] = (1/N) sum_i sum_{j<12} Xs[g][p][12i+j] Xi[t][g][q][12i+j]: a tiled complex
-// GEMM whose per-noise 12-term sums run in R (float or double) and whose sum over
-// noises is the NoiseSum above.  A CTA computes a TP x TQ tile of (p, q) for one (t, g);
+// GEMM whose 24-term sums over two noises run in R (float or double) and whose sum of
+// those over the noise pairs is the NoiseSum above.  A CTA computes a TP x TQ tile of (p, q) for one (t, g);
 // thread (ty, tx) of 16 x 16 holds p = p0 + ty + 16 a (a < 2) and q = q0 + tx + 16 b
 // (b < 3).  KN noises (12 KN values of K) are staged per pass (4 in FP32, 2 in FP64: the
 // static shared memory stays below 48 KB); rows are padded by one element so that the
@@ -257,7 +257,8 @@ __global__ void __launch_bounds__(256) comb_gemm(const cplx<R> *__restrict__ Xs,
       Bs[r * KW + k] = (q0 + r < nq && k < kw) ? B[(size_t)(q0 + r) * K + 12 * i0 + k] : cplx<R>{0, 0};
     }
     __syncthreads();
-    for (int ii = 0; ii < kw / 12; ++ii) {
+    // two noises (24 terms) per partial sum; a missing second noise is staged as zeros
+    for (int ii = 0; ii < kw / 12; ii += 2) {
       cplx<R> pa[2][3];
 #pragma unroll
       for (int a = 0; a < 2; ++a)
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(256) comb_gemm(const cplx<R> *__restrict__ Xs,
         for (int b = 0; b < 3; ++b) pa[a][b] = cplx<R>{0, 0};
       const cplx<R> *ar = As + ty * KW + 12 * ii, *br = Bs + tx * KW + 12 * ii;
 #pragma unroll
-      for (int k = 0; k < 12; ++k) {
+      for (int k = 0; k < 24; ++k) {
         const cplx<R> a0 = ar[k], a1 = ar[16 * KW + k];
         const cplx<R> b0 = br[k], b1 = br[16 * KW + k], b2 = br[32 * KW + k];
         cfma(pa[0][0], a0, b0);
@@ -291,7 +292,118 @@ __global__ void __launch_bounds__(256) comb_gemm(const cplx<R> *__restrict__ Xs,
     }
 }
 
+// Open-source-spin combine (meson):
+//   O[t][gs][gi][p][q][al][be] = (1/N) sum_{i,a} Xs[gs][p][i,al,a] Xi[t][gi][q][i,be,a]
+// with Xs the spectator part with Gamma_snk applied (comb_spec_meson) and Xi the
+// insertion part with Gamma_ins applied (comb_ins_baryon, which applies Gamma_ins only).
+// Rows are (p, al), columns (q, be); the tiling is comb_gemm's, with KN noises of three
+// colours staged per pass and four noises (12 terms) per partial sum.
+template <typename R>
+__global__ void __launch_bounds__(256) comb_gemm_open(const cplx<R> *__restrict__ Xs, const cplx<R> *__restrict__ Xi,
+                                                      int np, int nq, int n_r, int ngs, int ngi, double inv_n,
+                                                      float inv_n_pow2, double2 *__restrict__ out) {
+  constexpr int KN = sizeof(R) == 4 ? 8 : 4, KW = 3 * KN + 1;
+  __shared__ cplx<R> As[TP * KW];
+  __shared__ cplx<R> Bs[TQ * KW];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int c0 = blockIdx.x * TQ, r0 = blockIdx.y * TP;
+  const int z = blockIdx.z, gi = z % ngi, gs = (z / ngi) % ngs, t = z / (ngi * ngs);
+  const cplx<R> *A = Xs + (size_t)gs * np * 12 * n_r;                 // [p][i][al][a]
+  const cplx<R> *B = Xi + ((size_t)t * ngi + gi) * nq * 12 * n_r;      // [q][i][be][a]
+  NoiseSum<R> acc[2][3];
+  for (int i0 = 0; i0 < n_r; i0 += KN) {
+    const int kn = min(KN, n_r - i0);
+    for (int e = threadIdx.x; e < TP * 3 * KN; e += 256) {
+      const int r = e / (3 * KN), k = e % (3 * KN), ii = k / 3, a = k % 3, R_ = r0 + r;
+      As[r * KW + k] = (R_ < 4 * np && ii < kn) ? A[((size_t)(R_ >> 2) * n_r + i0 + ii) * 12 + (R_ & 3) * 3 + a]
+                                                : cplx<R>{0, 0};
+    }
+    for (int e = threadIdx.x; e < TQ * 3 * KN; e += 256) {
+      const int r = e / (3 * KN), k = e % (3 * KN), ii = k / 3, a = k % 3, C_ = c0 + r;
+      Bs[r * KW + k] = (C_ < 4 * nq && ii < kn) ? B[((size_t)(C_ >> 2) * n_r + i0 + ii) * 12 + (C_ & 3) * 3 + a]
+                                                : cplx<R>{0, 0};
+    }
+    __syncthreads();
+    for (int ii = 0; ii < kn; ii += 4) {   // missing noises of a group of four are staged as zeros
+      cplx<R> pa[2][3];
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) pa[a][b] = cplx<R>{0, 0};
+      const cplx<R> *ar = As + ty * KW + 3 * ii, *br = Bs + tx * KW + 3 * ii;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const cplx<R> a0 = ar[k], a1 = ar[16 * KW + k];
+        const cplx<R> b0 = br[k], b1 = br[16 * KW + k], b2 = br[32 * KW + k];
+        cfma(pa[0][0], a0, b0);
+        cfma(pa[0][1], a0, b1);
+        cfma(pa[0][2], a0, b2);
+        cfma(pa[1][0], a1, b0);
+        cfma(pa[1][1], a1, b1);
+        cfma(pa[1][2], a1, b2);
+      }
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) acc[a][b].add(pa[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int R_ = r0 + ty + 16 * a, C_ = c0 + tx + 16 * b;
+      if (R_ < 4 * np && C_ < 4 * nq)
+        out[(((size_t)z * np + (R_ >> 2)) * nq + (C_ >> 2)) * 16 + (R_ & 3) * 4 + (C_ & 3)] =
+            acc[a][b].get(inv_n, inv_n_pow2);
+    }
+}
+
 unsigned blocks(size_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
+
+// Noises staged per pass by the staging kernels, and their shared memory: as many as fit
+// 96 KB next to the 2 ng Gamma matrices (two CTAs per SM), at least one.
+template <typename R>
+int noise_chunk(int ng, int n_r, int *nch, size_t *smem) {
+  const size_t g_bytes = (size_t)2 * ng * 16 * sizeof(cplx<R>), row = (size_t)SROW * sizeof(cplx<R>);
+  if (g_bytes + row > 200 * 1024) {
+    set_error("combine: %d Gamma structures do not fit shared memory", ng);
+    return LHC_EINVAL;
+  }
+  *nch = (int)std::min<size_t>((size_t)n_r, g_bytes + row <= 96 * 1024 ? (96 * 1024 - g_bytes) / row : 1);
+  *smem = g_bytes + (size_t)*nch * row;
+  if (*smem > 48 * 1024) {
+    static bool attr = false;
+    if (!attr) {
+      LHC_CHECK_CUDA(cudaFuncSetAttribute(comb_ins_meson<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      LHC_CHECK_CUDA(cudaFuncSetAttribute(comb_ins_baryon<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      LHC_CHECK_CUDA(cudaFuncSetAttribute(comb_spec_meson<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      attr = true;
+    }
+  }
+  return LHC_OK;
+}
+
+template <typename R>
+int launch_combine_open(const double2 *spec, int np, const double2 *ins, int nq, int n_r, int nt, const double2 *snk,
+                        int ngs, const double2 *ins_g, int ngi, void *scratch, double2 *out, cudaStream_t st) {
+  cplx<R> *Xs = static_cast<cplx<R> *>(scratch);
+  cplx<R> *Xi = Xs + (size_t)ngs * np * 12 * n_r;
+  int nch;
+  size_t smem;
+  LHC_TRY(noise_chunk<R>(ngs, n_r, &nch, &smem));
+  comb_spec_meson<R><<<np, 256, smem, st>>>(spec, np, n_r, nch, snk, ngs, Xs);
+  note_launch();
+  LHC_TRY(noise_chunk<R>(ngi, n_r, &nch, &smem));
+  comb_ins_baryon<R><<<nt * nq, 256, smem, st>>>(ins, nq, n_r, nch, ins_g, ngi, Xi);   // Gamma_ins only
+  note_launch();
+  const dim3 grid((4 * nq + TQ - 1) / TQ, (4 * np + TP - 1) / TP, nt * ngs * ngi);
+  const float inv_pow2 = (n_r & (n_r - 1)) == 0 ? 1.0f / (float)n_r : 0.0f;   // exact for N = 2^m
+  comb_gemm_open<R><<<grid, 256, 0, st>>>(Xs, Xi, np, nq, n_r, ngs, ngi, 1.0 / n_r, inv_pow2, out);
+  note_launch();
+  return LHC_OK;
+}
 
 template <typename R>
 int launch_combine(int kind, const double2 *spec, int np, const double2 *ins, int nq, int n_r, int nt,
@@ -363,6 +475,25 @@ int run_combine_scratch(int kind, const double2 *spec, int np, const double2 *in
     LHC_TRY(launch_combine<float>(kind, spec, np, ins, nq, n_r, nt, snk, ins_g, src, ng, Xs, out, st));
   else
     LHC_TRY(launch_combine<double>(kind, spec, np, ins, nq, n_r, nt, snk, ins_g, src, ng, Xs, out, st));
+  LHC_CHECK_CUDA(cudaGetLastError());
+  return LHC_OK;
+}
+
+int run_combine_open(lhc_ctx ctx, const double2 *spec, int np, const double2 *ins, int nq, int n_r, int nt,
+                     const double2 *snk, int ngs, const double2 *ins_g, int ngi, int prec, double2 *out,
+                     cudaStream_t st) {
+  if ((size_t)nt * ngs * ngi > 65535) {
+    set_error("combine_open: nt * ngs * ngi = %lld exceeds 65535", (long long)nt * ngs * ngi);
+    return LHC_EINVAL;
+  }
+  const size_t es = prec == LHC_MIXED ? sizeof(cplx<float>) : sizeof(cplx<double>);
+  const size_t K = (size_t)12 * n_r;
+  LHC_TRY(ensure(ctx, ctx->ws, ((size_t)ngs * np * K + (size_t)nt * ngi * nq * K) * es));
+  ProfScope ps(ctx, st, LHC_KERNEL_COMBINE, 8.0 * nt * ngs * ngi * (double)np * nq * K * 4.0 / 3.0);
+  if (prec == LHC_MIXED)
+    LHC_TRY(launch_combine_open<float>(spec, np, ins, nq, n_r, nt, snk, ngs, ins_g, ngi, ctx->ws.p, out, st));
+  else
+    LHC_TRY(launch_combine_open<double>(spec, np, ins, nq, n_r, nt, snk, ngs, ins_g, ngi, ctx->ws.p, out, st));
   LHC_CHECK_CUDA(cudaGetLastError());
   return LHC_OK;
 }
