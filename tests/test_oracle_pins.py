@@ -221,3 +221,23 @@ def test_pins_catch_transposed_gamma_src(monkeypatch):
     monkeypatch.setattr(C, "combine_meson", _combine_src_transposed)
     with pytest.raises(AssertionError):
         P.check_full_dilution_meson()
+
+
+def test_baryon_exchange_is_an_index_permutation():
+    """Swapping the two spectator propagators of the eps-eps contraction (the second Wick
+    topology of two identical spectator flavours) permutes the open indices
+    (a1', a1) <-> (a2', a2) of the spectator: eps_{a'b'c'} eps_{abc} is invariant when
+    both colour pairs are exchanged.  Checked on the oracle's spectator."""
+    from oracle import contractions as OC
+    from oracle.momenta import momenta
+    from paper_1711_02384_gb300 import inputs
+    import numpy as np
+    L, n_r = 2, 2
+    GA = inputs.propagator(2200, L, 1)[0]
+    GB = inputs.propagator(2200, L, 1, tensor_id=inputs.TID_PROP_B)[0]
+    eta = inputs.noise(2201, L, n_r, 0)
+    g5 = np.diag([1.0, 1.0, -1.0, -1.0]).astype(complex)
+    k, r3 = momenta(1)[:4], np.array([1, 0, 1])
+    ab = OC.spectator_baryon(GA, GB, eta, g5, r3, k, L).reshape(len(k), n_r, 4, 4, 4, 4, 4, 3)
+    ba = OC.spectator_baryon(GB, GA, eta, g5, r3, k, L).reshape(len(k), n_r, 4, 4, 4, 4, 4, 3)
+    assert np.abs(ba - ab.transpose(0, 1, 4, 5, 2, 3, 6, 7)).max() < 1e-12 * np.abs(ab).max()
