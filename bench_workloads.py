@@ -11,6 +11,8 @@ serve     a Poisson stream of three-point jobs on 16^3x32 .. 48^3x96 lattices th
           the plain FP64 path one job at a time
 mom1      the meson 24^3x48 step at 1 momentum vs 93 momenta (the paper's observation that
           many more momenta cost little extra)
+allmom    every momentum of a 16^3 slice (4096): the projection as a discrete Fourier
+          transform (FP64) against the direct FP64 and mixed projections
 
 Inputs are seeded random device tensors (torch): these rows measure throughput; parity
 is the tests' job.  Each row prints one JSON line.
@@ -333,9 +335,52 @@ def run_mom1(args, dev, g):
                                  "precision": args.prec}, "runs": out}))
 
 
+# --------------------------------------------------------------------------- allmom
+
+def run_allmom(args, dev, g):
+    L, NR, NT = 16, 16, 4
+    V3 = L ** 3
+    lo = -(L // 2)
+    k = np.array([(x, y, z) for z in range(lo, lo + L) for y in range(lo, lo + L) for x in range(lo, lo + L)],
+                 dtype=np.int32)
+    nq = len(k)
+    S = _rand((NT + 1, V3, 12, 12), torch.complex128, dev, g)
+    psi = _rand((NR, NT + 1, V3, 12), torch.complex128, dev, g)
+    eta = _rand((NR, V3, 12), torch.complex128, dev, g)
+    oi = torch.empty((NT, nq, NR, 192), dtype=torch.complex128, device=dev)
+    osp = torch.empty((nq, NR, 192), dtype=torch.complex128, device=dev)
+    ctx = lhc.Context(0)
+    r = (3, 5, 7, 0)
+    units = (NT + 1) * V3 * NR * nq
+    out = {}
+    for name, prec, mode, steps in (("dft_fp64", "fp64", "dft", args.steps), ("gemm_mixed", "mixed", "gemm", args.steps),
+                                    ("gemm_fp64", "fp64", "gemm", 1)):
+        ctx.set_projection(mode)
+
+        def step():
+            ctx.insertion(S, psi, 0, NT - 1, r, k, prec=prec, out=oi)
+            ctx.spectator(S, eta, NT, r, k, prec=prec, out=osp)
+
+        ms, clk, nl = _timed(step, steps, 1 if name == "gemm_fp64" else args.warmup, dev)
+        out[name] = {"ms_per_step": ms / steps, "value": units * steps / (ms / 1e3), "gpu_launches": nl,
+                     "clocks": clk}
+    ctx.close()
+    print(json.dumps({"metric": "site*noise*mom contractions/s (all momenta)", "value": out["dft_fp64"]["value"],
+                      "unit": UNIT, "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": out["dft_fp64"]["ms_per_step"], "dtype": "f64",
+                      "data": "synthetic (seeded random device tensors)",
+                      "config": {"workload": "meson insertion (4 slices) + spectator on 16^3, 16 noises, all 4096 "
+                                             "momenta, complex128; projection by DFT vs direct",
+                                 "l2": "inputs of every step larger than L2 (129 MB)"},
+                      "runs": out,
+                      "dft_vs_gemm_fp64": out["gemm_fp64"]["ms_per_step"] / out["dft_fp64"]["ms_per_step"],
+                      "dft_vs_gemm_mixed": out["gemm_mixed"]["ms_per_step"] / out["dft_fp64"]["ms_per_step"]}))
+
+
 def run(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     g = torch.Generator(device=dev)
     g.manual_seed(1711)
-    {"baryon32": run_baryon32, "batched": run_batched, "serve": run_serve, "mom1": run_mom1}[args.workload](args, dev, g)
+    {"baryon32": run_baryon32, "batched": run_batched, "serve": run_serve, "mom1": run_mom1,
+     "allmom": run_allmom}[args.workload](args, dev, g)

@@ -291,6 +291,21 @@ unsigned long long lhc_launch_count(void);
 int lhc_combine_open(lhc_ctx ctx, const void *spec, int np, const void *ins, int nq, int n_r, int nt,
                      const void *snk, int ngs, const void *ins_g, int ngi, int prec, void *out, void *stream);
 
+/* ---- Momentum projection by discrete Fourier transform (all-momenta mode).
+ * The projection of Eqs. 9 and 10 over every momentum of a slice is a 3-D discrete
+ * Fourier transform of the contracted values. In this mode the library contracts in
+ * FP64 and transforms along x, y and z with L-point sums (3L complex multiply-adds per
+ * value, against nq for the direct projection, for any L). It then gathers the
+ * requested momenta (any list, order or duplicates), each times exp(-+i p.r) for the
+ * source position. The result is FP64 for both precisions.
+ * LHC_PROJ_AUTO (the default) uses it for LHC_FP64 calls with nq >= L^3 / 2, where it
+ * is far cheaper than the FP64 projection. LHC_MIXED calls keep the tensor-core
+ * projection, which GB300's FP64 rate makes competitive up to about L = 24.
+ * LHC_PROJ_GEMM never uses the transform, LHC_PROJ_DFT always. The paper projects
+ * directly (it uses at most 93 momenta). */
+typedef enum { LHC_PROJ_AUTO = 0, LHC_PROJ_GEMM = 1, LHC_PROJ_DFT = 2 } lhc_projection;
+int lhc_set_projection(lhc_ctx ctx, int mode);
+
 /* ---- Free-field Wilson-Dirac operator and solver: inputs for end-to-end checks.
  *
  * The paper computes propagators and solutions on gauge configurations with a

@@ -212,6 +212,15 @@ void launch_contract(const SliceJob &j, int s0, int ns, double2 *U, cudaStream_t
 
 }  // namespace
 
+int contract_f64(const SliceJob &j, int s0, int ns, double2 *U, cudaStream_t st) {
+  if (j.dtype == LHC_C128)
+    launch_contract<double2>(j, s0, ns, U, st);
+  else
+    launch_contract<float2>(j, s0, ns, U, st);
+  LHC_CHECK_CUDA(cudaGetLastError());
+  return LHC_OK;
+}
+
 void launch_phase_f64(double2 *P, const int *k_dev, int nq, int L, int rx, int ry, int rz, int sign,
                       const double2 *roots_dev, cudaStream_t st) {
   size_t total = (size_t)nq * L * L * L;

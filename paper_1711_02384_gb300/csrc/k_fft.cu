@@ -1,0 +1,161 @@
+// All-momenta mode of the momentum projection (Eqs. 9, 10): when the momentum list is a
+// large part of the L^3 momenta of a slice, the projection sum_x e^{+-i p.(x - r)} U(x)
+// is a discrete Fourier transform of U over the slice, evaluated for every momentum at
+// once and then gathered in the requested order:
+//
+//   F(k) = sum_x exp(s 2 pi i k.x / L) U(x)          (s = +1 insertion, -1 spectator)
+//   out[q] = exp(-s 2 pi i k_q.r / L) F(k_q mod L),
+//
+// which is the phase of the direct sum, exp(s 2 pi i k.(x - r)/L), split in two.  F is
+// computed as three passes of L-point transforms along x, y and z, each in place on the
+// contracted values in FP64; a pass costs L complex multiply-adds per value, so the whole
+// transform costs 3L per value against nq for the direct projection.  Any L works (the
+// transforms are direct sums over a root table, not a radix factorization).  The site
+// contraction is the FP64 path's; the result is FP64 throughout.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "lhc_internal.h"
+
+namespace lhc {
+namespace {
+
+constexpr int kDftCols = 32;   // columns per block of a line transform
+
+// One block per (line, group of kDftCols columns): the L values of the line for those
+// columns are staged in shared memory, transformed, and written back in place.  Lines
+// along direction d (0 = x, 1 = y, 2 = z); the site stride along the line is L^d.
+__global__ void __launch_bounds__(256) dft_line_kernel(double2 *__restrict__ U, int L, size_t ncols, int d, int sign,
+                                                       const double2 *__restrict__ roots) {
+  extern __shared__ double2 sm[];   // [L][kDftCols] values, then [L] roots
+  double2 *line = sm, *w = sm + (size_t)L * kDftCols;
+  const size_t ngroups = (ncols + kDftCols - 1) / kDftCols;
+  const size_t b = blockIdx.x;
+  const size_t grp = b % ngroups, ln = b / ngroups;   // ln: index of the line among L^2
+  const size_t stride = d == 0 ? 1 : (d == 1 ? (size_t)L : (size_t)L * L);
+  // the line's first site: the two other coordinates from ln
+  size_t base;
+  {
+    const size_t u = ln % L, v = ln / L;
+    base = d == 0 ? (v * L + u) * L : (d == 1 ? v * L * L + u : v * L + u);
+  }
+  const size_t c0 = grp * kDftCols;
+  const int nc = (int)min((size_t)kDftCols, ncols - c0);
+  for (int e = threadIdx.x; e < L; e += blockDim.x) w[e] = roots[e];
+  for (int e = threadIdx.x; e < L * kDftCols; e += blockDim.x) {
+    const int x = e / kDftCols, c = e % kDftCols;
+    line[e] = c < nc ? U[(base + x * stride) * ncols + c0 + c] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  double2 res[(128 * kDftCols + 255) / 256];   // L <= 128: at most 16 outputs per thread
+  int nres = 0;
+  for (int e = threadIdx.x; e < L * kDftCols; e += blockDim.x) {
+    const int k = e / kDftCols, c = e % kDftCols;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int x = 0, m = 0; x < L; ++x, m = (m + k) % L) {   // m = (k x) mod L
+      const double2 a = line[x * kDftCols + c], z = w[m];
+      const double zi = sign * z.y;
+      acc.x = fma(a.x, z.x, fma(-a.y, zi, acc.x));
+      acc.y = fma(a.x, zi, fma(a.y, z.x, acc.y));
+    }
+    res[nres++] = acc;
+  }
+  __syncthreads();   // every thread has read the line before anyone writes it back
+  nres = 0;
+  for (int e = threadIdx.x; e < L * kDftCols; e += blockDim.x) {
+    const int k = e / kDftCols, c = e % kDftCols;
+    if (c < nc) U[(base + k * stride) * ncols + c0 + c] = res[nres];
+    ++nres;
+  }
+}
+
+// out[q][i0 + i][col] = exp(-s 2 pi i k_q.r / L) F[site(k_q mod L)][i][col]
+__global__ void dft_gather_kernel(const double2 *__restrict__ F, const int *__restrict__ kq, int nq, int L, int rx,
+                                  int ry, int rz, int sign, const double2 *__restrict__ roots, size_t ncols_chunk,
+                                  size_t out_row, size_t col0, double2 *__restrict__ out) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)nq * ncols_chunk) return;
+  const int q = (int)(idx / ncols_chunk);
+  const size_t c = idx % ncols_chunk;
+  const int kx = kq[3 * q], ky = kq[3 * q + 1], kz = kq[3 * q + 2];
+  const int mx = ((kx % L) + L) % L, my = ((ky % L) + L) % L, mz = ((kz % L) + L) % L;
+  long long m = ((long long)kx * rx + (long long)ky * ry + (long long)kz * rz) % L;
+  if (m < 0) m += L;
+  const double2 z = roots[m];
+  const double zi = -sign * z.y;   // exp(-s 2 pi i k.r / L)
+  const double2 f = F[((size_t)(mz * L + my) * L + mx) * ncols_chunk + c];
+  out[(size_t)q * out_row + col0 + c] = make_double2(f.x * z.x - f.y * zi, f.x * zi + f.y * z.x);
+}
+
+}  // namespace
+
+// Automatic choice: the FP64 transform replaces the FP64 projection for large momentum
+// sets (GB300's FP64 rate makes the direct FP64 projection the slowest part there); the
+// mixed path's tensor-core projection stays unless the transform is asked for.
+bool use_fft(lhc_ctx ctx, int prec, int V3, int nq) {
+  if (ctx->proj_mode == LHC_PROJ_DFT) return true;
+  if (ctx->proj_mode == LHC_PROJ_GEMM) return false;
+  return prec == LHC_FP64 && 2 * (long long)nq >= V3;
+}
+
+int run_part_fft(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int nq, const int r[4], int sign,
+                 cudaStream_t st) {
+  const SliceJob &j0 = jobs[0];
+  const int L = j0.L, V3 = j0.V3;
+  const int cols = j0.part == PART_SPEC_BARYON ? kBarCols : 192;
+  // noises per chunk: the FP64 values of a whole slice for that many noises within 2 GiB
+  const size_t per_noise = (size_t)V3 * cols * sizeof(double2);
+  const int nch = (int)std::max<size_t>(1, std::min<size_t>(j0.n_r, ((size_t)2 << 30) / per_noise));
+  const size_t ubytes = (size_t)nch * per_noise;
+  const size_t off_k = (ubytes + 255) & ~(size_t)255, off_roots = (off_k + 12 * (size_t)nq + 255) & ~(size_t)255;
+  LHC_TRY(ensure(ctx, ctx->ws, off_roots + (size_t)L * sizeof(double2)));
+  char *ws = static_cast<char *>(ctx->ws.p);
+  double2 *U = reinterpret_cast<double2 *>(ws);
+  int *kd = reinterpret_cast<int *>(ws + off_k);
+  double2 *roots = reinterpret_cast<double2 *>(ws + off_roots);
+  std::vector<double2> hroots(L);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int m = 0; m < L; ++m) hroots[m] = make_double2(std::cos(two_pi * m / L), std::sin(two_pi * m / L));
+  LHC_CHECK_CUDA(cudaMemcpyAsync(kd, k, 12 * (size_t)nq, cudaMemcpyHostToDevice, st));
+  LHC_CHECK_CUDA(cudaMemcpyAsync(roots, hroots.data(), (size_t)L * sizeof(double2), cudaMemcpyHostToDevice, st));
+  // the host arrays must outlive the copies
+  LHC_CHECK_CUDA(cudaStreamSynchronize(st));
+  const int rx = ((r[0] % L) + L) % L, ry = ((r[1] % L) + L) % L, rz = ((r[2] % L) + L) % L;
+  const size_t smem = ((size_t)L * kDftCols + L) * sizeof(double2);
+  if (smem > 48 * 1024)
+    LHC_CHECK_CUDA(cudaFuncSetAttribute(dft_line_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  for (int jt = 0; jt < nt; ++jt) {
+    const SliceJob &j = jobs[jt];
+    for (int i0 = 0; i0 < j.n_r; i0 += nch) {
+      SliceJob jc = j;
+      jc.n_r = std::min(nch, j.n_r - i0);
+      const size_t esz = j.dtype == LHC_C128 ? 16 : 8;
+      jc.vec = static_cast<const char *>(j.vec) + (size_t)i0 * j.vec_stride * esz;
+      const size_t ncc = (size_t)jc.n_r * cols;
+      {
+        size_t es = j.dtype == LHC_C128 ? 16 : 8;
+        const int nS = j.part == PART_SPEC_BARYON ? 2 : 1;
+        ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT,
+                     (double)V3 * (144.0 * nS + 12.0 * jc.n_r) * es + (double)V3 * ncc * 16.0);
+        LHC_TRY(contract_f64(jc, 0, V3, U, st));
+      }
+      {
+        ProfScope ps(ctx, st, LHC_KERNEL_PROJECT, 3.0 * 8.0 * L * (double)V3 * ncc);
+        const size_t blocks = (size_t)L * L * ((ncc + kDftCols - 1) / kDftCols);
+        for (int d = 0; d < 3; ++d) {
+          dft_line_kernel<<<(unsigned)blocks, 256, smem, st>>>(U, L, ncc, d, sign, roots);
+          note_launch();
+        }
+      }
+      const size_t n = (size_t)nq * ncc;
+      dft_gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(U, kd, nq, L, rx, ry, rz, sign, roots, ncc,
+                                                                     (size_t)j.n_r * cols, (size_t)i0 * cols, j.out);
+      note_launch();
+    }
+  }
+  LHC_CHECK_CUDA(cudaGetLastError());
+  return LHC_OK;
+}
+
+}  // namespace lhc

@@ -576,8 +576,9 @@ int run_part(lhc_ctx ctx, const PartCall &c, cudaStream_t st) {
                    : static_cast<double2 *>(c.out);
   if (any_host) LHC_TRY(stage_ready(ctx, slot, st));
 
+  const bool dft = use_fft(ctx, c.prec, V3, c.nq);   // all-momenta mode: the projection as a DFT
   const double2 *phase = nullptr;
-  if (c.prec == LHC_FP64) LHC_TRY(get_phase_f64(ctx, L, c.k, c.nq, c.r, c.sign, st, &phase));
+  if (c.prec == LHC_FP64 && !dft) LHC_TRY(get_phase_f64(ctx, L, c.k, c.nq, c.r, c.sign, st, &phase));
 
   std::vector<SliceJob> jobs(c.nt);
   for (int j = 0; j < c.nt; ++j) {
@@ -596,9 +597,12 @@ int run_part(lhc_ctx ctx, const PartCall &c, cudaStream_t st) {
     job.vec_stride = v_noise_stride;
     job.g5mask = g5mask_of(ctx);
     job.out = Od + (size_t)j * c.nq * c.n_r * cols;
-    if (c.prec == LHC_FP64) LHC_TRY(run_slice_f64(ctx, job, phase, st));
+    if (c.prec == LHC_FP64 && !dft) LHC_TRY(run_slice_f64(ctx, job, phase, st));
   }
-  if (c.prec == LHC_MIXED) LHC_TRY(run_part_mixed(ctx, jobs.data(), c.nt, c.k, c.nq, c.r, c.sign, st));
+  if (dft)
+    LHC_TRY(run_part_fft(ctx, jobs.data(), c.nt, c.k, c.nq, c.r, c.sign, st));
+  else if (c.prec == LHC_MIXED)
+    LHC_TRY(run_part_mixed(ctx, jobs.data(), c.nt, c.k, c.nq, c.r, c.sign, st));
   if (any_host) LHC_TRY(stage_end(ctx, slot, st, hO ? c.out : nullptr, Od, out_bytes));
   return LHC_OK;
 }
@@ -722,6 +726,15 @@ int lhc_combine_open(lhc_ctx ctx, const void *spec, int np, const void *ins, int
                            static_cast<double2 *>(out), st);
   int e = end_call(ctx, st);
   return s != LHC_OK ? s : e;
+}
+
+int lhc_set_projection(lhc_ctx ctx, int mode) {
+  if (!ctx) return fail(LHC_EINVAL, "ctx is NULL");
+  if (mode != LHC_PROJ_AUTO && mode != LHC_PROJ_GEMM && mode != LHC_PROJ_DFT)
+    return fail(LHC_EINVAL, "unknown projection mode %d", mode);
+  std::lock_guard<std::mutex> g(ctx->mu);
+  ctx->proj_mode = mode;
+  return LHC_OK;
 }
 
 }  // extern "C"

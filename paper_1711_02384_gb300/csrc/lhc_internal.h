@@ -126,6 +126,7 @@ struct lhc_ctx_s {
   bool prof_on = false;
   int *dev_err = nullptr;                 // sticky device error word (bounded waits that gave up)
   int tune_mode = 0;                      // lhc_tune_mode: time launch shapes of new shapes
+  int proj_mode = 0;                      // lhc_projection: auto, GEMM or DFT momentum projection
   std::vector<lhc::ProfRecord> prof;
 };
 
@@ -146,6 +147,14 @@ int get_phase_f64(lhc_ctx ctx, int L, const int *k, int nq, const int r[4], int 
 
 // FP64 path: contraction into a workspace, then projection (k_f64.cu)
 int run_slice_f64(lhc_ctx ctx, const SliceJob &job, const double2 *phase, cudaStream_t st);
+
+// FP64 site contraction of sites s0 .. s0+ns-1 into U[site - s0][i][cols] (k_f64.cu)
+int contract_f64(const SliceJob &j, int s0, int ns, double2 *U, cudaStream_t st);
+
+// all-momenta mode: FP64 contraction, three line DFTs over the slice, gather (k_fft.cu)
+bool use_fft(lhc_ctx ctx, int prec, int V3, int nq);
+int run_part_fft(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int nq, const int r[4], int sign,
+                 cudaStream_t st);
 
 // mixed path: all slices of one call in one set of launches (k_mixed.cu)
 int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int nq, const int r[4], int sign,

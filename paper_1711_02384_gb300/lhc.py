@@ -99,10 +99,11 @@ def lib():
         L.lhc_wilson_solve.argtypes = [vp, lp, ctypes.c_double, vp, vp, vp, ci, ctypes.c_double, ci, ip,
                                        ctypes.POINTER(ctypes.c_double), vp]
         L.lhc_combine_open.argtypes = [vp, vp, ci, vp, ci, ci, ci, vp, ci, vp, ci, ci, vp, vp]
+        L.lhc_set_projection.argtypes = [vp, ci]
         L.lhc_set_tuning.argtypes = [vp, ci, ctypes.c_char_p]
         L.lhc_tuning_table.argtypes = [ip, ci, ip]
         L.lhc_tuning_load.argtypes = [ctypes.c_char_p, ip]
-        for name in ("lhc_combine_open", "lhc_wilson_apply", "lhc_wilson_solve", "lhc_set_tuning", "lhc_tuning_table", "lhc_tuning_load",
+        for name in ("lhc_combine_open", "lhc_set_projection", "lhc_wilson_apply", "lhc_wilson_solve", "lhc_set_tuning", "lhc_tuning_table", "lhc_tuning_load",
                      "lhc_create", "lhc_destroy", "lhc_set_gamma5", "lhc_momenta", "lhc_insertion",
                      "lhc_spectator", "lhc_combine", "lhc_profile", "lhc_profile_read", "lhc_sync", "lhc_release_workspace",
                      "lhc_selftest_timeout", "lhc_serve_start", "lhc_serve_stop", "lhc_prop_register",
@@ -124,6 +125,7 @@ def launch_count() -> int:
 
 
 TUNE_OFF, TUNE_ON = 0, 1
+PROJECTIONS = {"auto": 0, "gemm": 1, "dft": 2}
 
 
 def tuning_table() -> np.ndarray:
@@ -236,6 +238,11 @@ class Context:
         ms, n, w = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
         _check(lib().lhc_profile_read(self._h, kernel, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)))
         return ms.value, n.value, w.value
+
+    def set_projection(self, mode: str):
+        """Momentum projection: "auto" (a DFT over the slice when nq >= L^3 / 2), "gemm"
+        (always the direct projection) or "dft" (always the all-momenta transform)."""
+        _check(lib().lhc_set_projection(self._h, PROJECTIONS[mode]))
 
     def set_tuning(self, enable: bool, path=None):
         """Autotune the launch shape of each new mixed-precision shape on its first call
