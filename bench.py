@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--streams", type=int, default=1,
+                    help="contexts and streams the step's three t_f sets are spread over (their kernels overlap)")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the heuristic launch shapes instead of autotuning them during warm-up")
     ap.add_argument("--workload", default="meson24",
@@ -229,17 +231,35 @@ def main():
     outs_spec = [torch.empty((nq, N_R, 192), dtype=torch.complex128, device=dev) for _ in TFS]
     outs_c = [torch.empty((tf + 1, 16, nq, nq), dtype=torch.complex128, device=dev) for tf in TFS]
 
-    def step():
+    # the three t_f sets are independent chains (insertion -> spectator -> combine); with
+    # --streams n they go to n contexts on n streams, so one set's memory-bound kernels
+    # overlap another's fused kernel
+    nstr = max(1, min(args.streams, len(TFS)))
+    ctxs = [ctx] + [lhc.Context(local) for _ in range(nstr - 1)]
+    sts = [st] + [torch.cuda.Stream(dev) for _ in range(nstr - 1)]
+
+    def step_on(cs, ss):
+        for s in ss[1:]:
+            s.wait_stream(ss[0])
         for j, tf in enumerate(TFS):
-            ctx.insertion(S, psis[j], 0, tf, r, k, prec=args.prec, out=outs_ins[j])
-            ctx.spectator(S, etas[j], tf, r, k, prec=args.prec, out=outs_spec[j])
-            ctx.combine(outs_spec[j], outs_ins[j], G[0], G[1], G[2], prec=args.prec, out=outs_c[j])
+            c, s = cs[j % len(cs)], ss[j % len(ss)].cuda_stream
+            c.insertion(S, psis[j], 0, tf, r, k, prec=args.prec, out=outs_ins[j], stream=s)
+            c.spectator(S, etas[j], tf, r, k, prec=args.prec, out=outs_spec[j], stream=s)
+            c.combine(outs_spec[j], outs_ins[j], G[0], G[1], G[2], prec=args.prec, out=outs_c[j], stream=s)
+        for s in ss[1:]:
+            ss[0].wait_stream(s)
+
+    def step():
+        step_on(ctxs, sts)
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    # launch shapes are tuned on one stream first: candidates timed next to other work
+    # would be picked for the wrong conditions
+    step_on([ctx], [st])
     for _ in range(args.warmup):
         step()
     barrier()
@@ -261,8 +281,9 @@ def main():
 
     # dominant kernel: timed with CUDA events on its own stream by the library
     kern = lhc.KERNEL_FUSED if args.prec == "mixed" else lhc.KERNEL_PROJECT
+    # (one context on one stream: every kernel of the step is timed alone)
     ctx.profile(True)
-    step()
+    step_on([ctx], [st])
     torch.cuda.synchronize(dev)
     ctx.profile(False)
     kms, kn, kwork = ctx.profile_read(kern)
@@ -358,6 +379,7 @@ def main():
             "dtype": "f32+f16x2->f32 (mixed)" if args.prec == "mixed" else "f64",
             "data": "synthetic (seeded Philox Gaussian propagators/solutions, Z2xZ2 noise)",
             "config": {"workload": WORKLOAD, "precision": args.prec, "parallelism": f"replicas x{world}",
+                       "streams": nstr,
                        "l2": "inputs (2.1 GB per step) larger than L2", "units_per_step": upstep,
                        "launch_shapes": "heuristic" if args.no_tune or args.prec != "mixed" else
                        "autotuned in warm-up: " + "; ".join(
@@ -366,7 +388,8 @@ def main():
             "clocks": clk, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": n_launches, "kernels": kernels,
         }))
-    ctx.close()
+    for c in ctxs:
+        c.close()
     if world > 1:
         dist.destroy_process_group()
 

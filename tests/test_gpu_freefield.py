@@ -103,3 +103,46 @@ def test_factorized_free_correlator_end_to_end(ctx, prec, tol):
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     print(f"free correlator end to end ({prec}): relative error {err:.3e}")
     assert err < tol
+
+
+def test_forward_and_backward_in_one_pass(ctx):
+    """Noise on two sink slices at once (x4' before the source, x4'' after it, as in the
+    paper's runs): one set of solves, one insertion call over x4' .. x4'' and one spectator
+    call per sink slice give both the backward and the forward three-point functions,
+    each equal to its momentum-space free correlator (full dilution on both slices, 1536
+    noises; the noises of one slice contribute nothing to the other's spectator)."""
+    L, T, m = 4, 8, 0.3
+    g = _gammas("chiral")
+    V3 = L ** 3
+    r, r4, tb, tfw = (2, 1, 3), 3, 1, 5          # backward sink 1, source 3, forward sink 5
+    rsite = (r[2] * L + r[1]) * L + r[0]
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    src = np.zeros((12, T, V3, 12), dtype=complex)
+    for sc in range(12):
+        src[sc, r4, rsite, sc] = 1.0
+    sol, _, res = ctx.wilson_solve(dev(src), m, g, tol=1e-13)
+    assert res < 1e-11
+    S = sol.permute(1, 2, 3, 0).contiguous()
+    N1 = 12 * V3
+    eta = torch.zeros((2 * N1, T, V3, 12), dtype=torch.complex128, device="cuda")
+    unit = torch.zeros((N1, V3, 12), dtype=torch.complex128)
+    for x0 in range(V3):
+        for sc in range(12):
+            unit[x0 * 12 + sc, x0, sc] = 1.0
+    eta[:N1, tb] = unit.cuda()
+    eta[N1:, tfw] = unit.cuda()
+    psi, _, res = ctx.wilson_solve(eta, m, g, tol=1e-13)
+    assert res < 1e-11
+    k = np.asarray(P.M.momenta(1), dtype=np.int32)
+    r4v = np.array([r[0], r[1], r[2], r4], dtype=np.int32)
+    ins = ctx.insertion(S, psi, tb, tfw, r4v, k, prec="fp64")                 # slices 1 .. 5, one call
+    rng = np.random.default_rng(7)
+    gs, gi, gc = (rng.standard_normal((1, 4, 4)) + 1j * rng.standard_normal((1, 4, 4)) for _ in range(3))
+    ff = P.FreeField(L=L, T=T, m=m)
+    for tsink, ty in ((tb, 2), (tfw, 4)):
+        spec = ctx.spectator(S, eta[:, tsink].contiguous(), tsink, r4v, k, prec="fp64")
+        c = ctx.combine(spec, ins[ty - tb], dev(gs), dev(gi), dev(gc), prec="fp64")
+        got = 2 * N1 * c.cpu().numpy()[0]
+        ref = ff.momentum_space_3pt(r4, r, tsink, ty, gs[0], gi[0], gc[0], k, k)
+        assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref), (tsink, ty)
+    ctx.sync()
