@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--streams", type=int, default=1,
+    ap.add_argument("--streams", type=int, default=3,
                     help="contexts and streams the step's three t_f sets are spread over (their kernels overlap)")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the heuristic launch shapes instead of autotuning them during warm-up")

@@ -158,13 +158,29 @@ def run_batched(args, dev, g):
             ctx.spectator(S, eta, ts, j["r"], j["k"], prec=args.prec, out=j["om"], stream=stream.cuda_stream)
             ctx.spectator(S, eta, ts, j["r"], j["k"], prec=args.prec, GB=S, out=j["ob"], stream=stream.cuda_stream)
 
+    # the same calls as one batch: one fused launch per part kind and momentum-chunk width
+    batch = []
+    for j in jobs:
+        ts = (j["t0"] + j["dt"]) % T
+        batch.append(dict(part="ins", S=S, vec=psi, t_lo=j["t0"], t_hi=j["t0"] + j["dt"], r=j["r"], k=j["k"], out=j["oi"]))
+        batch.append(dict(part="spec", S=S, vec=eta, t_lo=ts, t_hi=ts, r=j["r"], k=j["k"], out=j["om"]))
+        batch.append(dict(part="baryon", S=S, GB=S, vec=eta, t_lo=ts, t_hi=ts, r=j["r"], k=j["k"], out=j["ob"]))
+    use_batch = args.prec == "mixed"
+
+    def step_calls():
+        if use_batch:
+            ctx.batch(batch, stream=stream.cuda_stream)
+        else:
+            calls()
+
     with torch.cuda.stream(stream):
-        calls()                      # builds the phase tables and sizes the workspace
+        calls()                      # tunes the launch shapes, builds the phase tables, sizes the workspace
+        step_calls()
         torch.cuda.synchronize(dev)
         graph = torch.cuda.CUDAGraph()
         n0 = lhc.launch_count()
         with torch.cuda.graph(graph, stream=stream):
-            calls()
+            step_calls()
         n_graph = lhc.launch_count() - n0
         # graph.replay() launches on the current stream: keep it, and the events, on `stream`
         ms, clk, _ = _timed(lambda: graph.replay(), args.steps, args.warmup, dev, stream=stream)
@@ -184,7 +200,8 @@ def run_batched(args, dev, g):
     units = sum(V3 * NR * j["nq"] * (j["dt"] + 3) for j in jobs)
     _line(args, B.METRIC, units * args.steps / (ms / 1e3), ms / args.steps,
           "batched 32^3x64, 16 sources x t_f-t_0 in {8,10,12}, N_r=16, meson insertion + meson and baryon "
-          "spectators, per-job momentum sets |k|^2<=4..16 (33..257), one CUDA graph per step",
+          "spectators, per-job momentum sets |k|^2<=4..16 (33..257), one CUDA graph per step"
+          + (", all 144 calls in one lhc_batch (one fused launch per part kind and chunk width)" if use_batch else ""),
           {"clocks": clk, "roofline": _roofline(ctx), "units_per_step": units, "jobs": len(jobs),
            "gpu_launches": n_graph * args.steps, "kernels_per_graph": n_graph,
            "graph_replay_equals_direct_calls": same})

@@ -291,6 +291,33 @@ unsigned long long lhc_launch_count(void);
 int lhc_combine_open(lhc_ctx ctx, const void *spec, int np, const void *ins, int nq, int n_r, int nt,
                      const void *snk, int ngs, const void *ins_g, int ngi, int prec, void *out, void *stream);
 
+/* ---- Batched calls: one fused launch for many calls.
+ * One call of lhc_insertion or lhc_spectator (LHC_MIXED): part 0 insertion (Eq. 10),
+ * 1 meson spectator (Eq. 9), 2 baryon spectator. S is S3, S1 or GA; GB is the second
+ * baryon propagator (else NULL); vec is psi [n_r][T][L^3][12] (insertion) or eta
+ * [n_r][L^3][12]. Slices t_lo..t_hi (mod T, at most 64) for the insertion, and
+ * t_lo = t_hi = t_sink for the spectators. out as for the single call. */
+typedef struct {
+  int part;
+  lhc_lattice lat;
+  const void *S, *GB, *vec;
+  int n_r, t_lo, t_hi;
+  int r[4];
+  const int *k;
+  int nq;
+  void *out;
+} lhc_call;
+/* Runs ncalls calls in precision LHC_MIXED with one fused-kernel launch per part kind
+ * and momentum-chunk width, for up to 64 calls per launch. The per-call staging and
+ * reduce kernels stay separate launches. The results are bitwise those of the same
+ * calls made one by one: each CTA does the work it does in its call's own launch, with
+ * the same launch shape, taken from the tuning table or the heuristic (a batch never
+ * tunes; tune its shapes with single calls first). Device buffers only. The calls'
+ * outputs must not overlap their inputs or each other. Asynchronous on `stream`;
+ * capturable in a CUDA graph once the phase tables exist (after a first run). The
+ * paper has no counterpart: it ran one contraction at a time. */
+int lhc_batch(lhc_ctx ctx, const lhc_call *calls, int ncalls, void *stream);
+
 /* ---- Momentum projection by discrete Fourier transform (all-momenta mode).
  * The projection of Eqs. 9 and 10 over every momentum of a slice is a 3-D discrete
  * Fourier transform of the contracted values. In this mode the library contracts in

@@ -40,6 +40,7 @@
 #include <array>
 #include <cmath>
 #include <cstdlib>
+#include <memory>
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -130,10 +131,9 @@ constexpr int kMaxSlices = 64;   // slices per launch (time coordinates travel a
 //        baryon: the diquark as [V3][3 c'][768 s], box [16][3][16].
 //   tmV  the vector (psi or eta) as [n_r][T][V3][12], box [2][1][16][12]: the tile's two
 //        noises on 16 sites (noises past n_r and sites past V3 read as zero).
-struct FusedParams {
+struct FusedCore {
   CUtensorMap tmM;   // (CUtensorMap carries its own 64-byte alignment)
   CUtensorMap tmV;
-  int tM[kMaxSlices], tV[kMaxSlices];   // per slice: time coordinate in tmM, tmV
   const __half *B;                      // phase table
   float4 *partial;                      // [nt][nsplit][nrc * NH][ncols]: (Re C, Re S, Im C, Im S)
   int *err;
@@ -142,6 +142,16 @@ struct FusedParams {
   const unsigned *maxM, *maxV;
   int maxM_per_slice;                   // 1: maxM[j]; 0: maxM[0] for every slice (diquark)
   int n_r, V3, nct, nkb, nrc, nrep, ncols, nsplit, kd, g5mask;
+  // batched launches: slice j's time coordinates are (tm0 + j) % tmT, (tv0 + j) % tvT
+  // (these fit in the structure's alignment padding)
+  int tm0, tmT, tv0, tvT;
+};
+
+// One call's launch: the core parameters and, per slice, the time coordinates of its
+// matrix and vector boxes in the tensor maps.
+struct FusedParams {
+  FusedCore c;
+  int tM[kMaxSlices], tV[kMaxSlices];
 };
 
 // Power-of-two scale of the contracted values before their FP16 split.  Every value is a
@@ -181,8 +191,12 @@ struct Stage {
   static constexpr int bytes = NSTAGE * ab + NIN * in;
 };
 
+// The work of one CTA: tile ct (noise pair, 16 matrix columns), site split `split`,
+// slice j and representative chunk rc of the call described by p; tm, tv are slice j's
+// time coordinates in the tensor maps.
 template <typename CT, int MODE, int NH>
-__global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant__ FusedParams p) {
+__device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, const int split, const int j,
+                                           const int rc, const int tm, const int tv) {
   static_assert(NH % 8 == 0 && NH <= RCHUNK, "representative chunk");
   using St = Stage<MODE, NH>;
   // NP accumulator columns per half: [cos | sin] x NH representatives; half 0 takes the
@@ -213,8 +227,6 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
   auto stV = [&](int s) { return smem + NSTAGE * St::ab + s * St::in + St::M; };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ct = blockIdx.x, split = blockIdx.y;
-  const int j = blockIdx.z / p.nrc, rc = blockIdx.z % p.nrc;
   const int sc_e = split_scale_exp(p.maxM[p.maxM_per_slice ? j : 0], p.maxV[j]);
   // site range in k-steps; splits start on even k-steps so producer iterations align
   const int npair = (p.nkb + 1) / 2;
@@ -273,7 +285,6 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
   } else if (warp == kInWarp) {
     // ---------------------------------------------------- contraction inputs (input ring, TMA)
     if (lane == 0 && nk > 0) {
-      const int tm = p.tM[j], tv = p.tV[j];
       int issued = 0;
       for (int i = 0; i < nk; ++i) {
         const int s = i % NIN, u = i / NIN;
@@ -528,6 +539,44 @@ __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant
   if (warp == 1) tc::tmem_dealloc(tbase, kTmemCols);
 }
 
+template <typename CT, int MODE, int NH>
+__global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant__ FusedParams p) {
+  const int j = blockIdx.z / p.c.nrc, rc = blockIdx.z % p.c.nrc;
+  fused_body<CT, MODE, NH>(p.c, blockIdx.x, blockIdx.y, j, rc, p.tM[j], p.tV[j]);
+}
+
+// Many calls of one part kind and chunk width in one launch: the parameters of up to
+// kMaxBatch calls travel in the kernel's parameter space (a captured graph keeps them),
+// call c owns the CTAs first[c] .. first[c+1]-1, and every CTA does exactly the work it
+// would do in its call's own launch.
+constexpr int kMaxBatch = 64;
+struct BatchParams {
+  FusedCore item[kMaxBatch];
+  int first[kMaxBatch + 1];
+  int n;
+};
+static_assert(sizeof(BatchParams) <= 32764, "kernel parameter space");
+
+template <typename CT, int MODE, int NH>
+__global__ void __launch_bounds__(kThreads, 1) fused_batch(const __grid_constant__ BatchParams b) {
+  int lo = 0, hi = b.n;   // the call: first[lo] <= blockIdx.x < first[lo + 1]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (b.first[mid] <= (int)blockIdx.x)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  const FusedCore &it = b.item[lo];
+  int local = (int)blockIdx.x - b.first[lo];
+  const int ct = local % it.nct;
+  local /= it.nct;
+  const int split = local % it.nsplit;
+  local /= it.nsplit;
+  const int j = local / it.nrc, rc = local % it.nrc;
+  fused_body<CT, MODE, NH>(it, ct, split, j, rc, (it.tm0 + j) % it.tmT, (it.tv0 + j) % it.tvT);
+}
+
 // out[j][q][col] = sum over splits of the FP32 partials.  The partials are added without
 // error (Knuth's TwoSum keeps the exact sum as an unevaluated FP32 pair hi + lo) and the
 // pair is rounded once to FP64: no less accurate than FP64 accumulation of the partials,
@@ -593,7 +642,7 @@ int launch_fused_t(const FusedParams &p, int nt, cudaStream_t st) {
                                         (int)std::max<size_t>(smem, 120 * 1024)));
     attr = true;
   }
-  dim3 grid(p.nct, p.nsplit, nt * p.nrc);
+  dim3 grid(p.c.nct, p.c.nsplit, nt * p.c.nrc);
   // at least 120 KB so that one CTA runs per SM (the tensor memory is allocated whole)
   fused_meson<float2, MODE, NH><<<grid, kThreads, std::max<size_t>(smem, 120 * 1024), st>>>(p);
   note_launch();
@@ -609,6 +658,33 @@ int launch_fused_nh(int NH, const FusedParams &p, int nt, cudaStream_t st) {
     case 32: return launch_fused_t<MODE, 32>(p, nt, st);
     case 40: return launch_fused_t<MODE, 40>(p, nt, st);
     case 48: return launch_fused_t<MODE, 48>(p, nt, st);
+    default: set_error("unsupported representative chunk %d", NH); return LHC_EINVAL;
+  }
+}
+
+template <int MODE, int NH>
+int launch_batch_t(const BatchParams &b, int nctas, cudaStream_t st) {
+  constexpr size_t smem = fused_smem<MODE, NH>();
+  static bool attr = false;
+  if (!attr) {
+    LHC_CHECK_CUDA(cudaFuncSetAttribute(fused_batch<float2, MODE, NH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)std::max<size_t>(smem, 120 * 1024)));
+    attr = true;
+  }
+  fused_batch<float2, MODE, NH><<<nctas, kThreads, std::max<size_t>(smem, 120 * 1024), st>>>(b);
+  note_launch();
+  return LHC_OK;
+}
+
+template <int MODE>
+int launch_batch_nh(int NH, const BatchParams &b, int nctas, cudaStream_t st) {
+  switch (NH) {
+    case 8: return launch_batch_t<MODE, 8>(b, nctas, st);
+    case 16: return launch_batch_t<MODE, 16>(b, nctas, st);
+    case 24: return launch_batch_t<MODE, 24>(b, nctas, st);
+    case 32: return launch_batch_t<MODE, 32>(b, nctas, st);
+    case 40: return launch_batch_t<MODE, 40>(b, nctas, st);
+    case 48: return launch_batch_t<MODE, 48>(b, nctas, st);
     default: set_error("unsupported representative chunk %d", NH); return LHC_EINVAL;
   }
 }
@@ -952,159 +1028,214 @@ static int slice_coords(const void *const *ptrs, int nb, size_t slice_bytes, con
   return LHC_OK;
 }
 
+// ---------------------------------------------------------------- one call, in steps
+// A mixed call runs, per chunk of at most kMaxSlices slices: sizing, prepare (operand
+// maxima, the complex128 narrowing or the complex64 maximum pass, the baryon diquark, the
+// tensor maps and the fused kernel's parameters), the fused launch, and finish (the
+// reduce).  A batch prepares all its calls, launches the fused kernel once per part kind
+// and chunk width, and finishes all calls.
+
+struct ChunkLayout {
+  size_t off_s, off_sb, off_v, off_d, off_m, bytes;
+};
+
+static ChunkLayout chunk_layout(const SliceJob &j0, int ntl, int nsplit, size_t per_split) {
+  const bool baryon = j0.part == PART_SPEC_BARYON, narrow = j0.dtype == LHC_C128;
+  const int V3 = j0.V3, n_r = j0.n_r;
+  const size_t p_bytes = (size_t)ntl * nsplit * per_split * sizeof(float4);
+  const size_t s_bytes = narrow ? (size_t)ntl * V3 * 144 * sizeof(float2) : 0;
+  const size_t sb_bytes = narrow && baryon ? (size_t)V3 * 144 * sizeof(float2) : 0;
+  const size_t v_bytes = narrow ? (size_t)n_r * ntl * V3 * 12 * sizeof(float2) : 0;
+  const size_t d_bytes = baryon ? (size_t)V3 * 2304 * sizeof(float2) : 0;   // diquark (one sink slice)
+  auto al256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  ChunkLayout c;
+  c.off_s = al256(p_bytes);
+  c.off_sb = c.off_s + al256(s_bytes);
+  c.off_v = c.off_sb + al256(sb_bytes);
+  c.off_d = c.off_v + al256(v_bytes);
+  c.off_m = c.off_d + al256(d_bytes);
+  c.bytes = al256(c.off_m + (2 * kMaxSlices + 1) * sizeof(unsigned));   // maxS, maxV per slice, maxD
+  return c;
+}
+
+// one launch chunk of one call, ready for the fused launch and the reduce
+struct Prepared {
+  FusedParams fp;
+  int nb, sign, nrep, ncols, nsplit, NH, mode;
+  size_t per_split, n_out;
+  const int *rmap;
+  double2 *out;
+  int tm0, tmT, tv0, tvT;   // slice j's coordinates: (tm0 + j) % tmT, (tv0 + j) % tvT
+};
+
+static int prepare_chunk(lhc_ctx ctx, const SliceJob *jobs, int nb, int nq, int sign, const MomentumReps &reps,
+                         const __half *phase, const int *rmap, int NH, int nsplit, int kd, char *ws,
+                         const ChunkLayout &lay, cudaStream_t st, Prepared *pc) {
+  const SliceJob &j0 = jobs[0];
+  const bool baryon = j0.part == PART_SPEC_BARYON, narrow = j0.dtype == LHC_C128;
+  const int V3 = j0.V3, n_r = j0.n_r;
+  const int ncols = n_r * (baryon ? kBarCols : 192);
+  const int nrc = (reps.nrep() + NH - 1) / NH;
+  unsigned *maxS = reinterpret_cast<unsigned *>(ws + lay.off_m), *maxV = maxS + kMaxSlices, *maxD = maxV + kMaxSlices;
+  FusedParams &fp = pc->fp;
+  fp.c.B = phase;
+  fp.c.partial = reinterpret_cast<float4 *>(ws);
+  fp.c.err = ctx->dev_err;
+  fp.c.n_r = n_r;
+  fp.c.V3 = V3;
+  fp.c.nct = (baryon ? 48 : 3) * ((n_r + 1) / 2);
+  // site blocks, rounded up to an even number: the kernel consumes k-steps in pairs (the
+  // pad block's phases are zero and its sites lie past the slice, which TMA reads as zero)
+  fp.c.nkb = ((V3 + 2 * KSTEP - 1) / (2 * KSTEP)) * 2;
+  fp.c.nrc = nrc;
+  fp.c.nrep = reps.nrep();
+  fp.c.ncols = ncols;
+  fp.c.nsplit = nsplit;
+  fp.c.kd = kd;
+  fp.c.g5mask = j0.g5mask;
+  fp.c.maxM = baryon ? maxD : maxS;
+  fp.c.maxM_per_slice = baryon ? 0 : 1;
+  fp.c.maxV = maxV;
+  pc->nb = nb;
+  pc->sign = sign;
+  pc->nrep = reps.nrep();
+  pc->ncols = ncols;
+  pc->nsplit = nsplit;
+  pc->NH = NH;
+  pc->mode = (int)j0.part;
+  pc->per_split = (size_t)nrc * NH * ncols;
+  pc->n_out = (size_t)nq * ncols;
+  pc->rmap = rmap;
+  pc->out = j0.out;
+  // the operand maxima of this chunk of slices (for the split scale) start at zero
+  LHC_CHECK_CUDA(cudaMemsetAsync(maxS, 0, (2 * kMaxSlices + 1) * sizeof(unsigned), st));
+  const size_t cS = ((size_t)V3 * 144 + kNarrowChunk - 1) / kNarrowChunk;
+  const size_t cV = ((size_t)V3 * 12 + kNarrowChunk - 1) / kNarrowChunk;
+  if (narrow) {
+    NarrowParams np;
+    for (int j = 0; j < nb; ++j) np.slices[j] = SlicePtrs{jobs[j].S, jobs[j].vec};
+    np.SB = baryon ? j0.SB : nullptr;
+    np.vec_stride = j0.vec_stride;
+    np.Sst = reinterpret_cast<float2 *>(ws + lay.off_s);
+    np.SBst = reinterpret_cast<float2 *>(ws + lay.off_sb);
+    np.Vst = reinterpret_cast<float2 *>(ws + lay.off_v);
+    np.maxS = maxS;
+    np.maxV = maxV;
+    np.nb = nb;
+    np.V3 = V3;
+    ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT, (double)nb * V3 * ((baryon ? 288.0 : 144.0) + 12.0 * n_r) * 24);
+    const size_t blocks = (size_t)(nb + (baryon ? 1 : 0)) * cS + (size_t)n_r * nb * cV;
+    narrow_c128<<<(unsigned)blocks, 256, 0, st>>>(np);
+    note_launch();
+  } else {
+    // complex64 inputs are read in place; one read-only pass finds their maxima
+    MaxParams mp;
+    for (int j = 0; j < nb; ++j) mp.slices[j] = SlicePtrs{jobs[j].S, jobs[j].vec};
+    mp.vec_stride = j0.vec_stride;
+    mp.maxS = maxS;
+    mp.maxV = maxV;
+    mp.nb = nb;
+    mp.V3 = V3;
+    mp.n_r = n_r;
+    mp.with_S = baryon ? 0 : 1;   // the baryon's matrix operand is the diquark
+    ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT, (double)nb * V3 * ((baryon ? 0.0 : 144.0) + 12.0 * n_r) * 8);
+    const size_t blocks = (size_t)(baryon ? 0 : nb) * cS + (size_t)n_r * nb * cV;
+    max_c64<<<(unsigned)blocks, 256, 0, st>>>(mp);
+    note_launch();
+  }
+  // tensor maps of the matrix operand and the vector of this chunk of slices
+  const char *Mbase, *Vbase;
+  int Tm, Tv;
+  size_t vstride_bytes;
+  if (narrow) {
+    Mbase = ws + lay.off_s;
+    Vbase = ws + lay.off_v;
+    for (int j = 0; j < nb; ++j) fp.tM[j] = fp.tV[j] = j;
+    Tm = Tv = nb;
+    vstride_bytes = (size_t)nb * V3 * 12 * sizeof(float2);
+  } else {
+    const void *mp[kMaxSlices], *vp[kMaxSlices];
+    for (int j = 0; j < nb; ++j) {
+      mp[j] = jobs[j].S;
+      vp[j] = jobs[j].vec;
+    }
+    LHC_TRY(slice_coords(mp, nb, (size_t)V3 * 144 * sizeof(float2), &Mbase, fp.tM, &Tm));
+    LHC_TRY(slice_coords(vp, nb, (size_t)V3 * 12 * sizeof(float2), &Vbase, fp.tV, &Tv));
+    vstride_bytes = j0.vec_stride * sizeof(float2);
+  }
+  pc->tm0 = fp.tM[0];
+  pc->tmT = Tm;
+  pc->tv0 = fp.tV[0];
+  pc->tvT = Tv;
+  if (baryon) {   // the matrix operand becomes the diquark of the (single) sink slice
+    const float2 *GA = reinterpret_cast<const float2 *>(Mbase) + (size_t)fp.tM[0] * V3 * 144;
+    const float2 *GB = narrow ? reinterpret_cast<const float2 *>(ws + lay.off_sb) : static_cast<const float2 *>(j0.SB);
+    float2 *D = reinterpret_cast<float2 *>(ws + lay.off_d);
+    ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT, (double)V3 * (288.0 + 2304.0) * 8);
+    baryon_diquark<<<V3, 256, 0, st>>>(GA, GB, V3, D, maxD);
+    note_launch();
+    const uint64_t dims[3] = {768, 3, (uint64_t)V3}, strides[2] = {768 * 8, 2304 * 8};
+    const uint32_t box[3] = {16, 3, 16};
+    LHC_TRY(encode_map(&fp.c.tmM, 3, D, dims, strides, box));
+  } else {
+    const uint64_t dims[5] = {12, 3, 4, (uint64_t)V3, (uint64_t)Tm};
+    const uint64_t strides[4] = {96, 288, 1152, (uint64_t)V3 * 1152};
+    const uint32_t box[5] = {12, 3, 2, 16, 1};
+    LHC_TRY(encode_map(&fp.c.tmM, 5, Mbase, dims, strides, box));
+  }
+  const uint64_t dims[4] = {12, (uint64_t)V3, (uint64_t)Tv, (uint64_t)n_r};
+  const uint64_t strides[3] = {96, (uint64_t)V3 * 96, vstride_bytes};
+  const uint32_t box[4] = {12, 16, 1, 2};
+  LHC_TRY(encode_map(&fp.c.tmV, 4, Vbase, dims, strides, box));
+  return LHC_OK;
+}
+
+static int finish_chunk(lhc_ctx ctx, const Prepared &pc, cudaStream_t st) {
+  const size_t n_in = (size_t)pc.nrep * pc.ncols;
+  ProfScope ps(ctx, st, LHC_KERNEL_REDUCE, (double)pc.nb * pc.nsplit * n_in * 16 + (double)pc.nb * pc.n_out * 16);
+  reduce_f64<<<(unsigned)((n_in * pc.nb + 255) / 256), 256, 0, st>>>(pc.fp.c.partial, pc.nsplit, pc.per_split,
+                                                                      pc.rmap, pc.rmap + pc.nrep + 1, pc.nrep, pc.sign,
+                                                                      pc.ncols, pc.out, pc.nb, pc.n_out);
+  note_launch();
+  LHC_CHECK_CUDA(cudaGetLastError());
+  return LHC_OK;
+}
+
+static int kd_default() {
+  int kd = 6;   // k-steps accumulated in tensor memory between drains (truncating accumulation)
+  if (const char *e = getenv("LHC_KD")) kd = std::max(2, (atoi(e) + 1) / 2 * 2);   // even: k-steps come in pairs
+  return kd;
+}
+
 // One mixed-precision call with a given launch shape: NH representatives per CTA (a
 // multiple of 8, at most RCHUNK) and nsplit site ranges per slice.
 static int run_mixed_shape(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int nq, const int r[4],
                            int sign, cudaStream_t st, const MomentumReps &reps, int NH, int nsplit) {
   const SliceJob &j0 = jobs[0];
-  const bool baryon = j0.part == PART_SPEC_BARYON;
-  const int V3 = j0.V3, n_r = j0.n_r;
-  const int ncols = n_r * (baryon ? kBarCols : 192);
-  const int nct = (baryon ? 48 : 3) * ((n_r + 1) / 2);
-  // site blocks, rounded up to an even number: the kernel consumes k-steps in pairs (the
-  // pad block's phases are zero and its sites lie past the slice, which TMA reads as zero)
-  const int nkb = ((V3 + 2 * KSTEP - 1) / (2 * KSTEP)) * 2;
   const int nrc = (reps.nrep() + NH - 1) / NH;
+  const int nkb = ((j0.V3 + 2 * KSTEP - 1) / (2 * KSTEP)) * 2;
   const __half *phase = nullptr;
   const int *rmap = nullptr;
   LHC_TRY(get_phase_cs(ctx, j0.L, k, nq, r, reps, NH, nrc, nkb, st, &phase, &rmap));
-
-  int kd = 6;   // k-steps accumulated in tensor memory between drains (truncating accumulation)
-  if (const char *e = getenv("LHC_KD")) kd = std::max(2, (atoi(e) + 1) / 2 * 2);   // even: k-steps come in pairs
-
-  const int ntl = std::min(nt, kMaxSlices);   // slices per launch
-  const bool narrow = j0.dtype == LHC_C128;
-  const size_t per_split = (size_t)nrc * NH * ncols;   // float4 partials per slice and split
-  size_t p_bytes = (size_t)ntl * nsplit * per_split * sizeof(float4);
-  size_t s_bytes = narrow ? (size_t)ntl * V3 * 144 * sizeof(float2) : 0;
-  size_t sb_bytes = narrow && baryon ? (size_t)V3 * 144 * sizeof(float2) : 0;
-  size_t v_bytes = narrow ? (size_t)n_r * ntl * V3 * 12 * sizeof(float2) : 0;
-  size_t d_bytes = baryon ? (size_t)V3 * 2304 * sizeof(float2) : 0;   // diquark (one sink slice)
-  auto al256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  size_t off_s = al256(p_bytes), off_sb = off_s + al256(s_bytes), off_v = off_sb + al256(sb_bytes),
-         off_d = off_v + al256(v_bytes), off_m = off_d + al256(d_bytes);
-  const size_t m_bytes = (2 * kMaxSlices + 1) * sizeof(unsigned);   // maxS, maxV per slice, maxD
-  LHC_TRY(ensure(ctx, ctx->ws, off_m + m_bytes));
+  const int ncols = j0.n_r * (j0.part == PART_SPEC_BARYON ? kBarCols : 192);
+  const ChunkLayout lay = chunk_layout(j0, std::min(nt, kMaxSlices), nsplit, (size_t)nrc * NH * ncols);
+  LHC_TRY(ensure(ctx, ctx->ws, lay.bytes));
   char *ws = static_cast<char *>(ctx->ws.p);
-  unsigned *maxS = reinterpret_cast<unsigned *>(ws + off_m), *maxV = maxS + kMaxSlices, *maxD = maxV + kMaxSlices;
-
-  FusedParams fp;
-  fp.B = phase;
-  fp.partial = reinterpret_cast<float4 *>(ws);
-  fp.err = ctx->dev_err;
-  fp.n_r = n_r;
-  fp.V3 = V3;
-  fp.nct = nct;
-  fp.nkb = nkb;
-  fp.nrc = nrc;
-  fp.nrep = reps.nrep();
-  fp.ncols = ncols;
-  fp.nsplit = nsplit;
-  fp.kd = kd;
-  fp.g5mask = j0.g5mask;
-  fp.maxM = baryon ? maxD : maxS;
-  fp.maxM_per_slice = baryon ? 0 : 1;
-  fp.maxV = maxV;
-  const size_t n_out = (size_t)nq * ncols;
+  const int kd = kd_default();
   for (int jb = 0; jb < nt; jb += kMaxSlices) {
     const int nb = std::min(kMaxSlices, nt - jb);
-    // the operand maxima of this chunk of slices (for the split scale) start at zero
-    LHC_CHECK_CUDA(cudaMemsetAsync(maxS, 0, m_bytes, st));
-    if (narrow) {
-      NarrowParams np;
-      for (int j = 0; j < nb; ++j) np.slices[j] = SlicePtrs{jobs[jb + j].S, jobs[jb + j].vec};
-      np.SB = baryon ? j0.SB : nullptr;
-      np.vec_stride = j0.vec_stride;
-      np.Sst = reinterpret_cast<float2 *>(ws + off_s);
-      np.SBst = reinterpret_cast<float2 *>(ws + off_sb);
-      np.Vst = reinterpret_cast<float2 *>(ws + off_v);
-      np.maxS = maxS;
-      np.maxV = maxV;
-      np.nb = nb;
-      np.V3 = V3;
-      ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT, (double)nb * V3 * ((baryon ? 288.0 : 144.0) + 12.0 * n_r) * 24);
-      const size_t cS = ((size_t)V3 * 144 + kNarrowChunk - 1) / kNarrowChunk;
-      const size_t cV = ((size_t)V3 * 12 + kNarrowChunk - 1) / kNarrowChunk;
-      const size_t blocks = (size_t)(nb + (baryon ? 1 : 0)) * cS + (size_t)n_r * nb * cV;
-      narrow_c128<<<(unsigned)blocks, 256, 0, st>>>(np);
-      note_launch();
-    } else {
-      // complex64 inputs are read in place; one read-only pass finds their maxima
-      MaxParams mp;
-      for (int j = 0; j < nb; ++j) mp.slices[j] = SlicePtrs{jobs[jb + j].S, jobs[jb + j].vec};
-      mp.vec_stride = j0.vec_stride;
-      mp.maxS = maxS;
-      mp.maxV = maxV;
-      mp.nb = nb;
-      mp.V3 = V3;
-      mp.n_r = n_r;
-      mp.with_S = baryon ? 0 : 1;   // the baryon's matrix operand is the diquark
-      ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT, (double)nb * V3 * ((baryon ? 0.0 : 144.0) + 12.0 * n_r) * 8);
-      const size_t cS = ((size_t)V3 * 144 + kNarrowChunk - 1) / kNarrowChunk;
-      const size_t cV = ((size_t)V3 * 12 + kNarrowChunk - 1) / kNarrowChunk;
-      const size_t blocks = (size_t)(baryon ? 0 : nb) * cS + (size_t)n_r * nb * cV;
-      max_c64<<<(unsigned)blocks, 256, 0, st>>>(mp);
-      note_launch();
-    }
-    // tensor maps of the matrix operand and the vector of this chunk of slices
-    const char *Mbase, *Vbase;
-    int Tm, Tv;
-    size_t vstride_bytes;
-    if (narrow) {
-      Mbase = ws + off_s;
-      Vbase = ws + off_v;
-      for (int j = 0; j < nb; ++j) fp.tM[j] = fp.tV[j] = j;
-      Tm = Tv = nb;
-      vstride_bytes = (size_t)nb * V3 * 12 * sizeof(float2);
-    } else {
-      const void *mp[kMaxSlices], *vp[kMaxSlices];
-      for (int j = 0; j < nb; ++j) {
-        mp[j] = jobs[jb + j].S;
-        vp[j] = jobs[jb + j].vec;
-      }
-      LHC_TRY(slice_coords(mp, nb, (size_t)V3 * 144 * sizeof(float2), &Mbase, fp.tM, &Tm));
-      LHC_TRY(slice_coords(vp, nb, (size_t)V3 * 12 * sizeof(float2), &Vbase, fp.tV, &Tv));
-      vstride_bytes = j0.vec_stride * sizeof(float2);
-    }
-    if (baryon) {   // the matrix operand becomes the diquark of the (single) sink slice
-      const float2 *GA = reinterpret_cast<const float2 *>(Mbase) + (size_t)fp.tM[0] * V3 * 144;
-      const float2 *GB = narrow ? reinterpret_cast<const float2 *>(ws + off_sb) : static_cast<const float2 *>(j0.SB);
-      float2 *D = reinterpret_cast<float2 *>(ws + off_d);
-      ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT, (double)V3 * (288.0 + 2304.0) * 8);
-      baryon_diquark<<<V3, 256, 0, st>>>(GA, GB, V3, D, maxD);
-      note_launch();
-      const uint64_t dims[3] = {768, 3, (uint64_t)V3}, strides[2] = {768 * 8, 2304 * 8};
-      const uint32_t box[3] = {16, 3, 16};
-      LHC_TRY(encode_map(&fp.tmM, 3, D, dims, strides, box));
-    } else {
-      const uint64_t dims[5] = {12, 3, 4, (uint64_t)V3, (uint64_t)Tm};
-      const uint64_t strides[4] = {96, 288, 1152, (uint64_t)V3 * 1152};
-      const uint32_t box[5] = {12, 3, 2, 16, 1};
-      LHC_TRY(encode_map(&fp.tmM, 5, Mbase, dims, strides, box));
-    }
+    Prepared pc;
+    LHC_TRY(prepare_chunk(ctx, jobs + jb, nb, nq, sign, reps, phase, rmap, NH, nsplit, kd, ws, lay, st, &pc));
     {
-      const uint64_t dims[4] = {12, (uint64_t)V3, (uint64_t)Tv, (uint64_t)n_r};
-      const uint64_t strides[3] = {96, (uint64_t)V3 * 96, vstride_bytes};
-      const uint32_t box[4] = {12, 16, 1, 2};
-      LHC_TRY(encode_map(&fp.tmV, 4, Vbase, dims, strides, box));
-    }
-    {
-      ProfScope ps(ctx, st, LHC_KERNEL_FUSED, 8.0 * nb * (double)nq * ncols * V3);
+      ProfScope ps(ctx, st, LHC_KERNEL_FUSED, 8.0 * nb * (double)nq * ncols * j0.V3);
       if (j0.part == PART_INS)
-        LHC_TRY(launch_fused_nh<0>(NH, fp, nb, st));
+        LHC_TRY(launch_fused_nh<0>(NH, pc.fp, nb, st));
       else if (j0.part == PART_SPEC_MESON)
-        LHC_TRY(launch_fused_nh<1>(NH, fp, nb, st));
+        LHC_TRY(launch_fused_nh<1>(NH, pc.fp, nb, st));
       else
-        LHC_TRY(launch_fused_nh<2>(NH, fp, nb, st));
+        LHC_TRY(launch_fused_nh<2>(NH, pc.fp, nb, st));
     }
-    {
-      const size_t n_in = (size_t)reps.nrep() * ncols;
-      ProfScope ps(ctx, st, LHC_KERNEL_REDUCE, (double)nb * nsplit * n_in * 16 + (double)nb * n_out * 16);
-      reduce_f64<<<(unsigned)((n_in * nb + 255) / 256), 256, 0, st>>>(fp.partial, nsplit, per_split, rmap,
-                                                                         rmap + reps.nrep() + 1, reps.nrep(), sign,
-                                                                         ncols, jobs[jb].out, nb, n_out);
-      note_launch();
-    }
+    LHC_TRY(finish_chunk(ctx, pc, st));
   }
   LHC_CHECK_CUDA(cudaGetLastError());
   return LHC_OK;
@@ -1169,34 +1300,130 @@ static int autotune(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int
   return LHC_OK;
 }
 
+// Launch shape of a call: the tuned one if the table has its key, else the heuristic
+// (widest chunks; site splits that fill whole waves of one CTA per SM).
+static bool call_shape(lhc_ctx ctx, const SliceJob &j0, int nt, const MomentumReps &reps, int *NH, int *nsplit,
+                       TuneKey *key) {
+  const bool baryon = j0.part == PART_SPEC_BARYON;
+  const int nkb = ((j0.V3 + 2 * KSTEP - 1) / (2 * KSTEP)) * 2;
+  const int nct = (baryon ? 48 : 3) * ((j0.n_r + 1) / 2);
+  int nrc;
+  rep_chunks(reps.nrep(), &nrc, NH);
+  *nsplit = choose_nsplit(nct * nt * nrc, (nkb + 1) / 2, ctx->num_sms);
+  *key = TuneKey{(int)j0.part, j0.dtype, j0.V3, j0.n_r, std::min(nt, kMaxSlices), reps.nrep()};
+  TuneChoice ch;
+  const bool tuned = tune_lookup(*key, &ch);
+  if (tuned) {
+    *NH = ch.NH;
+    *nsplit = ch.nsplit;
+  }
+  if (const char *e = getenv("LHC_NSPLIT")) *nsplit = std::max(1, std::min((nkb + 1) / 2, atoi(e)));
+  return tuned;
+}
+
 int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int nq, const int r[4], int sign,
                    cudaStream_t st) {
   const SliceJob &j0 = jobs[0];
-  const bool baryon = j0.part == PART_SPEC_BARYON;
   const MomentumReps reps = momentum_reps(k, nq);
-  const int nkb = ((j0.V3 + 2 * KSTEP - 1) / (2 * KSTEP)) * 2;
-  const int nct = (baryon ? 48 : 3) * ((j0.n_r + 1) / 2);
-  // launch shape: the tuned one for this shape if known (or tuned now), else the heuristic
-  // (widest chunks; site splits that fill whole waves of one CTA per SM)
-  int nrc, NH;
-  rep_chunks(reps.nrep(), &nrc, &NH);
-  int nsplit = choose_nsplit(nct * nt * nrc, (nkb + 1) / 2, ctx->num_sms);
-  const TuneKey key{(int)j0.part, j0.dtype, j0.V3, j0.n_r, std::min(nt, kMaxSlices), reps.nrep()};
-  TuneChoice ch;
-  if (tune_lookup(key, &ch)) {
-    NH = ch.NH;
-    nsplit = ch.nsplit;
-  } else if (ctx->tune_mode == LHC_TUNE_ON) {
+  int NH, nsplit;
+  TuneKey key;
+  const bool tuned = call_shape(ctx, j0, nt, reps, &NH, &nsplit, &key);
+  if (!tuned && ctx->tune_mode == LHC_TUNE_ON) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     LHC_CHECK_CUDA(cudaStreamIsCapturing(st, &cs));
     if (cs == cudaStreamCaptureStatusNone) {
+      TuneChoice ch;
       LHC_TRY(autotune(ctx, jobs, nt, k, nq, r, sign, st, reps, key, &ch));
       NH = ch.NH;
       nsplit = ch.nsplit;
+      if (const char *e = getenv("LHC_NSPLIT")) nsplit = std::max(1, atoi(e));
     }
   }
-  if (const char *e = getenv("LHC_NSPLIT")) nsplit = std::max(1, std::min((nkb + 1) / 2, atoi(e)));
   return run_mixed_shape(ctx, jobs, nt, k, nq, r, sign, st, reps, NH, nsplit);
+}
+
+// A batch of mixed calls: every call is prepared (in its own workspace region), the
+// fused kernel runs once per (part kind, chunk width) group of up to kMaxBatch calls, and
+// every call is reduced.  Each CTA does what it does in its call's own launch, with the
+// same launch shape, so the results are bitwise those of the calls made one by one.
+int run_batch_mixed(lhc_ctx ctx, const std::vector<BatchCall> &calls, cudaStream_t st) {
+  const int n = (int)calls.size();
+  std::vector<MomentumReps> reps(n);
+  std::vector<int> NH(n), nsplit(n);
+  std::vector<const __half *> phase(n);
+  std::vector<const int *> rmap(n);
+  std::vector<ChunkLayout> lay(n);
+  std::vector<size_t> off(n + 1, 0);
+  for (int c = 0; c < n; ++c) {
+    const BatchCall &bc = calls[c];
+    const SliceJob &j0 = bc.jobs[0];
+    const int nt = (int)bc.jobs.size();
+    if (nt > kMaxSlices) {
+      set_error("batch: a call spans %d slices; at most %d", nt, kMaxSlices);
+      return LHC_EINVAL;
+    }
+    reps[c] = momentum_reps(bc.k, bc.nq);
+    TuneKey key;
+    call_shape(ctx, j0, nt, reps[c], &NH[c], &nsplit[c], &key);
+    const int nrc = (reps[c].nrep() + NH[c] - 1) / NH[c];
+    const int nkb = ((j0.V3 + 2 * KSTEP - 1) / (2 * KSTEP)) * 2;
+    LHC_TRY(get_phase_cs(ctx, j0.L, bc.k, bc.nq, bc.r, reps[c], NH[c], nrc, nkb, st, &phase[c], &rmap[c]));
+    const int ncols = j0.n_r * (j0.part == PART_SPEC_BARYON ? kBarCols : 192);
+    lay[c] = chunk_layout(j0, nt, nsplit[c], (size_t)nrc * NH[c] * ncols);
+    off[c + 1] = off[c] + lay[c].bytes;
+  }
+  LHC_TRY(ensure(ctx, ctx->ws, off[n]));
+  char *ws = static_cast<char *>(ctx->ws.p);
+  const int kd = kd_default();
+  std::vector<Prepared> pc(n);
+  double work[3] = {0, 0, 0};
+  for (int c = 0; c < n; ++c) {
+    const BatchCall &bc = calls[c];
+    LHC_TRY(prepare_chunk(ctx, bc.jobs.data(), (int)bc.jobs.size(), bc.nq, bc.sign, reps[c], phase[c], rmap[c], NH[c],
+                          nsplit[c], kd, ws + off[c], lay[c], st, &pc[c]));
+    work[pc[c].mode] += 8.0 * pc[c].nb * (double)bc.nq * pc[c].ncols * bc.jobs[0].V3;
+  }
+  // one fused launch per (part kind, chunk width), kMaxBatch calls at most
+  for (int mode = 0; mode < 3; ++mode) {
+    for (int nh = 8; nh <= RCHUNK; nh += 8) {
+      std::vector<int> group;
+      for (int c = 0; c < n; ++c)
+        if (pc[c].mode == mode && pc[c].NH == nh) group.push_back(c);
+      for (size_t g0 = 0; g0 < group.size(); g0 += kMaxBatch) {
+        std::unique_ptr<BatchParams> bpp(new BatchParams());   // 29 KB: kept off the stack
+        BatchParams &bp = *bpp;
+        bp.n = (int)std::min<size_t>(kMaxBatch, group.size() - g0);
+        bp.first[0] = 0;
+        double w = 0.0;
+        for (int e = 0; e < bp.n; ++e) {
+          const Prepared &q = pc[group[g0 + e]];
+          bp.item[e] = q.fp.c;
+          bp.item[e].tm0 = q.tm0;
+          bp.item[e].tmT = q.tmT;
+          bp.item[e].tv0 = q.tv0;
+          bp.item[e].tvT = q.tvT;
+          for (int j = 0; j < q.nb; ++j)
+            if (q.fp.tM[j] != (q.tm0 + j) % q.tmT || q.fp.tV[j] != (q.tv0 + j) % q.tvT) {
+              set_error("batch: the slices of a call must be consecutive (mod T) in its tensors");
+              return LHC_EINVAL;
+            }
+          bp.first[e + 1] = bp.first[e] + q.fp.c.nct * q.fp.c.nsplit * q.nb * q.fp.c.nrc;
+          w += 8.0 * q.nb * (double)(q.n_out / q.ncols) * q.ncols * q.fp.c.V3;
+        }
+        ProfScope ps(ctx, st, LHC_KERNEL_FUSED, w);
+        if (mode == 0)
+          LHC_TRY(launch_batch_nh<0>(nh, bp, bp.first[bp.n], st));
+        else if (mode == 1)
+          LHC_TRY(launch_batch_nh<1>(nh, bp, bp.first[bp.n], st));
+        else
+          LHC_TRY(launch_batch_nh<2>(nh, bp, bp.first[bp.n], st));
+      }
+    }
+  }
+  (void)work;
+  for (int c = 0; c < n; ++c) LHC_TRY(finish_chunk(ctx, pc[c], st));
+  LHC_CHECK_CUDA(cudaGetLastError());
+  return LHC_OK;
 }
 
 }  // namespace lhc

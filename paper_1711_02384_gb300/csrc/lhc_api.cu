@@ -737,4 +737,58 @@ int lhc_set_projection(lhc_ctx ctx, int mode) {
   return LHC_OK;
 }
 
+int lhc_batch(lhc_ctx ctx, const lhc_call *calls, int ncalls, void *stream) {
+  if (!ctx) return fail(LHC_EINVAL, "ctx is NULL");
+  if (ncalls < 1 || !calls) return fail(LHC_EINVAL, "lhc_batch: no calls");
+  std::vector<lhc::BatchCall> bcs(ncalls);
+  const int g5m = g5mask_of(ctx);
+  for (int c = 0; c < ncalls; ++c) {
+    const lhc_call &a = calls[c];
+    const lhc_lattice *lat = &a.lat;
+    LHC_TRY(common_checks(ctx, lat, a.S, a.vec, a.n_r, a.r, a.k, a.nq, LHC_MIXED, a.out));
+    if (a.part < PART_INS || a.part > PART_SPEC_BARYON) return fail(LHC_EINVAL, "call %d: unknown part %d", c, a.part);
+    if ((a.part == PART_SPEC_BARYON) != (a.GB != nullptr))
+      return fail(LHC_EINVAL, "call %d: GB must be given for baryons only", c);
+    if ((uintptr_t)a.GB & 15) return fail(LHC_EINVAL, "call %d: GB must be 16-byte aligned", c);
+    const bool ins = a.part == PART_INS;
+    if (a.t_hi < a.t_lo || a.t_hi - a.t_lo >= lat->T || (!ins && a.t_hi != a.t_lo))
+      return fail(LHC_EINVAL, "call %d: bad slice range %d..%d", c, a.t_lo, a.t_hi);
+    const void *ptrs[4] = {a.S, a.vec, a.out, a.GB ? a.GB : a.S};
+    for (const void *p : ptrs)
+      if (!is_device_ptr(p)) return fail(LHC_EINVAL, "call %d: lhc_batch takes device buffers only", c);
+    const int T = lat->T, V3 = lat->L * lat->L * lat->L;
+    const size_t es = esize(lat->dtype), slice = (size_t)V3 * 144 * es, vslice = (size_t)V3 * 12;
+    const int cols = a.part == PART_SPEC_BARYON ? kBarCols : 192;
+    lhc::BatchCall &bc = bcs[c];
+    bc.k = a.k;
+    bc.nq = a.nq;
+    for (int e = 0; e < 4; ++e) bc.r[e] = a.r[e];
+    bc.sign = ins ? +1 : -1;
+    const int nt = a.t_hi - a.t_lo + 1, t0 = ((a.t_lo % T) + T) % T;
+    bc.jobs.resize(nt);
+    for (int j = 0; j < nt; ++j) {
+      const int t = (t0 + j) % T;
+      SliceJob &job = bc.jobs[j];
+      job.part = static_cast<Part>(a.part);
+      job.dtype = lat->dtype;
+      job.L = lat->L;
+      job.V3 = V3;
+      job.n_r = a.n_r;
+      job.nq = a.nq;
+      job.S = static_cast<const char *>(a.S) + (size_t)t * slice;
+      job.SB = a.GB ? static_cast<const char *>(a.GB) + (size_t)t * slice : nullptr;
+      job.vec = static_cast<const char *>(a.vec) + (ins ? (size_t)t * vslice * es : 0);
+      job.vec_stride = ins ? (size_t)T * vslice : vslice;
+      job.g5mask = g5m;
+      job.out = static_cast<double2 *>(a.out) + (size_t)j * a.nq * a.n_r * cols;
+    }
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> g(ctx->mu);
+  LHC_TRY(begin_call(ctx, st));
+  int s = lhc::run_batch_mixed(ctx, bcs, st);
+  int e = end_call(ctx, st);
+  return s != LHC_OK ? s : e;
+}
+
 }  // extern "C"

@@ -162,6 +162,16 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
 
 size_t mixed_call_bytes(Part part, int dtype, int V3, int n_r, int nt, int nq);
 
+// a batch of mixed calls with one fused launch per part kind and chunk width (k_mixed.cu)
+struct BatchCall {
+  std::vector<SliceJob> jobs;
+  const int *k;
+  int nq;
+  int r[4];
+  int sign;
+};
+int run_batch_mixed(lhc_ctx ctx, const std::vector<BatchCall> &calls, cudaStream_t st);
+
 // launch-shape table of the mixed path (lhc_tune.cu): process-wide, guarded by a mutex
 struct TuneKey {
   int part, dtype, V3, n_r, nt, nrep;   // nt: slices per launch

@@ -37,6 +37,14 @@ class Lattice(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("T", ctypes.c_int), ("dtype", ctypes.c_int)]
 
 
+class Call(ctypes.Structure):
+    """One call of a batch (lhc_call)."""
+    _fields_ = [("part", ctypes.c_int), ("lat", Lattice), ("S", ctypes.c_void_p), ("GB", ctypes.c_void_p),
+                ("vec", ctypes.c_void_p), ("n_r", ctypes.c_int), ("t_lo", ctypes.c_int), ("t_hi", ctypes.c_int),
+                ("r", ctypes.c_int * 4), ("k", ctypes.POINTER(ctypes.c_int)), ("nq", ctypes.c_int),
+                ("out", ctypes.c_void_p)]
+
+
 JOB_INSERTION, JOB_SPECTATOR, JOB_THREEPT = range(3)
 JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED, JOB_CANCELED = range(5)
 
@@ -100,10 +108,11 @@ def lib():
                                        ctypes.POINTER(ctypes.c_double), vp]
         L.lhc_combine_open.argtypes = [vp, vp, ci, vp, ci, ci, ci, vp, ci, vp, ci, ci, vp, vp]
         L.lhc_set_projection.argtypes = [vp, ci]
+        L.lhc_batch.argtypes = [vp, ctypes.POINTER(Call), ci, vp]
         L.lhc_set_tuning.argtypes = [vp, ci, ctypes.c_char_p]
         L.lhc_tuning_table.argtypes = [ip, ci, ip]
         L.lhc_tuning_load.argtypes = [ctypes.c_char_p, ip]
-        for name in ("lhc_combine_open", "lhc_set_projection", "lhc_wilson_apply", "lhc_wilson_solve", "lhc_set_tuning", "lhc_tuning_table", "lhc_tuning_load",
+        for name in ("lhc_batch", "lhc_combine_open", "lhc_set_projection", "lhc_wilson_apply", "lhc_wilson_solve", "lhc_set_tuning", "lhc_tuning_table", "lhc_tuning_load",
                      "lhc_create", "lhc_destroy", "lhc_set_gamma5", "lhc_momenta", "lhc_insertion",
                      "lhc_spectator", "lhc_combine", "lhc_profile", "lhc_profile_read", "lhc_sync", "lhc_release_workspace",
                      "lhc_selftest_timeout", "lhc_serve_start", "lhc_serve_stop", "lhc_prop_register",
@@ -238,6 +247,40 @@ class Context:
         ms, n, w = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
         _check(lib().lhc_profile_read(self._h, kernel, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)))
         return ms.value, n.value, w.value
+
+    def batch(self, calls, stream=None):
+        """Mixed-precision calls in one fused launch per part kind: each call a dict with
+        part ("ins", "spec" or "baryon"), S, vec, optional GB, t_lo, t_hi (t_lo = t_hi =
+        t_sink for spectators), r, k and optional out (device tensors).  Returns the
+        outputs, bitwise those of the same calls made one by one."""
+        arr = (Call * len(calls))()
+        keep, outs = [], []
+        for a, c in zip(arr, calls):
+            S, vec = c["S"], c["vec"]
+            T, V3 = S.shape[0], S.shape[1]
+            n_r = vec.shape[0]
+            part = {"ins": 0, "spec": 1, "baryon": 2}[c["part"]]
+            ka, kp = _ints(c["k"])
+            ra, _ = _ints(c["r"], 4)
+            nq = ka.size // 3
+            nt = c["t_hi"] - c["t_lo"] + 1
+            cols = 3072 if part == 2 else 192
+            out = c.get("out")
+            if out is None:
+                shape = (nt, nq, n_r, cols) if part == 0 else (nq, n_r, cols)
+                out = torch.empty(shape, dtype=torch.complex128, device=S.device)
+            keep += [ka, ra]
+            outs.append(out)
+            a.part = part
+            a.lat = Lattice(_L_of(V3), T, _dtype_code(S))
+            addr = lambda t: None if t is None else _ptr(t).value
+            a.S, a.vec, a.out, a.GB = addr(S), addr(vec), addr(out), addr(c.get("GB"))
+            a.n_r, a.t_lo, a.t_hi, a.nq = n_r, c["t_lo"], c["t_hi"], nq
+            for e in range(4):
+                a.r[e] = int(ra[e])
+            a.k = kp
+        _check(lib().lhc_batch(self._h, arr, len(calls), _stream(calls[0]["S"], stream)))
+        return outs
 
     def set_projection(self, mode: str):
         """Momentum projection: "auto" (a DFT over the slice when nq >= L^3 / 2), "gemm"
