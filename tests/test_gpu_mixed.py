@@ -126,6 +126,29 @@ def test_meson_24c48_sampled_slices(ctx):
     assert report("24c48 spec", CS.block_err(gs, ref, 1)) < CS.MIXED_TOL
 
 
+def test_meson_48c_largest_served_lattice(ctx):
+    """The largest lattice of the served workload (48^3, 110592 sites: the longest sums
+    over sites per slice) at full size: one insertion slice and the spectator, 4 noises,
+    93 momenta, complex64 inputs, against the oracle on the same complex64-rounded inputs."""
+    from oracle.momenta import momenta
+    from oracle import contractions as OC
+    from paper_1711_02384_gb300 import inputs
+    L, n_r, t = 48, 4, 1
+    k = momenta(8)
+    S = inputs.propagator(2600, L, 2, slices=[0, 1]).astype(np.complex64)
+    psi = inputs.solutions(2601, L, 2, n_r, slices=[0, 1]).astype(np.complex64)
+    eta = inputs.noise(2602, L, n_r, t).astype(np.complex64)
+    r = np.array([5, 17, 40, 0], dtype=np.int32)
+    g5 = CS.g5_matrix()
+    gi = ctx.insertion(dev(S), dev(psi), t, t, r, k, prec="mixed").cpu().numpy()
+    gs = ctx.spectator(dev(S), dev(eta), t, r, k, prec="mixed").cpu().numpy()
+    ctx.sync()
+    ri = OC.insertion(S[t:t + 1].astype(complex), psi[:, t:t + 1].astype(complex), g5, r[:3], k, L)
+    rs = OC.spectator_meson(S[t].astype(complex), eta.astype(complex), g5, r[:3], k, L)
+    assert report("48c ins", CS.block_err(gi, ri, 2)) < CS.MIXED_TOL
+    assert report("48c spec", CS.block_err(gs, rs, 1)) < CS.MIXED_TOL
+
+
 def test_noise_offset_beyond_int32(ctx):
     """complex64 solutions whose noise offset (noise x T x V3 x 12 elements) passes 2^31
     for the last noises: 16^3 x 1536 lattice, 32 noises, two insertion slices near the end
