@@ -77,9 +77,11 @@ def make_inputs():
 
 
 def gamma_sets():
-    from oracle import gamma as OG          # the 16 Dirac structures (plain constants)
-    g16 = OG.gamma16(OG.chiral())
-    g4 = np.broadcast_to(OG.chiral()[3], (16, 4, 4)).copy()
+    """Gamma_snk, Gamma_ins, Gamma_src of the combine: the 16 Dirac structures at sink and
+    source, gamma_4 at the insertion."""
+    from paper_1711_02384_gb300 import inputs
+    g16 = inputs.dirac_structures()
+    g4 = np.broadcast_to(inputs.dirac_matrices()[3], (16, 4, 4)).copy()
     return g16, g4, g16.copy()
 
 

@@ -179,3 +179,30 @@ def source_positions(seed: int, L: int, T: int, n: int) -> np.ndarray:
     out[:, 2] = w[:, 2] % L
     out[:, 3] = w[:, 3] % T
     return out
+
+
+def dirac_matrices() -> np.ndarray:
+    """Euclidean Dirac matrices gamma_1..gamma_4 in a chiral basis, complex128 [4][4][4]:
+    gamma_k = [[0, -i sigma_k], [i sigma_k, 0]], gamma_4 = [[0, 1], [1, 0]], Hermitian,
+    with gamma_1 gamma_2 gamma_3 gamma_4 = diag(1, 1, -1, -1) (the library's default
+    gamma5).  Input data for the benchmark's Gamma structures."""
+    sig = [np.array([[0, 1], [1, 0]], dtype=complex), np.array([[0, -1j], [1j, 0]]),
+           np.array([[1, 0], [0, -1]], dtype=complex)]
+    z, one = np.zeros((2, 2), dtype=complex), np.eye(2, dtype=complex)
+    g = [np.block([[z, -1j * sk], [1j * sk, z]]) for sk in sig] + [np.block([[z, one], [one, z]])]
+    return np.array(g)
+
+
+def dirac_structures() -> np.ndarray:
+    """The 16 products gamma_1^n1 gamma_2^n2 gamma_3^n3 gamma_4^n4 (n in {0, 1}), indexed
+    by n1 + 2 n2 + 4 n3 + 8 n4, complex128 [16][4][4]."""
+    g = dirac_matrices()
+    out = np.empty((16, 4, 4), dtype=complex)
+    for n in range(16):
+        m = np.eye(4, dtype=complex)
+        for mu in range(4):
+            if (n >> mu) & 1:
+                m = m @ g[mu]
+        out[n] = m
+    return out
+

@@ -241,3 +241,19 @@ def test_baryon_exchange_is_an_index_permutation():
     ab = OC.spectator_baryon(GA, GB, eta, g5, r3, k, L).reshape(len(k), n_r, 4, 4, 4, 4, 4, 3)
     ba = OC.spectator_baryon(GB, GA, eta, g5, r3, k, L).reshape(len(k), n_r, 4, 4, 4, 4, 4, 3)
     assert np.abs(ba - ab.transpose(0, 1, 4, 5, 2, 3, 6, 7)).max() < 1e-12 * np.abs(ab).max()
+
+
+def test_benchmark_dirac_basis_is_a_clifford_basis():
+    """The benchmark's Gamma structures (built in the input module, apart from the
+    oracle): Hermitian gamma_mu with {gamma_mu, gamma_nu} = 2 delta, gamma5 =
+    diag(1, 1, -1, -1), and 16 products that span the 4x4 matrices."""
+    import numpy as np
+    from paper_1711_02384_gb300 import inputs
+    g = inputs.dirac_matrices()
+    for a in range(4):
+        assert np.allclose(g[a], g[a].conj().T)
+        for b in range(4):
+            assert np.allclose(g[a] @ g[b] + g[b] @ g[a], 2 * (a == b) * np.eye(4))
+    assert np.allclose(g[0] @ g[1] @ g[2] @ g[3], np.diag([1, 1, -1, -1]))
+    G = inputs.dirac_structures().reshape(16, 16)
+    assert np.linalg.matrix_rank(G) == 16
