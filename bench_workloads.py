@@ -13,6 +13,12 @@ mom1      the meson 24^3x48 step at 1 momentum vs 93 momenta (the paper's observ
           many more momenta cost little extra)
 allmom    every momentum of a 16^3 slice (4096): the projection as a discrete Fourier
           transform (FP64) against the direct FP64 and mixed projections
+paper     the paper's own measurement on its lattice shape: 32^3 x 96, source at t = 30,
+          sinks 10 slices before and after it, 50 noises on both sink slices, 93 momenta at
+          sink and insertion, meson and baryon spectators, one insertion call over both
+          directions, combines; time per configuration (the paper quotes about 575 s on 8
+          KNL nodes for its whole measurement, as context)
+extras    the open-spin combine's 16 x 16 Dirac sweep and the free-field solver, timed
 
 Inputs are seeded random device tensors (torch): these rows measure throughput; parity
 is the tests' job.  Each row prints one JSON line.
@@ -394,10 +400,97 @@ def run_allmom(args, dev, g):
                       "dft_vs_gemm_mixed": out["gemm_mixed"]["ms_per_step"] / out["dft_fp64"]["ms_per_step"]}))
 
 
+# --------------------------------------------------------------------------- paper
+
+def run_paper(args, dev, g):
+    L, NR, D = 32, 50, 10
+    V3 = L ** 3
+    nsl = 2 * D + 1                                   # slab of slices x4' .. x4'' (source in the middle)
+    k = lhc.momenta(8)
+    nq = len(k)
+    S = _rand((nsl, V3, 12, 12), torch.complex128, dev, g)
+    psi = _rand((NR, nsl, V3, 12), torch.complex128, dev, g)
+    eta_b = _rand((NR, V3, 12), torch.complex128, dev, g)     # the noise on the backward sink slice
+    eta_f = _rand((NR, V3, 12), torch.complex128, dev, g)     # and on the forward one
+    g16 = torch.from_numpy(B.gamma_sets()[0]).to(dev)
+    g4 = torch.from_numpy(B.gamma_sets()[1]).to(dev)
+    Ws = _rand((4, 4, 4, 4), torch.complex128, dev, g)
+    Wc = _rand((4, 4, 4, 4), torch.complex128, dev, g)
+    ctx = lhc.Context(0)
+    ctx.set_tuning(not args.no_tune)
+    r = (0, 0, 0, D)                                  # slab index of the source time (t = 30 of 96)
+    oi = torch.empty((nsl, nq, NR, 192), dtype=torch.complex128, device=dev)
+    om = [torch.empty((nq, NR, 192), dtype=torch.complex128, device=dev) for _ in range(2)]
+    ob = [torch.empty((nq, NR, 3072), dtype=torch.complex128, device=dev) for _ in range(2)]
+    cm = [torch.empty((D + 1, 16, nq, nq), dtype=torch.complex128, device=dev) for _ in range(2)]
+    cb = [torch.empty((D + 1, 4, nq, nq), dtype=torch.complex128, device=dev) for _ in range(2)]
+
+    def step():
+        ctx.insertion(S, psi, 0, nsl - 1, r, k, prec=args.prec, out=oi)   # both directions in one call
+        for d, (ts, eta) in enumerate(((0, eta_b), (nsl - 1, eta_f))):
+            ctx.spectator(S, eta, ts, r, k, prec=args.prec, out=om[d])
+            ctx.spectator(S, eta, ts, r, k, prec=args.prec, GB=S, out=ob[d])
+            ins = oi[0:D + 1] if d == 0 else oi[D:nsl]
+            ctx.combine(om[d], ins, g16, g4, g16, prec=args.prec, out=cm[d])
+            ctx.combine(ob[d], ins, Ws, g4[:4], Wc, prec=args.prec, out=cb[d])
+
+    ms, clk, nl = _timed(step, args.steps, args.warmup, dev)
+    units = (nsl + 4) * V3 * NR * nq
+    ctx.close()
+    _line(args, B.METRIC, units * args.steps / (ms / 1e3), ms / args.steps,
+          "the paper's measurement shape: 32^3x96, source t=30, sinks t=20 and t=40 (forward and backward), "
+          "50 noises on both sink slices, 93 momenta at sink and insertion, one insertion call over t=20..40, "
+          "meson and baryon spectators, meson combine (16 structures) and baryon combine (4) per direction, "
+          "complex128 inputs",
+          {"clocks": clk, "units_per_step": units, "gpu_launches": nl,
+           "ms_per_configuration": ms / args.steps,
+           "paper_context": "about 575 s per configuration on 8 KNL nodes (QPACE3) for the paper's whole "
+                            "measurement with k^2, k'^2 <= 8; other hardware, and its scope (I/O, smearing) differs"})
+
+
+# --------------------------------------------------------------------------- extras
+
+def run_extras(args, dev, g):
+    ctx = lhc.Context(0)
+    out = {}
+    # the open-spin combine's sweep over all 16 x 16 x 16 Dirac structures on one slice
+    nq, NR = 93, 16
+    spec = _rand((nq, NR, 192), torch.complex128, dev, g)
+    ins = _rand((1, nq, NR, 192), torch.complex128, dev, g)
+    g16 = torch.from_numpy(B.gamma_sets()[0]).to(dev)
+    res = torch.empty((1, 16, 16, nq, nq, 4, 4), dtype=torch.complex128, device=dev)
+    for prec in ("mixed", "fp64"):
+        ms, clk, nl = _timed(lambda: ctx.combine_open(spec, ins, g16, g16, prec=prec, out=res), args.steps,
+                             args.warmup, dev)
+        out["open_combine_" + prec] = {"ms_per_sweep": ms / args.steps,
+                                       "correlators_per_s": 16 ** 3 * nq * nq * args.steps / (ms / 1e3),
+                                       "clocks": clk}
+    # free-field Wilson-Dirac solves: 12 point sources on 16^3 x 32
+    from paper_1711_02384_gb300 import inputs
+    L, T = 16, 32
+    src = torch.zeros((12, T, L ** 3, 12), dtype=torch.complex128, device=dev)
+    for sc in range(12):
+        src[sc, 0, 0, sc] = 1.0
+    gam = inputs.dirac_matrices()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    sol, it, rr = ctx.wilson_solve(src, 0.3, gam, tol=1e-12)
+    torch.cuda.synchronize(dev)
+    out["free_solve_16c32"] = {"ms": 1e3 * (time.perf_counter() - t0), "rhs": 12, "iterations": it,
+                               "relative_residual": rr, "mass": 0.3}
+    ctx.close()
+    print(json.dumps({"metric": "open-spin combine sweep and free-field solve", "unit": "ms", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+                      "data": "synthetic (seeded random device tensors)",
+                      "config": {"workload": "Dirac sweep 16x16x16 over one slice (93x93 momenta, 16 noises); "
+                                             "12 point sources, free Wilson-Dirac, 16^3x32, m = 0.3"},
+                      "runs": out}))
+
+
 def run(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     g = torch.Generator(device=dev)
     g.manual_seed(1711)
     {"baryon32": run_baryon32, "batched": run_batched, "serve": run_serve, "mom1": run_mom1,
-     "allmom": run_allmom}[args.workload](args, dev, g)
+     "allmom": run_allmom, "paper": run_paper, "extras": run_extras}[args.workload](args, dev, g)
