@@ -18,7 +18,8 @@ paper     the paper's own measurement on its lattice shape: 32^3 x 96, source at
           sink and insertion, meson and baryon spectators, one insertion call over both
           directions, combines; time per configuration (the paper quotes about 575 s on 8
           KNL nodes for its whole measurement, as context)
-extras    the open-spin combine's 16 x 16 Dirac sweep and the free-field solver, timed
+extras    the open-spin combine's 16 x 16 Dirac sweep, the baryon open combine (source spins
+          open) and the free-field solver, timed
 
 Inputs are seeded random device tensors (torch): these rows measure throughput; parity
 is the tests' job.  Each row prints one JSON line.
@@ -465,6 +466,18 @@ def run_extras(args, dev, g):
         out["open_combine_" + prec] = {"ms_per_sweep": ms / args.steps,
                                        "correlators_per_s": 16 ** 3 * nq * nq * args.steps / (ms / 1e3),
                                        "clocks": clk}
+    # the baryon open combine: 4 sink structures x 16 insertion Gammas, source spins open
+    bspec = _rand((nq, NR, 3072), torch.complex128, dev, g)
+    w4 = _rand((4, 4, 4, 4), torch.complex128, dev, g)
+    bres = torch.empty((1, 4, 16, nq, nq, 4, 4, 4), dtype=torch.complex128, device=dev)
+    for prec in ("mixed", "fp64"):
+        ms, clk, nl = _timed(lambda: ctx.combine_open_baryon(bspec, ins, w4, g16, prec=prec, out=bres), args.steps,
+                             args.warmup, dev)
+        out["open_baryon_combine_" + prec] = {"ms_per_call": ms / args.steps, "sink_structures": 4,
+                                              "insertion_gammas": 16,
+                                              "open_blocks_per_s": 4 * 16 * nq * nq * args.steps / (ms / 1e3),
+                                              "clocks": clk}
+    del bspec, bres
     # free-field Wilson-Dirac solves: 12 point sources on 16^3 x 32
     from paper_1711_02384_gb300 import inputs
     L, T = 16, 32
@@ -483,6 +496,7 @@ def run_extras(args, dev, g):
                       "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
                       "data": "synthetic (seeded random device tensors)",
                       "config": {"workload": "Dirac sweep 16x16x16 over one slice (93x93 momenta, 16 noises); "
+                                             "baryon open combine, 4 W_snk x 16 Gamma_ins, (a1, a2, b) open; "
                                              "12 point sources, free Wilson-Dirac, 16^3x32, m = 0.3"},
                       "runs": out}))
 

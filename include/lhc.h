@@ -291,6 +291,28 @@ unsigned long long lhc_launch_count(void);
 int lhc_combine_open(lhc_ctx ctx, const void *spec, int np, const void *ins, int nq, int n_r, int nt,
                      const void *snk, int ngs, const void *ins_g, int ngi, int prec, void *out, void *stream);
 
+/* Open-source-spin combine (baryon): Eq. 8 for the baryon with the source structure
+ * W_src left open (Sec. 2: with open indices every spin structure, parity projector or
+ * diquark, follows after the expensive contractions),
+ *
+ *   out[t][gs][gi][p][q][(a1*4 + a2)*4 + b]
+ *     = (1/N) sum_i sum_c Bhat_i[gs](p)[(a1*4 + a2)*3 + c] Ihat_i[t][gi](q)[b*3 + c],
+ *   Bhat_i[gs] = sum_{a1p,a2p,bp} Wsnk[gs][a1p][a2p][bp]
+ *                  spec_i[((((a1p*4 + a1)*4 + a2p)*4 + a2)*4 + bp)*3 + c],
+ *   Ihat_i[gi] = sum_{at,bt} Gins[gi][at][bt] ins_i[(at*4 + bt)*12 + b*3 + c],
+ *
+ * lhc_combine's baryon quantities before W_src is applied. For any source structure,
+ *   C = sum_{a1,a2,b} Wsrc[a1][a2][b] out[...][(a1*4 + a2)*4 + b]
+ * equals lhc_combine's LHC_BARYON result for (Wsnk[gs], Gins[gi], Wsrc).
+ * spec: [np][n_r][3072] (lhc_spectator, LHC_BARYON), ins: [nt][nq][n_r][192],
+ * wsnk: [ngs][4][4][4], ins_g: [ngi][4][4]; out: complex128 [nt][ngs][ngi][np][nq][64];
+ * nt*ngs*ngi <= 65535, ngs <= 150 (shared memory). Device buffers only (LHC_EINVAL
+ * otherwise). prec as for lhc_combine: LHC_MIXED sums each group of four noises in
+ * FP32 and the groups exactly. */
+int lhc_combine_open_baryon(lhc_ctx ctx, const void *spec, int np, const void *ins, int nq, int n_r, int nt,
+                            const void *wsnk, int ngs, const void *ins_g, int ngi, int prec, void *out,
+                            void *stream);
+
 /* ---- Batched calls: one fused launch for many calls.
  * One call of lhc_insertion or lhc_spectator (LHC_MIXED): part 0 insertion (Eq. 10),
  * 1 meson spectator (Eq. 9), 2 baryon spectator. S is S3, S1 or GA; GB is the second

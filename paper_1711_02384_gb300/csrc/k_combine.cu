@@ -188,6 +188,34 @@ __global__ void comb_spec_baryon(const double2 *__restrict__ B, int np, int n_r,
   for (int b = 0; b < 4; ++b) o[b * 3] = out[b];
 }
 
+// CTA per (p, i), the source spins left open:
+//   Xs[g][p][i][(a1*4 + a2)*3 + c] = sum_{a1p,a2p,bp} Wsnk[g][a1p][a2p][bp] B[p][i][a1p,a1,a2p,a2,bp,c]
+// The noise's 3072 values and the ng Wsnk tensors are staged in shared memory; a task is
+// one (g, a1, a2, c).
+template <typename R>
+__global__ void comb_spec_baryon_open(const double2 *__restrict__ B, int np, int n_r, const double2 *__restrict__ Wsnk,
+                                      int ng, cplx<R> *__restrict__ Xs) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cplx<R> *sW = reinterpret_cast<cplx<R> *>(sm_raw), *sB = sW + ng * 64;
+  const int pi = blockIdx.x, p = pi / n_r, i = pi % n_r;
+  stage(sW, Wsnk, ng * 64);
+  stage(sB, B + (size_t)pi * 3072, 3072);
+  __syncthreads();
+  for (int task = threadIdx.x; task < ng * 48; task += blockDim.x) {
+    const int c = task % 3, a2 = (task / 3) % 4, a1 = (task / 12) % 4, g = task / 48;
+    const cplx<R> *W = sW + g * 64;
+    cplx<R> h{0, 0};
+#pragma unroll
+    for (int a1p = 0; a1p < 4; ++a1p)
+#pragma unroll
+      for (int a2p = 0; a2p < 4; ++a2p)
+#pragma unroll
+        for (int bp = 0; bp < 4; ++bp)
+          cfma(h, W[(a1p * 4 + a2p) * 4 + bp], sB[((((a1p * 4 + a1) * 4 + a2p) * 4 + a2) * 4 + bp) * 3 + c]);
+    Xs[(((size_t)g * np + p) * n_r + i) * 48 + task % 48] = h;
+  }
+}
+
 // Sum over noises of the per-noise terms: in double for R = double; for R = float an
 // unevaluated pair hi + lo per component, each term added with Knuth's TwoSum (the pair
 // holds the sum exactly up to the rounding of lo), rounded once to double at the end.
@@ -292,13 +320,15 @@ __global__ void __launch_bounds__(256) comb_gemm(const cplx<R> *__restrict__ Xs,
     }
 }
 
-// Open-source-spin combine (meson):
-//   O[t][gs][gi][p][q][al][be] = (1/N) sum_{i,a} Xs[gs][p][i,al,a] Xi[t][gi][q][i,be,a]
-// with Xs the spectator part with Gamma_snk applied (comb_spec_meson) and Xi the
-// insertion part with Gamma_ins applied (comb_ins_baryon, which applies Gamma_ins only).
-// Rows are (p, al), columns (q, be); the tiling is comb_gemm's, with KN noises of three
-// colours staged per pass and four noises (12 terms) per partial sum.
-template <typename R>
+// Open-source-spin combine:
+//   O[t][gs][gi][p][q][e][be] = (1/N) sum_{i,a} Xs[gs][p][i,e,a] Xi[t][gi][q][i,be,a]
+// with Xi the insertion part with Gamma_ins applied (comb_ins_baryon, which applies
+// Gamma_ins only) and Xs the spectator part with the sink structure applied: for a
+// meson e = al (RS = 4 open row spins, comb_spec_meson), for a baryon e = (a1, a2)
+// (RS = 16, comb_spec_baryon_open).  Rows are (p, e), columns (q, be); the tiling is
+// comb_gemm's, with KN noises of three colours staged per pass and four noises (12
+// terms) per partial sum.
+template <typename R, int RS>
 __global__ void __launch_bounds__(256) comb_gemm_open(const cplx<R> *__restrict__ Xs, const cplx<R> *__restrict__ Xi,
                                                       int np, int nq, int n_r, int ngs, int ngi, double inv_n,
                                                       float inv_n_pow2, double2 *__restrict__ out) {
@@ -308,15 +338,15 @@ __global__ void __launch_bounds__(256) comb_gemm_open(const cplx<R> *__restrict_
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int c0 = blockIdx.x * TQ, r0 = blockIdx.y * TP;
   const int z = blockIdx.z, gi = z % ngi, gs = (z / ngi) % ngs, t = z / (ngi * ngs);
-  const cplx<R> *A = Xs + (size_t)gs * np * 12 * n_r;                 // [p][i][al][a]
+  const cplx<R> *A = Xs + (size_t)gs * np * 3 * RS * n_r;             // [p][i][e][a]
   const cplx<R> *B = Xi + ((size_t)t * ngi + gi) * nq * 12 * n_r;      // [q][i][be][a]
   NoiseSum<R> acc[2][3];
   for (int i0 = 0; i0 < n_r; i0 += KN) {
     const int kn = min(KN, n_r - i0);
     for (int e = threadIdx.x; e < TP * 3 * KN; e += 256) {
       const int r = e / (3 * KN), k = e % (3 * KN), ii = k / 3, a = k % 3, R_ = r0 + r;
-      As[r * KW + k] = (R_ < 4 * np && ii < kn) ? A[((size_t)(R_ >> 2) * n_r + i0 + ii) * 12 + (R_ & 3) * 3 + a]
-                                                : cplx<R>{0, 0};
+      As[r * KW + k] = (R_ < RS * np && ii < kn) ? A[((size_t)(R_ / RS) * n_r + i0 + ii) * 3 * RS + (R_ % RS) * 3 + a]
+                                                 : cplx<R>{0, 0};
     }
     for (int e = threadIdx.x; e < TQ * 3 * KN; e += 256) {
       const int r = e / (3 * KN), k = e % (3 * KN), ii = k / 3, a = k % 3, C_ = c0 + r;
@@ -354,8 +384,8 @@ __global__ void __launch_bounds__(256) comb_gemm_open(const cplx<R> *__restrict_
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
       const int R_ = r0 + ty + 16 * a, C_ = c0 + tx + 16 * b;
-      if (R_ < 4 * np && C_ < 4 * nq)
-        out[(((size_t)z * np + (R_ >> 2)) * nq + (C_ >> 2)) * 16 + (R_ & 3) * 4 + (C_ & 3)] =
+      if (R_ < RS * np && C_ < 4 * nq)
+        out[(((size_t)z * np + R_ / RS) * nq + (C_ >> 2)) * 4 * RS + (R_ % RS) * 4 + (C_ & 3)] =
             acc[a][b].get(inv_n, inv_n_pow2);
     }
 }
@@ -385,22 +415,51 @@ int noise_chunk(int ng, int n_r, int *nch, size_t *smem) {
   return LHC_OK;
 }
 
+// Shared memory of comb_spec_baryon_open: one noise's 3072 values and ng Wsnk tensors.
 template <typename R>
-int launch_combine_open(const double2 *spec, int np, const double2 *ins, int nq, int n_r, int nt, const double2 *snk,
-                        int ngs, const double2 *ins_g, int ngi, void *scratch, double2 *out, cudaStream_t st) {
+int spec_open_smem(int ng, size_t *smem) {
+  *smem = ((size_t)ng * 64 + 3072) * sizeof(cplx<R>);
+  if (*smem > 200 * 1024) {
+    set_error("combine_open: %d sink structures do not fit shared memory", ng);
+    return LHC_EINVAL;
+  }
+  if (*smem > 48 * 1024) {
+    static bool attr = false;
+    if (!attr) {
+      LHC_CHECK_CUDA(
+          cudaFuncSetAttribute(comb_spec_baryon_open<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      attr = true;
+    }
+  }
+  return LHC_OK;
+}
+
+template <typename R>
+int launch_combine_open(int kind, const double2 *spec, int np, const double2 *ins, int nq, int n_r, int nt,
+                        const double2 *snk, int ngs, const double2 *ins_g, int ngi, void *scratch, double2 *out,
+                        cudaStream_t st) {
+  const int RS = kind == LHC_MESON ? 4 : 16;
   cplx<R> *Xs = static_cast<cplx<R> *>(scratch);
-  cplx<R> *Xi = Xs + (size_t)ngs * np * 12 * n_r;
+  cplx<R> *Xi = Xs + (size_t)ngs * np * 3 * RS * n_r;
   int nch;
   size_t smem;
-  LHC_TRY(noise_chunk<R>(ngs, n_r, &nch, &smem));
-  comb_spec_meson<R><<<np, 256, smem, st>>>(spec, np, n_r, nch, snk, ngs, Xs);
+  if (kind == LHC_MESON) {
+    LHC_TRY(noise_chunk<R>(ngs, n_r, &nch, &smem));
+    comb_spec_meson<R><<<np, 256, smem, st>>>(spec, np, n_r, nch, snk, ngs, Xs);
+  } else {
+    LHC_TRY(spec_open_smem<R>(ngs, &smem));
+    comb_spec_baryon_open<R><<<np * n_r, 256, smem, st>>>(spec, np, n_r, snk, ngs, Xs);
+  }
   note_launch();
   LHC_TRY(noise_chunk<R>(ngi, n_r, &nch, &smem));
   comb_ins_baryon<R><<<nt * nq, 256, smem, st>>>(ins, nq, n_r, nch, ins_g, ngi, Xi);   // Gamma_ins only
   note_launch();
-  const dim3 grid((4 * nq + TQ - 1) / TQ, (4 * np + TP - 1) / TP, nt * ngs * ngi);
+  const dim3 grid((4 * nq + TQ - 1) / TQ, (RS * np + TP - 1) / TP, nt * ngs * ngi);
   const float inv_pow2 = (n_r & (n_r - 1)) == 0 ? 1.0f / (float)n_r : 0.0f;   // exact for N = 2^m
-  comb_gemm_open<R><<<grid, 256, 0, st>>>(Xs, Xi, np, nq, n_r, ngs, ngi, 1.0 / n_r, inv_pow2, out);
+  if (kind == LHC_MESON)
+    comb_gemm_open<R, 4><<<grid, 256, 0, st>>>(Xs, Xi, np, nq, n_r, ngs, ngi, 1.0 / n_r, inv_pow2, out);
+  else
+    comb_gemm_open<R, 16><<<grid, 256, 0, st>>>(Xs, Xi, np, nq, n_r, ngs, ngi, 1.0 / n_r, inv_pow2, out);
   note_launch();
   return LHC_OK;
 }
@@ -479,21 +538,26 @@ int run_combine_scratch(int kind, const double2 *spec, int np, const double2 *in
   return LHC_OK;
 }
 
-int run_combine_open(lhc_ctx ctx, const double2 *spec, int np, const double2 *ins, int nq, int n_r, int nt,
+int run_combine_open(lhc_ctx ctx, int kind, const double2 *spec, int np, const double2 *ins, int nq, int n_r, int nt,
                      const double2 *snk, int ngs, const double2 *ins_g, int ngi, int prec, double2 *out,
                      cudaStream_t st) {
   if ((size_t)nt * ngs * ngi > 65535) {
     set_error("combine_open: nt * ngs * ngi = %lld exceeds 65535", (long long)nt * ngs * ngi);
     return LHC_EINVAL;
   }
+  const int RS = kind == LHC_MESON ? 4 : 16;
+  if ((size_t)RS * np > 65535u * TP) {
+    set_error("combine_open: %d sink momenta exceed the grid", np);
+    return LHC_EINVAL;
+  }
   const size_t es = prec == LHC_MIXED ? sizeof(cplx<float>) : sizeof(cplx<double>);
-  const size_t K = (size_t)12 * n_r;
-  LHC_TRY(ensure(ctx, ctx->ws, ((size_t)ngs * np * K + (size_t)nt * ngi * nq * K) * es));
-  ProfScope ps(ctx, st, LHC_KERNEL_COMBINE, 8.0 * nt * ngs * ngi * (double)np * nq * K * 4.0 / 3.0);
+  const size_t K = (size_t)3 * n_r;   // (noise, colour)
+  LHC_TRY(ensure(ctx, ctx->ws, ((size_t)ngs * np * RS * K + (size_t)nt * ngi * nq * 4 * K) * es));
+  ProfScope ps(ctx, st, LHC_KERNEL_COMBINE, 8.0 * nt * ngs * ngi * (double)RS * np * 4.0 * nq * K);
   if (prec == LHC_MIXED)
-    LHC_TRY(launch_combine_open<float>(spec, np, ins, nq, n_r, nt, snk, ngs, ins_g, ngi, ctx->ws.p, out, st));
+    LHC_TRY(launch_combine_open<float>(kind, spec, np, ins, nq, n_r, nt, snk, ngs, ins_g, ngi, ctx->ws.p, out, st));
   else
-    LHC_TRY(launch_combine_open<double>(spec, np, ins, nq, n_r, nt, snk, ngs, ins_g, ngi, ctx->ws.p, out, st));
+    LHC_TRY(launch_combine_open<double>(kind, spec, np, ins, nq, n_r, nt, snk, ngs, ins_g, ngi, ctx->ws.p, out, st));
   LHC_CHECK_CUDA(cudaGetLastError());
   return LHC_OK;
 }

@@ -709,23 +709,39 @@ int lhc_combine(lhc_ctx ctx, int kind, const void *spec, int np, const void *ins
   return s != LHC_OK ? s : e2;
 }
 
-int lhc_combine_open(lhc_ctx ctx, const void *spec, int np, const void *ins, int nq, int n_r, int nt,
-                     const void *snk, int ngs, const void *ins_g, int ngi, int prec, void *out, void *stream) {
+namespace {
+int combine_open(lhc_ctx ctx, int kind, const char *name, const void *spec, int np, const void *ins, int nq,
+                 int n_r, int nt, const void *snk, int ngs, const void *ins_g, int ngi, int prec, void *out,
+                 void *stream) {
   if (!ctx) return fail(LHC_EINVAL, "ctx is NULL");
   if (!spec || !ins || !snk || !ins_g || !out) return fail(LHC_EINVAL, "NULL buffer argument");
   if (np < 1 || nq < 1 || n_r < 1 || nt < 1 || ngs < 1 || ngi < 1) return fail(LHC_EINVAL, "sizes must be positive");
   if (prec != LHC_FP64 && prec != LHC_MIXED) return fail(LHC_EINVAL, "unknown precision %d", prec);
   const void *ptr[5] = {spec, ins, snk, ins_g, out};
   for (const void *p : ptr)
-    if (!is_device_ptr(p)) return fail(LHC_EINVAL, "lhc_combine_open takes device buffers only");
+    if (!is_device_ptr(p)) return fail(LHC_EINVAL, "%s takes device buffers only", name);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> g(ctx->mu);
   LHC_TRY(begin_call(ctx, st));
-  int s = run_combine_open(ctx, static_cast<const double2 *>(spec), np, static_cast<const double2 *>(ins), nq, n_r,
-                           nt, static_cast<const double2 *>(snk), ngs, static_cast<const double2 *>(ins_g), ngi, prec,
-                           static_cast<double2 *>(out), st);
+  int s = run_combine_open(ctx, kind, static_cast<const double2 *>(spec), np, static_cast<const double2 *>(ins), nq,
+                           n_r, nt, static_cast<const double2 *>(snk), ngs, static_cast<const double2 *>(ins_g), ngi,
+                           prec, static_cast<double2 *>(out), st);
   int e = end_call(ctx, st);
   return s != LHC_OK ? s : e;
+}
+}  // namespace
+
+int lhc_combine_open(lhc_ctx ctx, const void *spec, int np, const void *ins, int nq, int n_r, int nt,
+                     const void *snk, int ngs, const void *ins_g, int ngi, int prec, void *out, void *stream) {
+  return combine_open(ctx, LHC_MESON, "lhc_combine_open", spec, np, ins, nq, n_r, nt, snk, ngs, ins_g, ngi, prec, out,
+                      stream);
+}
+
+int lhc_combine_open_baryon(lhc_ctx ctx, const void *spec, int np, const void *ins, int nq, int n_r, int nt,
+                            const void *wsnk, int ngs, const void *ins_g, int ngi, int prec, void *out,
+                            void *stream) {
+  return combine_open(ctx, LHC_BARYON, "lhc_combine_open_baryon", spec, np, ins, nq, n_r, nt, wsnk, ngs, ins_g, ngi,
+                      prec, out, stream);
 }
 
 int lhc_set_projection(lhc_ctx ctx, int mode) {

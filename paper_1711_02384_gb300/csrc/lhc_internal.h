@@ -189,8 +189,8 @@ int run_combine(lhc_ctx ctx, int kind, const double2 *spec, int np, const double
                 int n_r, int nt, const double2 *snk, const double2 *ins_g, const double2 *src, int ng,
                 int prec, double2 *out, cudaStream_t st);
 
-// open-source-spin meson combine (k_combine.cu)
-int run_combine_open(lhc_ctx ctx, const double2 *spec, int np, const double2 *ins, int nq, int n_r, int nt,
+// open-source-spin combine, meson or baryon (k_combine.cu)
+int run_combine_open(lhc_ctx ctx, int kind, const double2 *spec, int np, const double2 *ins, int nq, int n_r, int nt,
                      const double2 *snk, int ngs, const double2 *ins_g, int ngi, int prec, double2 *out,
                      cudaStream_t st);
 

@@ -107,12 +107,13 @@ def lib():
         L.lhc_wilson_solve.argtypes = [vp, lp, ctypes.c_double, vp, vp, vp, ci, ctypes.c_double, ci, ip,
                                        ctypes.POINTER(ctypes.c_double), vp]
         L.lhc_combine_open.argtypes = [vp, vp, ci, vp, ci, ci, ci, vp, ci, vp, ci, ci, vp, vp]
+        L.lhc_combine_open_baryon.argtypes = [vp, vp, ci, vp, ci, ci, ci, vp, ci, vp, ci, ci, vp, vp]
         L.lhc_set_projection.argtypes = [vp, ci]
         L.lhc_batch.argtypes = [vp, ctypes.POINTER(Call), ci, vp]
         L.lhc_set_tuning.argtypes = [vp, ci, ctypes.c_char_p]
         L.lhc_tuning_table.argtypes = [ip, ci, ip]
         L.lhc_tuning_load.argtypes = [ctypes.c_char_p, ip]
-        for name in ("lhc_batch", "lhc_combine_open", "lhc_set_projection", "lhc_wilson_apply", "lhc_wilson_solve", "lhc_set_tuning", "lhc_tuning_table", "lhc_tuning_load",
+        for name in ("lhc_batch", "lhc_combine_open", "lhc_combine_open_baryon", "lhc_set_projection", "lhc_wilson_apply", "lhc_wilson_solve", "lhc_set_tuning", "lhc_tuning_table", "lhc_tuning_load",
                      "lhc_create", "lhc_destroy", "lhc_set_gamma5", "lhc_momenta", "lhc_insertion",
                      "lhc_spectator", "lhc_combine", "lhc_profile", "lhc_profile_read", "lhc_sync", "lhc_release_workspace",
                      "lhc_selftest_timeout", "lhc_serve_start", "lhc_serve_stop", "lhc_prop_register",
@@ -395,6 +396,22 @@ class Context:
             out = torch.empty(shape, dtype=torch.complex128, device=spec.device)
         _check(lib().lhc_combine_open(self._h, _ptr(spec), np_, _ptr(ins), nq, n_r, nt, _ptr(snk), ngs, _ptr(ins_g),
                                       ngi, PRECISIONS[prec], _ptr(out), _stream(spec, stream)))
+        return out[0] if single else out
+
+    def combine_open_baryon(self, spec, ins, wsnk, ins_g, prec="fp64", out=None, stream=None):
+        """Open-source-spin baryon combine: spec [np][n_r][3072], ins [nt][nq][n_r][192] (or
+        one slice [nq][n_r][192]), wsnk [ngs][4][4][4], ins_g [ngi][4][4]; returns complex128
+        [nt][ngs][ngi][np][nq][4 a1][4 a2][4 b] (no nt axis for one slice).  Contract with
+        Wsrc[a1][a2][b] for any source structure."""
+        single = ins.dim() == 3
+        nt = 1 if single else ins.shape[0]
+        np_, n_r, nq = spec.shape[0], spec.shape[1], ins.shape[-3]
+        ngs, ngi = wsnk.shape[0], ins_g.shape[0]
+        shape = (nt, ngs, ngi, np_, nq, 4, 4, 4)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.complex128, device=spec.device)
+        _check(lib().lhc_combine_open_baryon(self._h, _ptr(spec), np_, _ptr(ins), nq, n_r, nt, _ptr(wsnk), ngs,
+                                             _ptr(ins_g), ngi, PRECISIONS[prec], _ptr(out), _stream(spec, stream)))
         return out[0] if single else out
 
     # ------------------------------------------------------------------ job server

@@ -65,3 +65,49 @@ def test_dirac_basis_sweep(ctx, parts):
     for s, i, c in rng.integers(0, 16, size=(12, 3)):
         ref = OC.combine_meson(spec, ins[0], g16[s:s + 1], g16[i:i + 1], g16[c:c + 1])[0]
         assert np.linalg.norm(C[s, i, c] - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+@pytest.fixture(scope="module")
+def baryon_parts():
+    from oracle.momenta import momenta
+    c = CS.Case(4, 8, 5, momenta(2), seed=2110, r=(2, 0, 1, 0))
+    return c.ref_spectator_baryon(5), c.ref_insertion(2, 5)     # [np][n_r][3072], [nt][nq][n_r][192]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-6)])
+def test_open_baryon_combine_contracts_to_combine(ctx, baryon_parts, prec, tol):
+    """Contracting the open (a1, a2, b) source spins with any W_src gives the baryon combine
+    of Eq. 8 for that structure: against the oracle and the library's closed combine."""
+    spec, ins = baryon_parts
+    ws = CS.random_gammas(2111, 2, (4, 4, 4))
+    gi = CS.random_gammas(2112, 3, (4, 4))
+    wc = CS.random_gammas(2113, 2, (4, 4, 4))
+    op = ctx.combine_open_baryon(dev(spec), dev(ins), dev(ws), dev(gi), prec=prec).cpu().numpy()
+    ctx.sync()
+    assert op.shape == (4, 2, 3, spec.shape[0], ins.shape[1], 4, 4, 4)
+    for a in range(2):
+        for b in range(3):
+            for w in wc:
+                got = np.einsum("tpqxyz,xyz->tpq", op[:, a, b], w)
+                ref = np.stack([OC.combine_baryon(spec, ins[t], ws[a:a + 1], gi[b:b + 1], w[None])[0]
+                                for t in range(ins.shape[0])])
+                assert CS.block_err(got, ref, 1) < tol
+                lib = ctx.combine(dev(spec), dev(ins), dev(ws[a:a + 1]), dev(gi[b:b + 1]), dev(w[None]),
+                                  prec=prec).cpu().numpy()[:, 0]
+                assert CS.block_err(got, lib, 1) < (1e-12 if prec == "fp64" else 2 * tol)
+
+
+def test_open_baryon_single_slice_and_ragged(ctx, baryon_parts):
+    """One insertion slice (no nt axis), one noise, and momentum lists that leave ragged
+    row and column tiles (16 np and 4 nq not multiples of the 32 x 48 tile)."""
+    spec, ins = baryon_parts
+    spec1, ins1 = spec[:3, :1], ins[1, :5, :1]
+    ws = CS.random_gammas(2114, 1, (4, 4, 4))
+    gi = CS.random_gammas(2115, 1, (4, 4))
+    op = ctx.combine_open_baryon(dev(spec1), dev(ins1), dev(ws), dev(gi), prec="fp64").cpu().numpy()
+    ctx.sync()
+    assert op.shape == (1, 1, 3, 5, 4, 4, 4)
+    # W[a1'][a2'][b'] = xyz, Gamma_ins = uv, B[p][a1',a1,a2',a2,b',c] = pxjyhzc, I[q][u,v,b,c]
+    ref = np.einsum("xyz,uv,pxjyhzc,quvbc->pqjhb", ws[0], gi[0],
+                    spec1[:, 0].reshape(3, 4, 4, 4, 4, 4, 3), ins1[:, 0].reshape(5, 4, 4, 4, 3))
+    assert np.abs(op[0, 0] - ref).max() <= 1e-12 * np.abs(ref).max()
