@@ -314,43 +314,60 @@ def main():
             kernels[name] = {"ms_per_step": kms_i, "launches_per_step": kn_i}
 
     # End to end, inputs on the host: every step uploads the propagator slices 0..12 once
-    # (a plain device copy: the six calls of the step share them), passes the solutions
-    # and noise vectors to the library as pinned host buffers (it stages them, overlapping
-    # the copies with the kernels of earlier calls), keeps the open-spin outputs on the
-    # device for the combine, and reads back to the host both the open-spin outputs (the
-    # method's data product) and the correlators (the combine writes them to host memory).
+    # (a plain device copy on a copy stream: the six calls of the step share them), passes
+    # the solutions and noise vectors to the library as pinned host buffers (it stages
+    # them in call order, overlapping the copies with the kernels of earlier calls), keeps
+    # the open-spin outputs on the device for the combine, and reads back to the host both
+    # the open-spin outputs (the method's data product) and the correlators (the combine
+    # writes them to host memory).  The device copy of the propagator and the open-spin
+    # outputs alternate between two buffers by step parity, so a step waits only for the
+    # step two back and consecutive steps overlap: the host link stays busy across step
+    # boundaries.
     e2e = None
     if not args.no_e2e and rank == 0:
         nS = max(TFS) + 1
         S_p = torch.from_numpy(np.ascontiguousarray(S_h[:nS])).pin_memory()
-        S_d = torch.empty(S_p.shape, dtype=S_p.dtype, device=dev)
+        S_d = [torch.empty(S_p.shape, dtype=S_p.dtype, device=dev) for _ in range(2)]
         psis_p = [torch.from_numpy(p).pin_memory() for p in psis_h]
         etas_p = [torch.from_numpy(e).pin_memory() for e in etas_h]
         G_p = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (g16, g4, gsrc)]
-        G_d = [torch.empty(g.shape, dtype=g.dtype, device=dev) for g in G_p]
+        G_d = [[torch.empty(g.shape, dtype=g.dtype, device=dev) for g in G_p] for _ in range(2)]
+        oi = [outs_ins, [torch.empty_like(o) for o in outs_ins]]
+        osp = [outs_spec, [torch.empty_like(o) for o in outs_spec]]
         hi = [torch.empty((tf + 1, nq, N_R, 192), dtype=torch.complex128).pin_memory() for tf in TFS]
         hs = [torch.empty((nq, N_R, 192), dtype=torch.complex128).pin_memory() for _ in TFS]
         hc = [torch.empty((tf + 1, 16, nq, nq), dtype=torch.complex128).pin_memory() for tf in TFS]
-        side = torch.cuda.Stream(dev)
+        side, up = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        st_done = [torch.cuda.Event(), torch.cuda.Event()]     # kernels of the step done with buffers b
+        side_done = [torch.cuda.Event(), torch.cuda.Event()]   # read-backs of the step done with buffers b
+        nstep = [0]
 
         def step_host():
-            st.wait_stream(side)              # last step's read-backs are done with the outputs
-            S_d.copy_(S_p, non_blocking=True)
-            for gd, gp in zip(G_d, G_p):
-                gd.copy_(gp, non_blocking=True)
+            b = nstep[0] & 1
+            nstep[0] += 1
+            up.wait_event(st_done[b])           # the step two back has finished with S_d[b], G_d[b]
+            with torch.cuda.stream(up):
+                S_d[b].copy_(S_p, non_blocking=True)
+                for gd, gp in zip(G_d[b], G_p):
+                    gd.copy_(gp, non_blocking=True)
+            st.wait_stream(up)
+            st.wait_event(side_done[b])         # and its read-backs with the open-spin outputs b
             for j, tf in enumerate(TFS):
-                ctx.insertion(S_d, psis_p[j], 0, tf, r, k, prec=args.prec, out=outs_ins[j], stream=st.cuda_stream)
-                ctx.spectator(S_d, etas_p[j], tf, r, k, prec=args.prec, out=outs_spec[j], stream=st.cuda_stream)
-                ctx.combine(outs_spec[j], outs_ins[j], G_d[0], G_d[1], G_d[2], prec=args.prec, out=hc[j],
+                ctx.insertion(S_d[b], psis_p[j], 0, tf, r, k, prec=args.prec, out=oi[b][j], stream=st.cuda_stream)
+                ctx.spectator(S_d[b], etas_p[j], tf, r, k, prec=args.prec, out=osp[b][j], stream=st.cuda_stream)
+                ctx.combine(osp[b][j], oi[b][j], G_d[b][0], G_d[b][1], G_d[b][2], prec=args.prec, out=hc[j],
                             stream=st.cuda_stream)
                 side.wait_stream(st)          # the open-spin outputs go back while the next set runs
                 with torch.cuda.stream(side):
-                    hi[j].copy_(outs_ins[j], non_blocking=True)
-                    hs[j].copy_(outs_spec[j], non_blocking=True)
+                    hi[j].copy_(oi[b][j], non_blocking=True)
+                    hs[j].copy_(osp[b][j], non_blocking=True)
+            st_done[b].record(st)
+            side_done[b].record(side)
 
-        step_host()
+        for _ in range(2):                    # both buffer parities; staging slots sized
+            step_host()
         torch.cuda.synchronize(dev)
-        ne = max(1, min(args.steps, 5))
+        ne = max(1, min(args.steps, 10))
         t0 = time.perf_counter()
         for _ in range(ne):
             step_host()
@@ -363,7 +380,8 @@ def main():
         d2h += sum((tf + 1) * 16 * nq * nq * 16 for tf in TFS)                       # correlators
         e2e = {"value": upstep / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": dt * 1e3,
-               "pattern": "propagator slices uploaded once per step; solutions and noise as pinned host "
+               "pattern": "propagator slices uploaded once per step (double-buffered, steps overlap); "
+                          "solutions and noise as pinned host "
                           "buffers through the library; open-spin outputs and correlators read back"}
 
     cpu = None

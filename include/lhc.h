@@ -28,10 +28,11 @@
  * pageable), and must be 16-byte aligned (the kernels move complex64 data in 16-byte
  * copies); misaligned buffers return LHC_EINVAL.  Every call is asynchronous on `stream`
  * (a cudaStream_t; NULL = legacy default stream), with device or host buffers alike.
- * Host buffers are staged through two device slots that alternate between calls: the
- * input copies run on a copy stream of the context and overlap the kernels of the
- * previous call, and the output copy runs on a second copy stream that `stream` waits
- * for.  So once `stream` (or the device) is synchronized after a call, its host output
+ * Host buffers are staged through eight device slots that successive calls take in
+ * turn: the input copies run in call order on a copy stream of the context and overlap
+ * the kernels of earlier calls (a call with several slices copies them in up to four
+ * groups, each followed by its kernels), and the output copy runs on a second copy
+ * stream that `stream` waits for.  So once `stream` (or the device) is synchronized after a call, its host output
  * is written and its host inputs have been read; until then the caller must not change
  * the inputs or read the output.  A later call may take an earlier call's host output
  * as its input: the library tracks host ranges that output copies in flight will write

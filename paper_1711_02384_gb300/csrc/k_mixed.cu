@@ -1321,13 +1321,15 @@ static bool call_shape(lhc_ctx ctx, const SliceJob &j0, int nt, const MomentumRe
   return tuned;
 }
 
+// shape_nt > 0: the launch shape (and its tuning key) is that of a call of shape_nt slices,
+// of which these nt are a group; every slice is then computed exactly as in that call.
 int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int nq, const int r[4], int sign,
-                   cudaStream_t st) {
+                   cudaStream_t st, int shape_nt) {
   const SliceJob &j0 = jobs[0];
   const MomentumReps reps = momentum_reps(k, nq);
   int NH, nsplit;
   TuneKey key;
-  const bool tuned = call_shape(ctx, j0, nt, reps, &NH, &nsplit, &key);
+  const bool tuned = call_shape(ctx, j0, shape_nt > 0 ? shape_nt : nt, reps, &NH, &nsplit, &key);
   if (!tuned && ctx->tune_mode == LHC_TUNE_ON) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     LHC_CHECK_CUDA(cudaStreamIsCapturing(st, &cs));

@@ -197,16 +197,19 @@ static std::mutex g_sync_mu;
 
 // ---------------------------------------------------------------- host staging
 // A call with host buffers takes the next of kStageSlots staging slots.  Its input
-// copies run on the slot's H2D stream as soon as the slot is free (the call kStageSlots
+// copies run on the context's H2D stream once the slot is free (the call kStageSlots
 // back has finished with it) and any output copy in flight into the same host memory has
 // landed; the caller's stream waits for them, runs the kernels, and the D2H stream
 // copies the output back, which the caller's stream waits for in turn.  So the copies of
 // one call overlap the kernels of the ones before, and a stream or device synchronize
-// still covers all.
+// still covers all.  One H2D stream, not one per slot: the calls' copies then land in
+// call order at the full link rate, and each call's kernels start as soon as its own
+// inputs are in, instead of all calls' inputs arriving together at the end of a shared
+// transfer.
 static int stage_streams(lhc_ctx ctx) {
   if (ctx->d2h) return LHC_OK;
+  LHC_CHECK_CUDA(cudaStreamCreateWithFlags(&ctx->h2d, cudaStreamNonBlocking));
   for (int s = 0; s < lhc_ctx_s::kStageSlots; ++s) {
-    LHC_CHECK_CUDA(cudaStreamCreateWithFlags(&ctx->h2d[s], cudaStreamNonBlocking));
     LHC_CHECK_CUDA(cudaEventCreateWithFlags(&ctx->slot_free[s], cudaEventDisableTiming));
     LHC_CHECK_CUDA(cudaEventCreateWithFlags(&ctx->in_ready[s], cudaEventDisableTiming));
   }
@@ -215,20 +218,46 @@ static int stage_streams(lhc_ctx ctx) {
   return LHC_OK;
 }
 
+// Grows staging slot s in stream order on the H2D stream, which already waits for the
+// slot's previous call: the old buffer goes back with cudaFreeAsync and the new one comes
+// from cudaMallocAsync, so a growing slot never synchronizes the device (cudaFree would).
+static int stage_grow(lhc_ctx ctx, int s, size_t bytes) {
+  DevBuf &b = ctx->stage[s];
+  if (b.bytes >= bytes) return LHC_OK;
+  const size_t want = bytes + bytes / 4;
+  while (ctx->budget && ctx->used - b.bytes + want > ctx->budget && !ctx->phase_lru.empty()) evict_one_phase(ctx);
+  if (ctx->budget && ctx->used - b.bytes + want > ctx->budget)
+    return fail(LHC_EBUDGET, "staging slot of %zu bytes exceeds the HBM budget (%zu of %zu in use)", want,
+                ctx->used - b.bytes, ctx->budget);
+  if (b.p) {
+    LHC_CHECK_CUDA(cudaFreeAsync(b.p, ctx->h2d));
+    ctx->used -= b.bytes;
+    b = DevBuf{};
+  }
+  cudaError_t e = cudaMallocAsync(&b.p, want, ctx->h2d);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b = DevBuf{};
+    return fail(LHC_ENOMEM, "cudaMallocAsync(%zu): %s", want, cudaGetErrorString(e));
+  }
+  b.bytes = want;
+  ctx->used += want;
+  return LHC_OK;
+}
+
 // Takes a staging slot of at least `bytes`; *base is its device address.
 static int stage_begin(lhc_ctx ctx, size_t bytes, int *slot, char **base) {
   LHC_TRY(stage_streams(ctx));
   const int s = ctx->next_slot;
   ctx->next_slot = (s + 1) % lhc_ctx_s::kStageSlots;
-  if (ctx->slot_used[s]) LHC_CHECK_CUDA(cudaStreamWaitEvent(ctx->h2d[s], ctx->slot_free[s], 0));
-  LHC_TRY(ensure(ctx, ctx->stage[s], bytes));   // growing synchronizes the device first
+  if (ctx->slot_used[s]) LHC_CHECK_CUDA(cudaStreamWaitEvent(ctx->h2d, ctx->slot_free[s], 0));
+  LHC_TRY(stage_grow(ctx, s, bytes));
   *slot = s;
   *base = static_cast<char *>(ctx->stage[s].p);
   return LHC_OK;
 }
 
-// Host -> slot copy on the slot's H2D stream, after any output copy still writing that
-// memory.
+// Host -> slot copy on the H2D stream, after any output copy still writing that memory.
 static int stage_in(lhc_ctx ctx, int slot, void *dst, const void *src, size_t bytes) {
   const char *a = static_cast<const char *>(src);
   for (auto it = ctx->pending_out.begin(); it != ctx->pending_out.end();) {
@@ -238,16 +267,17 @@ static int stage_in(lhc_ctx ctx, int slot, void *dst, const void *src, size_t by
       continue;
     }
     cudaGetLastError();   // cudaErrorNotReady is not an error here
-    if (a < it->p + it->n && it->p < a + bytes) LHC_CHECK_CUDA(cudaStreamWaitEvent(ctx->h2d[slot], it->ev, 0));
+    if (a < it->p + it->n && it->p < a + bytes) LHC_CHECK_CUDA(cudaStreamWaitEvent(ctx->h2d, it->ev, 0));
     ++it;
   }
-  LHC_CHECK_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->h2d[slot]));
+  (void)slot;
+  LHC_CHECK_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->h2d));
   return LHC_OK;
 }
 
 // The kernels on `st` may start once the inputs have landed.
 static int stage_ready(lhc_ctx ctx, int slot, cudaStream_t st) {
-  LHC_CHECK_CUDA(cudaEventRecord(ctx->in_ready[slot], ctx->h2d[slot]));
+  LHC_CHECK_CUDA(cudaEventRecord(ctx->in_ready[slot], ctx->h2d));
   LHC_CHECK_CUDA(cudaStreamWaitEvent(st, ctx->in_ready[slot], 0));
   return LHC_OK;
 }
@@ -287,11 +317,11 @@ static void stage_destroy(lhc_ctx ctx) {
   ctx->pending_out.clear();
   ctx->event_pool.clear();
   if (ctx->d2h) {
+    cudaStreamDestroy(ctx->h2d);
+    ctx->h2d = nullptr;
     for (int s = 0; s < lhc_ctx_s::kStageSlots; ++s) {
-      cudaStreamDestroy(ctx->h2d[s]);
       cudaEventDestroy(ctx->slot_free[s]);
       cudaEventDestroy(ctx->in_ready[s]);
-      ctx->h2d[s] = nullptr;
     }
     cudaStreamDestroy(ctx->d2h);
     cudaEventDestroy(ctx->comp_done);
@@ -535,46 +565,24 @@ int run_part(lhc_ctx ctx, const PartCall &c, cudaStream_t st) {
   const char *S = static_cast<const char *>(c.S), *SB = static_cast<const char *>(c.SB),
              *V = static_cast<const char *>(c.vec);
   size_t S_tstride = slice_elems * es;   // bytes between slices
-  // the call's slices t0 .. t0+nt-1 (mod T) as runs of consecutive t: one copy per run
-  std::vector<std::pair<int, int>> runs;   // (first j, length)
-  for (int j = 0; j < c.nt;) {
-    const int t = (c.t0 + j) % T, len = std::min(c.nt - j, T - t);
-    runs.emplace_back(j, len);
-    j += len;
-  }
-  if (hS || hSB) {
-    // the needed slices, as [nt][V3][144]
-    for (const auto &rn : runs) {
-      const size_t t = (size_t)((c.t0 + rn.first) % T), n = (size_t)rn.second * S_tstride;
-      if (hS) LHC_TRY(stage_in(ctx, slot, sp + rn.first * S_tstride, S + t * S_tstride, n));
-      if (hSB) LHC_TRY(stage_in(ctx, slot, sp + al(bS) + rn.first * S_tstride, SB + t * S_tstride, n));
+  // runs of consecutive t among the call's slices j0 .. j1-1 (t = t0 + j mod T): one copy
+  // per run
+  auto runs_of = [&](int j0, int j1) {
+    std::vector<std::pair<int, int>> runs;   // (first j, length)
+    for (int j = j0; j < j1;) {
+      const int t = (c.t0 + j) % T, len = std::min(j1 - j, T - t);
+      runs.emplace_back(j, len);
+      j += len;
     }
-  }
+    return runs;
+  };
   const char *Sd = hS ? sp : S;
   const char *SBd = hSB ? sp + al(bS) : SB;
   // vec layout on device: noise stride and slice base
-  const char *Vd = V;
-  size_t v_noise_stride = c.vec_has_time ? (size_t)T * vec_slice : vec_slice;   // elements
-  bool v_staged = false;
-  if (hV) {
-    char *dst = sp + al(bS) + al(bSB);
-    if (!c.vec_has_time) {   // eta: [n_r][V3][12], one block
-      LHC_TRY(stage_in(ctx, slot, dst, V, (size_t)c.n_r * vec_slice * es));
-    } else {   // psi: per noise, the runs of slices
-      for (int i = 0; i < c.n_r; ++i)
-        for (const auto &rn : runs) {
-          const size_t t = (size_t)((c.t0 + rn.first) % T);
-          LHC_TRY(stage_in(ctx, slot, dst + ((size_t)i * nvt + rn.first) * vec_slice * es,
-                           V + ((size_t)i * T + t) * vec_slice * es, (size_t)rn.second * vec_slice * es));
-        }
-    }
-    Vd = dst;
-    v_noise_stride = nvt * vec_slice;
-    v_staged = true;
-  }
+  const char *Vd = hV ? sp + al(bS) + al(bSB) : V;
+  const size_t v_noise_stride = hV ? nvt * vec_slice : (c.vec_has_time ? (size_t)T * vec_slice : vec_slice);
   double2 *Od = hO ? reinterpret_cast<double2 *>(sp + al(bS) + al(bSB) + al(bV))
                    : static_cast<double2 *>(c.out);
-  if (any_host) LHC_TRY(stage_ready(ctx, slot, st));
 
   const bool dft = use_fft(ctx, c.prec, V3, c.nq);   // all-momenta mode: the projection as a DFT
   const double2 *phase = nullptr;
@@ -592,17 +600,49 @@ int run_part(lhc_ctx ctx, const PartCall &c, cudaStream_t st) {
     job.nq = c.nq;
     job.S = Sd + (hS ? (size_t)j : (size_t)t) * S_tstride;
     job.SB = c.SB ? SBd + (hSB ? (size_t)j : (size_t)t) * S_tstride : nullptr;
-    size_t vt = c.vec_has_time ? (v_staged ? (size_t)j : (size_t)t) : 0;
+    size_t vt = c.vec_has_time ? (hV ? (size_t)j : (size_t)t) : 0;
     job.vec = Vd + vt * vec_slice * es;
     job.vec_stride = v_noise_stride;
     job.g5mask = g5mask_of(ctx);
     job.out = Od + (size_t)j * c.nq * c.n_r * cols;
-    if (c.prec == LHC_FP64 && !dft) LHC_TRY(run_slice_f64(ctx, job, phase, st));
   }
-  if (dft)
-    LHC_TRY(run_part_fft(ctx, jobs.data(), c.nt, c.k, c.nq, c.r, c.sign, st));
-  else if (c.prec == LHC_MIXED)
-    LHC_TRY(run_part_mixed(ctx, jobs.data(), c.nt, c.k, c.nq, c.r, c.sign, st));
+  // With host inputs the slices go in up to four groups: each group's copies are followed
+  // by its kernels, which start as soon as that group has landed, so a call's own
+  // transfer overlaps its kernels (one group per call would leave all of them after it).
+  const bool host_in = hS || hSB || hV;
+  const int ngroups = host_in ? std::min(c.nt, 4) : 1;
+  const int gsz = (c.nt + ngroups - 1) / ngroups;
+  for (int g0 = 0; g0 < c.nt; g0 += gsz) {
+    const int g1 = std::min(c.nt, g0 + gsz);
+    const auto runs = runs_of(g0, g1);
+    for (const auto &rn : runs) {   // the group's slices of S (and SB), as [nt][V3][144]
+      const size_t t = (size_t)((c.t0 + rn.first) % T), n = (size_t)rn.second * S_tstride;
+      if (hS) LHC_TRY(stage_in(ctx, slot, sp + rn.first * S_tstride, S + t * S_tstride, n));
+      if (hSB) LHC_TRY(stage_in(ctx, slot, sp + al(bS) + rn.first * S_tstride, SB + t * S_tstride, n));
+    }
+    if (hV) {
+      char *dst = sp + al(bS) + al(bSB);
+      if (!c.vec_has_time) {   // eta: [n_r][V3][12], one block (a spectator call has one slice)
+        if (g0 == 0) LHC_TRY(stage_in(ctx, slot, dst, V, (size_t)c.n_r * vec_slice * es));
+      } else {   // psi: per noise, the group's runs of slices
+        for (int i = 0; i < c.n_r; ++i)
+          for (const auto &rn : runs) {
+            const size_t t = (size_t)((c.t0 + rn.first) % T);
+            LHC_TRY(stage_in(ctx, slot, dst + ((size_t)i * nvt + rn.first) * vec_slice * es,
+                             V + ((size_t)i * T + t) * vec_slice * es, (size_t)rn.second * vec_slice * es));
+          }
+      }
+    }
+    if (any_host) LHC_TRY(stage_ready(ctx, slot, st));
+    if (dft) {
+      LHC_TRY(run_part_fft(ctx, jobs.data() + g0, g1 - g0, c.k, c.nq, c.r, c.sign, st));
+    } else if (c.prec == LHC_MIXED) {
+      // the call's launch shape for every group: each slice computed as in one launch
+      LHC_TRY(run_part_mixed(ctx, jobs.data() + g0, g1 - g0, c.k, c.nq, c.r, c.sign, st, c.nt));
+    } else {
+      for (int j = g0; j < g1; ++j) LHC_TRY(run_slice_f64(ctx, jobs[j], phase, st));
+    }
+  }
   if (any_host) LHC_TRY(stage_end(ctx, slot, st, hO ? c.out : nullptr, Od, out_bytes));
   return LHC_OK;
 }

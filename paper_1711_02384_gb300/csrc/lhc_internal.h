@@ -102,14 +102,15 @@ struct lhc_ctx_s {
   int g5[4] = {1, 1, -1, -1};
   std::mutex mu;
   lhc::DevBuf ws;                         // general workspace (grown on demand)
-  // Host-buffer staging: kStageSlots device slots used by successive calls in turn, each
-  // with its own H2D copy stream (a call's copies wait for nothing but its own slot and
-  // its own host dependencies), one D2H copy stream, and the host ranges that output
-  // copies still in flight will write (a later call reading such a range waits for
-  // that copy).
-  static constexpr int kStageSlots = 4;
+  // Host-buffer staging: kStageSlots device slots used by successive calls in turn, one
+  // H2D copy stream (copies land in call order; a slot's reuse waits for the call
+  // kStageSlots back, which with 8 slots is normally long done), one D2H copy stream,
+  // and the host ranges that output copies still in flight will write (a later call
+  // reading such a range waits for that copy).  A slot only holds device memory once a
+  // host-buffer call has used it.
+  static constexpr int kStageSlots = 8;
   lhc::DevBuf stage[kStageSlots];
-  cudaStream_t h2d[kStageSlots] = {}, d2h = nullptr;
+  cudaStream_t h2d = nullptr, d2h = nullptr;
   cudaEvent_t slot_free[kStageSlots] = {}, in_ready[kStageSlots] = {}, comp_done = nullptr;
   bool slot_used[kStageSlots] = {};
   int next_slot = 0;
@@ -158,7 +159,7 @@ int run_part_fft(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int nq
 
 // mixed path: all slices of one call in one set of launches (k_mixed.cu)
 int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int nq, const int r[4], int sign,
-                   cudaStream_t st);
+                   cudaStream_t st, int shape_nt = 0);
 
 size_t mixed_call_bytes(Part part, int dtype, int V3, int n_r, int nt, int nq);
 

@@ -1,7 +1,8 @@
-"""Calls with host (pinned) buffers run asynchronously through two alternating staging
-slots: a chain of insertion, spectator and combine calls whose combine reads the host
-outputs of the calls before it must give, bit for bit, the results of the same calls on
-device buffers; and one synchronize at the end must suffice."""
+"""Calls with host (pinned) buffers run asynchronously through the staging slots, with a
+call's slices copied and computed in groups: a chain of insertion, spectator and combine
+calls whose combine reads the host outputs of the calls before it must give, bit for
+bit, the results of the same calls on device buffers; and one synchronize at the end
+must suffice."""
 import numpy as np
 import pytest
 
