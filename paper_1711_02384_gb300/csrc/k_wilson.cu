@@ -19,6 +19,10 @@ namespace {
 
 struct Gammas {
   double2 g[4][16];   // gamma_mu[s][s'] row-major, mu = x, y, z, t
+  // The same matrices when every row has a single entry, a unit phase (any chiral or
+  // Dirac-Pauli basis): row s of gamma_mu is i^ph[mu][s] in column col[mu][s].
+  bool sparse;
+  int col[4][4], ph[4][4];
 };
 
 // One thread per (rhs, t, site, colour): the four spins of one colour at one site.
@@ -74,6 +78,72 @@ __global__ void wilson_kernel(const double2 *__restrict__ in, double2 *__restric
   for (int s = 0; s < 4; ++s) o[3 * s] = acc[s];
 }
 
+// i^ph * (x + i y) for ph in 0..3: exact (sign changes and a swap)
+__device__ __forceinline__ double2 unit_phase(int ph, double2 v) {
+  switch (ph & 3) {
+    case 0: return v;
+    case 1: return make_double2(-v.y, v.x);
+    case 2: return make_double2(-v.x, -v.y);
+    default: return make_double2(v.y, -v.x);
+  }
+}
+
+// The same stencil for gamma matrices with one unit-phase entry per row: each spin row
+// takes one difference, multiplied by a phase without FP64 multiplications.  GB300's
+// FP64 pipe runs at a small fraction of the FP32 rate, and the dense 4x4 complex products
+// above cost about 7 times the FP64 instructions.
+__global__ void wilson_sparse_kernel(const double2 *__restrict__ in, double2 *__restrict__ out, int L, int T,
+                                     int nrhs, double m, double sigma, Gammas gm) {
+  const size_t V3 = (size_t)L * L * L, n = (size_t)nrhs * T * V3 * 3;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int c = (int)(idx % 3);
+  size_t rest = idx / 3;
+  const size_t site = rest % V3;
+  rest /= V3;
+  const int t = (int)(rest % T);
+  const size_t rhs = rest / T;
+  const int x = (int)(site % L), y = (int)((site / L) % L), z = (int)(site / ((size_t)L * L));
+  const double2 *f = in + rhs * T * V3 * 12;
+  auto at = [&](int tt, int xx, int yy, int zz) {
+    return f + ((size_t)tt * V3 + ((size_t)zz * L + yy) * L + xx) * 12 + c;
+  };
+  double2 acc[4];
+  const double2 *h = at(t, x, y, z);
+#pragma unroll
+  for (int s = 0; s < 4; ++s) acc[s] = make_double2((m + 4.0) * h[3 * s].x, (m + 4.0) * h[3 * s].y);
+  // sigma = +1 (D) or -1 (D^dagger) flips every phase by i^2
+  const int flip = sigma < 0.0 ? 2 : 0;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const int d[4][4] = {{1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1}};
+    const double2 *fw = at((t + d[mu][3]) % T, (x + d[mu][0]) % L, (y + d[mu][1]) % L, (z + d[mu][2]) % L);
+    const double2 *bw =
+        at((t - d[mu][3] + T) % T, (x - d[mu][0] + L) % L, (y - d[mu][1] + L) % L, (z - d[mu][2] + L) % L);
+    double2 pf[4], pb[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      pf[s] = fw[3 * s];
+      pb[s] = bw[3 * s];
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      // -1/2 [ (psi_f + psi_b)_s - sigma i^ph (psi_f - psi_b)_col ]
+      const int cs = gm.col[mu][s];
+      double2 dd = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int s2 = 0; s2 < 4; ++s2)   // register select, no dynamic indexing
+        if (s2 == cs) dd = make_double2(pf[s2].x - pb[s2].x, pf[s2].y - pb[s2].y);
+      const double2 g = unit_phase(gm.ph[mu][s] + flip, dd);
+      acc[s].x -= 0.5 * ((pf[s].x + pb[s].x) - g.x);
+      acc[s].y -= 0.5 * ((pf[s].y + pb[s].y) - g.y);
+    }
+  }
+  double2 *o = out + rhs * T * V3 * 12 + ((size_t)t * V3 + site) * 12 + c;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) o[3 * s] = acc[s];
+}
+
 // partial[rhs][block] = sum over this block's share of Re(conj(a) b) for one rhs
 __global__ void dot_kernel(const double2 *__restrict__ a, const double2 *__restrict__ b, size_t n, double *partial) {
   const size_t rhs = blockIdx.y;
@@ -101,6 +171,21 @@ __global__ void axpby_kernel(const double *__restrict__ a, const double2 *__rest
   y[idx] = make_double2(a[rhs] * xv.x + b[rhs] * yv.x, a[rhs] * xv.y + b[rhs] * yv.y);
 }
 
+// The same with the scalars in the kernel's parameters (up to kParamRhs right-hand
+// sides): no copy, and no wait for one before the host reuses its scalars.
+constexpr int kParamRhs = 64;
+struct AxpbyCoef {
+  double a[kParamRhs], b[kParamRhs];
+};
+__global__ void axpby_param_kernel(const __grid_constant__ AxpbyCoef cf, const double2 *__restrict__ x,
+                                   double2 *__restrict__ y, size_t n, int nrhs) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * nrhs) return;
+  const size_t rhs = idx / n;
+  const double2 xv = x[idx], yv = y[idx];
+  y[idx] = make_double2(cf.a[rhs] * xv.x + cf.b[rhs] * yv.x, cf.a[rhs] * xv.y + cf.b[rhs] * yv.y);
+}
+
 constexpr int kDotBlocks = 64;
 
 struct Solver {
@@ -115,7 +200,10 @@ struct Solver {
 
   int apply(const double2 *in, double2 *out, double sigma) {
     const size_t threads = (size_t)nrhs * T * L * L * L * 3;
-    wilson_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(in, out, L, T, nrhs, m, sigma, gm);
+    if (gm.sparse)
+      wilson_sparse_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(in, out, L, T, nrhs, m, sigma, gm);
+    else
+      wilson_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(in, out, L, T, nrhs, m, sigma, gm);
     note_launch();
     LHC_CHECK_CUDA(cudaGetLastError());
     return LHC_OK;
@@ -132,6 +220,14 @@ struct Solver {
   }
   // y = a x + b y with per-rhs host scalars
   int axpby(const std::vector<double> &a, const double2 *x, const std::vector<double> &b, double2 *y) {
+    if (nrhs <= kParamRhs) {
+      AxpbyCoef cf{};
+      for (int r = 0; r < nrhs; ++r) cf.a[r] = a[r], cf.b[r] = b[r];
+      axpby_param_kernel<<<(unsigned)((n * nrhs + 255) / 256), 256, 0, st>>>(cf, x, y, n, nrhs);
+      note_launch();
+      LHC_CHECK_CUDA(cudaGetLastError());
+      return LHC_OK;
+    }
     std::vector<double> ab(2 * (size_t)nrhs);
     for (int r = 0; r < nrhs; ++r) ab[r] = a[r], ab[nrhs + r] = b[r];
     LHC_CHECK_CUDA(cudaMemcpyAsync(coef, ab.data(), sizeof(double) * ab.size(), cudaMemcpyHostToDevice, st));
@@ -153,6 +249,29 @@ int load_gammas(const double *g, Gammas *out) {
         return LHC_EINVAL;
       }
       out->g[mu][e] = make_double2(re, im);
+    }
+  // one unit-phase entry per row?  (exact comparisons: the basis matrices hold 0, +-1)
+  out->sparse = true;
+  for (int mu = 0; mu < 4 && out->sparse; ++mu)
+    for (int s = 0; s < 4 && out->sparse; ++s) {
+      int nz = 0;
+      for (int s2 = 0; s2 < 4; ++s2) {
+        const double2 v = out->g[mu][s * 4 + s2];
+        if (v.x == 0.0 && v.y == 0.0) continue;
+        ++nz;
+        out->col[mu][s] = s2;
+        if (v.x == 1.0 && v.y == 0.0)
+          out->ph[mu][s] = 0;
+        else if (v.x == 0.0 && v.y == 1.0)
+          out->ph[mu][s] = 1;
+        else if (v.x == -1.0 && v.y == 0.0)
+          out->ph[mu][s] = 2;
+        else if (v.x == 0.0 && v.y == -1.0)
+          out->ph[mu][s] = 3;
+        else
+          nz = 2;   // not a unit phase: dense
+      }
+      if (nz != 1) out->sparse = false;
     }
   return LHC_OK;
 }

@@ -26,10 +26,16 @@ def ctx():
 
 
 def _gammas(basis):
+    if basis == "rotated":
+        # U gamma U^dagger for a random unitary U: a valid Hermitian basis whose matrices
+        # are dense (the library's general stencil; the other two take its sparse one)
+        rng = np.random.default_rng(7)
+        q, _ = np.linalg.qr(rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4)))
+        return np.array([q @ g @ q.conj().T for g in OG.chiral()])
     return np.array(OG.chiral() if basis == "chiral" else OG.dirac_pauli())
 
 
-@pytest.mark.parametrize("basis", ["chiral", "dirac_pauli"])
+@pytest.mark.parametrize("basis", ["chiral", "dirac_pauli", "rotated"])
 @pytest.mark.parametrize("dagger", [False, True])
 def test_wilson_operator_matches_stencil(ctx, basis, dagger):
     L, T, m = 4, 6, 0.3
