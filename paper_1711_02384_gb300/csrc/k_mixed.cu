@@ -41,6 +41,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <memory>
+#include <type_traits>
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -158,14 +159,28 @@ struct FusedParams {
 // sum over 3 colours of (vector x matrix) products, so |re|, |im| <= 6 mV mM with mV, mM
 // the largest real or imaginary parts of the operands.  The scale 2^e puts that bound at
 // 2^14: far below the FP16 maximum (65504), and typical values, which lie well below the
-// bound, keep their lo parts (2^-11 of the value) out of the FP16 subnormal range.  The
-// drain multiplies the sums by 2^-e, which is exact.
+// bound, keep their lo parts (2^-11 of the value) out of the FP16 subnormal range.  A bound
+// already in [2^6, 2^14] (unit-scale data) is left unscaled (e = 0), which spares the
+// producers the multiplications; a lo part that falls subnormal there is off by at most
+// 2^-25, below 2^-31 of the bound.  The drain multiplies the sums by 2^-e, which is exact.
 __device__ __forceinline__ int split_scale_exp(unsigned mM_bits, unsigned mV_bits) {
   const float b = 6.f * __uint_as_float(mM_bits) * __uint_as_float(mV_bits);
   if (!(b > 0.f) || !(b < 3.0e38f)) return 0;
   int x;
   frexpf(b, &x);   // b = f 2^x, f in [0.5, 1): b <= 2^x
-  return max(-100, min(100, 14 - x));
+  const int e = 14 - x;
+  return e >= 0 && e <= 8 ? 0 : max(-100, min(100, e));
+}
+
+// (a0, a1) += (b0, b1) as one packed FP32 instruction: two IEEE round-to-nearest additions,
+// bitwise those of two scalar adds, in one issue slot (the drain runs on the same SM
+// sub-partitions as the producers, whose instruction issue bounds the kernel)
+__device__ __forceinline__ void add2(float &a0, float &a1, float b0, float b1) {
+  unsigned long long a, b;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(a) : "f"(a0), "f"(a1));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(b) : "f"(b0), "f"(b1));
+  asm("add.rn.f32x2 %0, %0, %1;" : "+l"(a) : "l"(b));
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a0), "=f"(a1) : "l"(a));
 }
 
 // fp16 hi/lo split of two floats, packed as half2 pairs
@@ -387,12 +402,19 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
           if (c > 0) tc::tmem_ld16(rsum + n0, r);
           tc::tmem_wait_ld();
 #pragma unroll
-          for (int e = 0; e < 16; ++e) r[e] = c > 0 ? r[e] + v[e] : v[e];
+          for (int e = 0; e < 16; e += 2) {
+            if (c > 0) {
+              add2(r[e], r[e + 1], v[e], v[e + 1]);
+            } else {
+              r[e] = v[e];
+              r[e + 1] = v[e + 1];
+            }
+          }
           tc::tmem_st16(rsum + n0, r);
         } else {
           tc::tmem_wait_ld();
 #pragma unroll
-          for (int e = 0; e < 16; ++e) acc[n0 - NT + e] += v[e];
+          for (int e = 0; e < 16; e += 2) add2(acc[n0 - NT + e], acc[n0 - NT + e + 1], v[e], v[e + 1]);
         }
       }
       tc::tmem_wait_st();
@@ -457,81 +479,113 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
       const int sv = s0 + sp + 8 * jx;
       mo[jx] = MODE == 2 ? x * 48 + sp + 8 * jx : ((x * 2 + (sv / 12 - bt0)) * 3) * 12 + sv % 12;
     }
-    for (int it = 0; it < nit; ++it) {
-      const int kstep = NPK * it + kofs;
-      if (kstep >= nk) break;
-      const int si = kstep % NIN, ui = kstep / NIN;
-      // The first warp of the group waits for each barrier; the four warps block on the
-      // group's named barrier and follow its verdict together, so a wait that gives up (a
-      // loader stopped, or the limit ran out) ends the loop of all four at once.
-      volatile int *vin = verdict + 2 + 4 * kofs, *vempty = vin + 2;
-      if (wq == 0 && lane == 0) vin[it & 1] = tc::mbar_wait(&inFull[si], ui & 1, err, 6) ? 1 : 0;
-      tc::named_bar_sync(2 + kofs, 128);
-      if (!vin[it & 1]) break;
-      const float2 *Ms = reinterpret_cast<const float2 *>(stM(si));
-      const float2 *Vs = reinterpret_cast<const float2 *>(stV(si)) + x * 12;
-      float2 acc[2][8];
-#pragma unroll
-      for (int jx = 0; jx < 2; ++jx)
-#pragma unroll
-        for (int iv = 0; iv < 8; ++iv) acc[jx][iv] = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        float2 sv[2];
-#pragma unroll
-        for (int jx = 0; jx < 2; ++jx) {
-          const float2 m = Ms[mo[jx] + c * (MODE == 2 ? 16 : 12)];
-          sv[jx] = make_float2(m.x * sc, m.y * sc);   // the split scale, folded into the matrix value
-        }
-#pragma unroll
-        for (int iv = 0; iv < 8; ++iv) {
-          const float2 pv = Vs[(iv >> 2) * 16 * 12 + (iv & 3) * 3 + c];   // noise iv/4, spin iv%4
-#pragma unroll
-          for (int jx = 0; jx < 2; ++jx) {
-            float2 &a = acc[jx][iv];
-            if (MODE == 0) {          // conj(psi) * S
-              a.x = fmaf(pv.x, sv[jx].x, fmaf(pv.y, sv[jx].y, a.x));
-              a.y = fmaf(pv.x, sv[jx].y, fmaf(-pv.y, sv[jx].x, a.y));
-            } else if (MODE == 1) {   // eta * conj(S)
-              a.x = fmaf(pv.x, sv[jx].x, fmaf(pv.y, sv[jx].y, a.x));
-              a.y = fmaf(pv.y, sv[jx].x, fmaf(-pv.x, sv[jx].y, a.y));
-            } else {                  // eta * D
-              a.x = fmaf(pv.x, sv[jx].x, fmaf(-pv.y, sv[jx].y, a.x));
-              a.y = fmaf(pv.x, sv[jx].y, fmaf(pv.y, sv[jx].x, a.y));
-            }
-          }
-        }
-      }
-      // the input stage is read: hand it back to the input loader
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&inEmpty[si]);
-      const int s = kstep % NSTAGE, pr = s >> 1, u = kstep / NSTAGE;
-      if (u > 0) {
-        // the MMA must be done with this A stage (from NSTAGE k-steps ago)
-        if (wq == 0 && lane == 0) vempty[it & 1] = tc::mbar_wait(&empty[pr], (u - 1) & 1, err, 8) ? 1 : 0;
+    static_assert(NIN == 2 * NPK && NSTAGE == 2 * NPK, "stage indices from the iteration count");
+    // The loop is compiled twice: with the split scale and, for unit-scale data (e = 0),
+    // without its multiplications.
+    auto produce = [&](auto scaled) {
+      for (int it = 0; it < nit; ++it) {
+        const int kstep = NPK * it + kofs;
+        if (kstep >= nk) break;
+        // k-step kstep = NPK it + kofs uses input stage and A stage kstep % 6 = kofs + 3 (it & 1),
+        // in round kstep / 6 = it / 2
+        const int si = kofs + NPK * (it & 1), ui = it >> 1;
+        // The first warp of the group waits for each barrier; the four warps block on the
+        // group's named barrier and follow its verdict together, so a wait that gives up (a
+        // loader stopped, or the limit ran out) ends the loop of all four at once.
+        volatile int *vin = verdict + 2 + 4 * kofs, *vempty = vin + 2;
+        if (wq == 0 && lane == 0) vin[it & 1] = tc::mbar_wait(&inFull[si], ui & 1, err, 6) ? 1 : 0;
         tc::named_bar_sync(2 + kofs, 128);
-        if (!vempty[it & 1]) break;
-      }
-      char *a_st = stA(s);
-#pragma unroll
-      for (int jx = 0; jx < 2; ++jx) {
-        uint32_t rh[4], rl[4], ih[4], il[4];
-#pragma unroll
-        for (int pr = 0; pr < 4; ++pr) {
-          split2(acc[jx][2 * pr].x, acc[jx][2 * pr + 1].x, rh[pr], rl[pr]);
-          split2(acc[jx][2 * pr].y, acc[jx][2 * pr + 1].y, ih[pr], il[pr]);
+        if (!vin[it & 1]) break;
+        const float2 *Ms = reinterpret_cast<const float2 *>(stM(si));
+        const float2 *Vs = reinterpret_cast<const float2 *>(stV(si)) + x * 12;
+        float2 acc[2][8];
+  #pragma unroll
+        for (int jx = 0; jx < 2; ++jx)
+  #pragma unroll
+          for (int iv = 0; iv < 8; ++iv) acc[jx][iv] = make_float2(0.f, 0.f);
+        // the matrix values of both columns and all three colours (scaled for the split
+        // unless the data is unit-scale), then per (noise, spin) the vector's three colours,
+        // contiguous in the box, with one 16-byte and one 8-byte load; each accumulator
+        // still sums the colours in the order 0, 1, 2
+        float2 sv[3][2];
+  #pragma unroll
+        for (int c = 0; c < 3; ++c)
+  #pragma unroll
+          for (int jx = 0; jx < 2; ++jx) {
+            const float2 m = Ms[mo[jx] + c * (MODE == 2 ? 16 : 12)];
+            if constexpr (decltype(scaled)::value)
+              sv[c][jx] = make_float2(m.x * sc, m.y * sc);   // the split scale, folded into the matrix value
+            else
+              sv[c][jx] = m;
+          }
+  #pragma unroll
+        for (int iv = 0; iv < 8; ++iv) {
+          const float2 *pb = Vs + (iv >> 2) * 16 * 12 + (iv & 3) * 3;   // noise iv/4, spin iv%4
+          float2 pv[3];
+          if ((iv & 1) == 0) {   // colours 0, 1 start on a 16-byte boundary
+            const float4 q = *reinterpret_cast<const float4 *>(pb);
+            pv[0] = make_float2(q.x, q.y);
+            pv[1] = make_float2(q.z, q.w);
+            pv[2] = pb[2];
+          } else {               // colours 1, 2 do
+            pv[0] = pb[0];
+            const float4 q = *reinterpret_cast<const float4 *>(pb + 1);
+            pv[1] = make_float2(q.x, q.y);
+            pv[2] = make_float2(q.z, q.w);
+          }
+  #pragma unroll
+          for (int c = 0; c < 3; ++c)
+  #pragma unroll
+            for (int jx = 0; jx < 2; ++jx) {
+              float2 &a = acc[jx][iv];
+              const float2 p = pv[c], m = sv[c][jx];
+              if (MODE == 0) {          // conj(psi) * S
+                a.x = fmaf(p.x, m.x, fmaf(p.y, m.y, a.x));
+                a.y = fmaf(p.x, m.y, fmaf(-p.y, m.x, a.y));
+              } else if (MODE == 1) {   // eta * conj(S)
+                a.x = fmaf(p.x, m.x, fmaf(p.y, m.y, a.x));
+                a.y = fmaf(p.y, m.x, fmaf(-p.x, m.y, a.y));
+              } else {                  // eta * D
+                a.x = fmaf(p.x, m.x, fmaf(-p.y, m.y, a.x));
+                a.y = fmaf(p.x, m.y, fmaf(p.y, m.x, a.y));
+              }
+            }
         }
-        // row group s = sp + 8 jx, its 8 rows (noise, spin) contiguous at k = site x
-        const uint32_t off = (uint32_t)((sp + 8 * jx) * 144 + (x >> 3) * 2304 + (x & 7) * 16);
-        *reinterpret_cast<uint4 *>(a_st + 0 * ATILE + off) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
-        *reinterpret_cast<uint4 *>(a_st + 1 * ATILE + off) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
-        *reinterpret_cast<uint4 *>(a_st + 2 * ATILE + off) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
-        *reinterpret_cast<uint4 *>(a_st + 3 * ATILE + off) = make_uint4(il[0], il[1], il[2], il[3]);
+        // the input stage is read: hand it back to the input loader
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&inEmpty[si]);
+        const int s = si, pr = s >> 1, u = ui;
+        if (u > 0) {
+          // the MMA must be done with this A stage (from NSTAGE k-steps ago)
+          if (wq == 0 && lane == 0) vempty[it & 1] = tc::mbar_wait(&empty[pr], (u - 1) & 1, err, 8) ? 1 : 0;
+          tc::named_bar_sync(2 + kofs, 128);
+          if (!vempty[it & 1]) break;
+        }
+        char *a_st = stA(s);
+  #pragma unroll
+        for (int jx = 0; jx < 2; ++jx) {
+          uint32_t rh[4], rl[4], ih[4], il[4];
+  #pragma unroll
+          for (int pr = 0; pr < 4; ++pr) {
+            split2(acc[jx][2 * pr].x, acc[jx][2 * pr + 1].x, rh[pr], rl[pr]);
+            split2(acc[jx][2 * pr].y, acc[jx][2 * pr + 1].y, ih[pr], il[pr]);
+          }
+          // row group s = sp + 8 jx, its 8 rows (noise, spin) contiguous at k = site x
+          const uint32_t off = (uint32_t)((sp + 8 * jx) * 144 + (x >> 3) * 2304 + (x & 7) * 16);
+          *reinterpret_cast<uint4 *>(a_st + 0 * ATILE + off) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+          *reinterpret_cast<uint4 *>(a_st + 1 * ATILE + off) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+          *reinterpret_cast<uint4 *>(a_st + 2 * ATILE + off) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+          *reinterpret_cast<uint4 *>(a_st + 3 * ATILE + off) = make_uint4(il[0], il[1], il[2], il[3]);
+        }
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&full[pr]);
       }
-      tc::fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&full[pr]);
-    }
+    };
+    if (sc_e == 0)
+      produce(std::false_type{});
+    else
+      produce(std::true_type{});
   }
   tc::tc_fence_before();
   __syncthreads();

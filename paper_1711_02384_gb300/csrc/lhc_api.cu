@@ -209,6 +209,13 @@ static std::mutex g_sync_mu;
 static int stage_streams(lhc_ctx ctx) {
   if (ctx->d2h) return LHC_OK;
   LHC_CHECK_CUDA(cudaStreamCreateWithFlags(&ctx->h2d, cudaStreamNonBlocking));
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = ctx->device;
+  LHC_CHECK_CUDA(cudaMemPoolCreate(&ctx->stage_pool, &props));
+  uint64_t keep = UINT64_MAX;   // freed slot memory stays mapped for the next growth
+  LHC_CHECK_CUDA(cudaMemPoolSetAttribute(ctx->stage_pool, cudaMemPoolAttrReleaseThreshold, &keep));
   for (int s = 0; s < lhc_ctx_s::kStageSlots; ++s) {
     LHC_CHECK_CUDA(cudaEventCreateWithFlags(&ctx->slot_free[s], cudaEventDisableTiming));
     LHC_CHECK_CUDA(cudaEventCreateWithFlags(&ctx->in_ready[s], cudaEventDisableTiming));
@@ -218,30 +225,39 @@ static int stage_streams(lhc_ctx ctx) {
   return LHC_OK;
 }
 
-// Grows staging slot s in stream order on the H2D stream, which already waits for the
-// slot's previous call: the old buffer goes back with cudaFreeAsync and the new one comes
-// from cudaMallocAsync, so a growing slot never synchronizes the device (cudaFree would).
-static int stage_grow(lhc_ctx ctx, int s, size_t bytes) {
-  DevBuf &b = ctx->stage[s];
-  if (b.bytes >= bytes) return LHC_OK;
+// Grows every staging slot to `bytes` plus a quarter, in stream order on the H2D stream:
+// the stream first waits for each slot's last call, then the old buffers go back with
+// cudaFreeAsync and the new ones come from the context's pool with
+// cudaMallocFromPoolAsync.  No device synchronization (cudaFree would be one), and since
+// all slots grow together, calls of different sizes rotating over the slots grow nothing
+// once the largest has been seen.
+static int stage_grow(lhc_ctx ctx, size_t bytes) {
+  if (ctx->stage_bytes >= bytes) return LHC_OK;
   const size_t want = bytes + bytes / 4;
-  while (ctx->budget && ctx->used - b.bytes + want > ctx->budget && !ctx->phase_lru.empty()) evict_one_phase(ctx);
-  if (ctx->budget && ctx->used - b.bytes + want > ctx->budget)
-    return fail(LHC_EBUDGET, "staging slot of %zu bytes exceeds the HBM budget (%zu of %zu in use)", want,
-                ctx->used - b.bytes, ctx->budget);
-  if (b.p) {
-    LHC_CHECK_CUDA(cudaFreeAsync(b.p, ctx->h2d));
-    ctx->used -= b.bytes;
-    b = DevBuf{};
+  const size_t held = ctx->stage_bytes * (size_t)lhc_ctx_s::kStageSlots;
+  const size_t need = want * (size_t)lhc_ctx_s::kStageSlots;
+  while (ctx->budget && ctx->used - held + need > ctx->budget && !ctx->phase_lru.empty()) evict_one_phase(ctx);
+  if (ctx->budget && ctx->used - held + need > ctx->budget)
+    return fail(LHC_EBUDGET, "%d staging slots of %zu bytes exceed the HBM budget (%zu of %zu in use)",
+                lhc_ctx_s::kStageSlots, want, ctx->used - held, ctx->budget);
+  for (int s = 0; s < lhc_ctx_s::kStageSlots; ++s) {
+    DevBuf &b = ctx->stage[s];
+    if (ctx->slot_used[s]) LHC_CHECK_CUDA(cudaStreamWaitEvent(ctx->h2d, ctx->slot_free[s], 0));
+    if (b.p) {
+      LHC_CHECK_CUDA(cudaFreeAsync(b.p, ctx->h2d));
+      ctx->used -= b.bytes;
+      b = DevBuf{};
+    }
+    cudaError_t e = cudaMallocFromPoolAsync(&b.p, want, ctx->stage_pool, ctx->h2d);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      b = DevBuf{};
+      return fail(LHC_ENOMEM, "cudaMallocFromPoolAsync(%zu): %s", want, cudaGetErrorString(e));
+    }
+    b.bytes = want;
+    ctx->used += want;
   }
-  cudaError_t e = cudaMallocAsync(&b.p, want, ctx->h2d);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    b = DevBuf{};
-    return fail(LHC_ENOMEM, "cudaMallocAsync(%zu): %s", want, cudaGetErrorString(e));
-  }
-  b.bytes = want;
-  ctx->used += want;
+  ctx->stage_bytes = want;
   return LHC_OK;
 }
 
@@ -251,7 +267,7 @@ static int stage_begin(lhc_ctx ctx, size_t bytes, int *slot, char **base) {
   const int s = ctx->next_slot;
   ctx->next_slot = (s + 1) % lhc_ctx_s::kStageSlots;
   if (ctx->slot_used[s]) LHC_CHECK_CUDA(cudaStreamWaitEvent(ctx->h2d, ctx->slot_free[s], 0));
-  LHC_TRY(stage_grow(ctx, s, bytes));
+  LHC_TRY(stage_grow(ctx, bytes));
   *slot = s;
   *base = static_cast<char *>(ctx->stage[s].p);
   return LHC_OK;
@@ -306,8 +322,18 @@ static int stage_end(lhc_ctx ctx, int slot, cudaStream_t st, void *host_out, con
   return LHC_OK;
 }
 
-static void stage_release(lhc_ctx ctx) {
-  for (int s = 0; s < lhc_ctx_s::kStageSlots; ++s) dev_free(ctx, ctx->stage[s]);
+static void stage_release(lhc_ctx ctx) {   // the device is synchronized
+  for (int s = 0; s < lhc_ctx_s::kStageSlots; ++s) {
+    DevBuf &b = ctx->stage[s];
+    if (b.p) {
+      cudaFreeAsync(b.p, ctx->h2d);   // pool memory, returned in the H2D stream's order
+      ctx->used -= b.bytes;
+    }
+    b = DevBuf{};
+  }
+  ctx->stage_bytes = 0;
+  if (ctx->h2d) cudaStreamSynchronize(ctx->h2d);
+  if (ctx->stage_pool) cudaMemPoolTrimTo(ctx->stage_pool, 0);
 }
 
 static void stage_destroy(lhc_ctx ctx) {
@@ -326,6 +352,10 @@ static void stage_destroy(lhc_ctx ctx) {
     cudaStreamDestroy(ctx->d2h);
     cudaEventDestroy(ctx->comp_done);
     ctx->d2h = nullptr;
+  }
+  if (ctx->stage_pool) {
+    cudaMemPoolDestroy(ctx->stage_pool);
+    ctx->stage_pool = nullptr;
   }
 }
 

@@ -106,10 +106,14 @@ struct lhc_ctx_s {
   // H2D copy stream (copies land in call order; a slot's reuse waits for the call
   // kStageSlots back, which with 8 slots is normally long done), one D2H copy stream,
   // and the host ranges that output copies still in flight will write (a later call
-  // reading such a range waits for that copy).  A slot only holds device memory once a
-  // host-buffer call has used it.
+  // reading such a range waits for that copy).  All slots have one size, grown together
+  // (in stream order, from a memory pool of the context that keeps freed memory mapped)
+  // when a call needs more, so a rotation of differently sized calls over the slots
+  // grows nothing once the largest call has been seen.
   static constexpr int kStageSlots = 8;
   lhc::DevBuf stage[kStageSlots];
+  size_t stage_bytes = 0;                 // the size of every allocated slot
+  cudaMemPool_t stage_pool = nullptr;
   cudaStream_t h2d = nullptr, d2h = nullptr;
   cudaEvent_t slot_free[kStageSlots] = {}, in_ready[kStageSlots] = {}, comp_done = nullptr;
   bool slot_used[kStageSlots] = {};
