@@ -275,6 +275,8 @@ def main():
     e1.record(st)
     barrier()
     clk = clocks.stop()
+    for c in ctxs:   # a kernel that gave up a bounded wait raises here instead of giving a number
+        c.sync()
     n_launches = lhc.launch_count() - n_launch0
     ms = e0.elapsed_time(e1)
     ms = max_over_ranks(ms, world, dev)
@@ -372,6 +374,7 @@ def main():
             step_host()
         torch.cuda.synchronize(dev)
         dt = (time.perf_counter() - t0) / ne
+        ctx.sync()
         V3 = L ** 3
         h2d = S_p.numel() * 16 + sum(g.numel() * 16 for g in G_p)                 # propagator slices, Gammas
         h2d += sum(N_R * (tf + 1) * V3 * 12 * 16 + N_R * V3 * 12 * 16 for tf in TFS)   # psi slices, eta

@@ -52,7 +52,10 @@ def _roofline(ctx):
             "peak_source": "measured bf16 burst (fp16 same rate)"}
 
 
-def _timed(step, steps, warmup, dev, stream=None):
+def _timed(step, steps, warmup, dev, stream=None, ctx=None):
+    """CUDA-event time of `steps` calls of `step` after `warmup` untimed ones.  With `ctx`,
+    the library's error check follows the timed region: a kernel that gave up a bounded
+    wait (its results invalid, its time meaningless) raises instead of giving a number."""
     for _ in range(warmup):
         step()
     torch.cuda.synchronize(dev)
@@ -66,6 +69,8 @@ def _timed(step, steps, warmup, dev, stream=None):
         step()
     e1.record(st)
     torch.cuda.synchronize(dev)
+    if ctx is not None:
+        ctx.sync()
     return e0.elapsed_time(e1), clocks.stop(), lhc.launch_count() - n0
 
 
@@ -112,7 +117,7 @@ def run_baryon32(args, dev, g):
             ctx.spectator(GA, etas[j], tf, r, k, prec=args.prec, GB=GB, out=osb[j])
             ctx.combine(osb[j], oi[j], Ws, Gi, Wc, prec=args.prec, out=oc[j])
 
-    ms, clk, nl = _timed(step, args.steps, args.warmup, dev)
+    ms, clk, nl = _timed(step, args.steps, args.warmup, dev, ctx=ctx)
     units = sum(tf + 2 for tf in TFS) * V3 * NR * nq
     ctx.profile(True)
     step()
@@ -190,7 +195,7 @@ def run_batched(args, dev, g):
             step_calls()
         n_graph = lhc.launch_count() - n0
         # graph.replay() launches on the current stream: keep it, and the events, on `stream`
-        ms, clk, _ = _timed(lambda: graph.replay(), args.steps, args.warmup, dev, stream=stream)
+        ms, clk, _ = _timed(lambda: graph.replay(), args.steps, args.warmup, dev, stream=stream, ctx=ctx)
         # one replay against the same calls issued directly: identical bits expected
         outs = [o for j in jobs for o in (j["oi"], j["om"], j["ob"])]
         for o in outs:
@@ -346,7 +351,7 @@ def run_mom1(args, dev, g):
                 ctx.insertion(S, psis[j], 0, tf, r, k, prec=args.prec, out=oi[j])
                 ctx.spectator(S, etas[j], tf, r, k, prec=args.prec, out=osp[j])
 
-        ms, clk, nl = _timed(step, args.steps, args.warmup, dev)
+        ms, clk, nl = _timed(step, args.steps, args.warmup, dev, ctx=ctx)
         out[name] = {"ms_per_step": ms / args.steps, "nq": nq, "gpu_launches": nl, "clocks": clk,
                      "value": sum(tf + 2 for tf in TFS) * V3 * NR * nq * args.steps / (ms / 1e3)}
     ctx.close()
@@ -385,7 +390,7 @@ def run_allmom(args, dev, g):
             ctx.insertion(S, psi, 0, NT - 1, r, k, prec=prec, out=oi)
             ctx.spectator(S, eta, NT, r, k, prec=prec, out=osp)
 
-        ms, clk, nl = _timed(step, steps, 1 if name == "gemm_fp64" else args.warmup, dev)
+        ms, clk, nl = _timed(step, steps, 1 if name == "gemm_fp64" else args.warmup, dev, ctx=ctx)
         out[name] = {"ms_per_step": ms / steps, "value": units * steps / (ms / 1e3), "gpu_launches": nl,
                      "clocks": clk}
     ctx.close()
@@ -435,7 +440,7 @@ def run_paper(args, dev, g):
             ctx.combine(om[d], ins, g16, g4, g16, prec=args.prec, out=cm[d])
             ctx.combine(ob[d], ins, Ws, g4[:4], Wc, prec=args.prec, out=cb[d])
 
-    ms, clk, nl = _timed(step, args.steps, args.warmup, dev)
+    ms, clk, nl = _timed(step, args.steps, args.warmup, dev, ctx=ctx)
     units = (nsl + 4) * V3 * NR * nq
     ctx.close()
     _line(args, B.METRIC, units * args.steps / (ms / 1e3), ms / args.steps,
@@ -462,7 +467,7 @@ def run_extras(args, dev, g):
     res = torch.empty((1, 16, 16, nq, nq, 4, 4), dtype=torch.complex128, device=dev)
     for prec in ("mixed", "fp64"):
         ms, clk, nl = _timed(lambda: ctx.combine_open(spec, ins, g16, g16, prec=prec, out=res), args.steps,
-                             args.warmup, dev)
+                             args.warmup, dev, ctx=ctx)
         out["open_combine_" + prec] = {"ms_per_sweep": ms / args.steps,
                                        "correlators_per_s": 16 ** 3 * nq * nq * args.steps / (ms / 1e3),
                                        "clocks": clk}
@@ -472,7 +477,7 @@ def run_extras(args, dev, g):
     bres = torch.empty((1, 4, 16, nq, nq, 4, 4, 4), dtype=torch.complex128, device=dev)
     for prec in ("mixed", "fp64"):
         ms, clk, nl = _timed(lambda: ctx.combine_open_baryon(bspec, ins, w4, g16, prec=prec, out=bres), args.steps,
-                             args.warmup, dev)
+                             args.warmup, dev, ctx=ctx)
         out["open_baryon_combine_" + prec] = {"ms_per_call": ms / args.steps, "sink_structures": 4,
                                               "insertion_gammas": 16,
                                               "open_blocks_per_s": 4 * 16 * nq * nq * args.steps / (ms / 1e3),

@@ -1338,6 +1338,14 @@ static int autotune(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int
       status = s != LHC_OK ? s : LHC_ECUDA;
       break;
     }
+    // a candidate whose kernels gave up a bounded wait would time as the fastest (every
+    // later wait gives up at once): stop and report instead of choosing it
+    int code = 0;
+    if (cudaMemcpy(&code, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || code != 0) {
+      set_error("autotune: shape NH %d, %d splits: a bounded device wait gave up (site %d)", c.first, c.second, code);
+      status = LHC_ETIMEOUT;
+      break;
+    }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     const float us = ms * 500.f;   // per run

@@ -71,7 +71,11 @@ def _klists():
     mixed = np.concatenate([mixed, mixed[:5], -mixed[5:9]])          # duplicates and partners
     modL = np.array([[2, 0, 0], [-2, 0, 0], [2, 2, 0], [-2, 2, 0], [0, -2, 2], [1, 0, 0], [-1, 0, 0]])
     big = np.concatenate([momenta(18), np.array([[9, 0, 0], [0, 0, -9]])])   # 173 representatives: 4 chunks
-    return [("unpaired", half), ("shuffled", mixed), ("k=-k mod L", modL), ("four chunks", big)]
+    k9 = momenta(9)
+    extra = np.array([k for k in k9 if k @ k == 9 and tuple(k) > tuple(-k)])[:4]
+    r51 = np.concatenate([momenta(8), extra, -extra])               # 51 representatives: two chunks of 32
+    return [("unpaired", half), ("shuffled", mixed), ("k=-k mod L", modL), ("four chunks", big),
+            ("51 representatives", r51), ("62 representatives", k9)]
 
 
 @pytest.mark.parametrize("name,k", _klists(), ids=lambda v: v if isinstance(v, str) else "")
@@ -79,7 +83,8 @@ def test_momentum_lists(ctx, name, k):
     """The projection groups the momenta into pairs {k, -k} and forms both from the same
     cos and sin sums: momentum lists with unpaired momenta, broken pairs, duplicates,
     an arbitrary order, momenta whose negatives coincide modulo L (L = 4), and more
-    representatives than one chunk, all against the oracle."""
+    representatives than one chunk (51 and 62: two chunks; 173: four), all against the
+    oracle."""
     c = CS.Case(4, 4, 2, k, seed=1450, r=(3, 1, 2, 0))
     gi = ctx.insertion(dev(c.S), dev(c.psi), 0, 2, c.r, c.k, prec="mixed").cpu().numpy()
     gs = ctx.spectator(dev(c.S), dev(c.eta(2)), 2, c.r, c.k, prec="mixed").cpu().numpy()
