@@ -175,6 +175,13 @@ int lhc_release_workspace(lhc_ctx ctx);
  * LHC_ETIMEOUT and the context stays usable.  Returns the lhc_sync status. */
 int lhc_selftest_timeout(lhc_ctx ctx, int limit_us, void *stream);
 
+/* The same bounded wait without the report: on return (asynchronously, on `stream`) the
+ * context's device error word is set, as after a kernel that gave up a wait, until the
+ * next lhc_sync reports it.  Meanwhile the context's kernels give up their waits at once,
+ * and an autotuning call stops with LHC_ETIMEOUT instead of recording a shape.  For tests
+ * of failure handling; limit_us as above. */
+int lhc_selftest_flag(lhc_ctx ctx, int limit_us, void *stream);
+
 /* ---------------------------------------------------------------- job server
  * Continuous batching of contraction jobs (the serving form of the hot path; the paper
  * runs measurements as batch jobs and has no counterpart).  lhc_serve_start starts a

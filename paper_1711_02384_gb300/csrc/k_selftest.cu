@@ -42,3 +42,18 @@ extern "C" int lhc_selftest_timeout(lhc_ctx ctx, int limit_us, void *stream) {
   LHC_CHECK_CUDA(cudaGetLastError());
   return lhc_sync(ctx, stream);
 }
+
+extern "C" int lhc_selftest_flag(lhc_ctx ctx, int limit_us, void *stream) {
+  if (!ctx || limit_us < 1 || limit_us > 2000000) {
+    lhc::set_error("lhc_selftest_flag: bad arguments");
+    return LHC_EINVAL;
+  }
+  LHC_CHECK_CUDA(cudaSetDevice(ctx->device));
+  int clk_khz = 0;
+  LHC_CHECK_CUDA(cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, ctx->device));
+  const long long cycles = (long long)limit_us * (long long)clk_khz / 1000;
+  never_completed_wait<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(ctx->dev_err, cycles);
+  lhc::note_launch();
+  LHC_CHECK_CUDA(cudaGetLastError());
+  return LHC_OK;
+}

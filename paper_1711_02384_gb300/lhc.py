@@ -89,6 +89,7 @@ def lib():
         u64 = ctypes.c_uint64
         L.lhc_release_workspace.argtypes = [vp]
         L.lhc_selftest_timeout.argtypes = [vp, ci, vp]
+        L.lhc_selftest_flag.argtypes = [vp, ci, vp]
         L.lhc_serve_start.argtypes = [vp, ci]
         L.lhc_serve_stop.argtypes = [vp]
         L.lhc_prop_register.argtypes = [vp, vp, lp, ctypes.POINTER(u64)]
@@ -116,7 +117,7 @@ def lib():
         for name in ("lhc_batch", "lhc_combine_open", "lhc_combine_open_baryon", "lhc_set_projection", "lhc_wilson_apply", "lhc_wilson_solve", "lhc_set_tuning", "lhc_tuning_table", "lhc_tuning_load",
                      "lhc_create", "lhc_destroy", "lhc_set_gamma5", "lhc_momenta", "lhc_insertion",
                      "lhc_spectator", "lhc_combine", "lhc_profile", "lhc_profile_read", "lhc_sync", "lhc_release_workspace",
-                     "lhc_selftest_timeout", "lhc_serve_start", "lhc_serve_stop", "lhc_prop_register",
+                     "lhc_selftest_timeout", "lhc_selftest_flag", "lhc_serve_start", "lhc_serve_stop", "lhc_prop_register",
                      "lhc_prop_release", "lhc_submit", "lhc_poll", "lhc_wait", "lhc_cancel", "lhc_job_times",
                      "lhc_serve_stats"):
             getattr(L, name).restype = ci
@@ -482,3 +483,8 @@ class Context:
         """Run the bounded-wait self-test; returns the lhc_sync status (LHC_ETIMEOUT expected)."""
         st = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
         return lib().lhc_selftest_timeout(self._h, int(limit_us), ctypes.c_void_p(int(st)))
+
+    def selftest_flag(self, limit_us=1000, stream=None):
+        """The same bounded wait, leaving the device error word set until the next sync."""
+        st = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        _check(lib().lhc_selftest_flag(self._h, int(limit_us), ctypes.c_void_p(int(st))))

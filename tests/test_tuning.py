@@ -1,6 +1,7 @@
 """Launch-shape autotuner of the mixed path: the table file format and loading (host
 only), and on the GPU that a tuned call keeps parity with the oracle, records its shape,
-persists it, and that later calls of the shape reproduce the tuned call bit for bit."""
+persists it, that later calls of the shape reproduce the tuned call bit for bit, and that
+tuning stops instead of recording a shape whose kernels gave up a bounded wait."""
 import ctypes
 
 import numpy as np
@@ -70,3 +71,30 @@ def test_tuned_call_parity_persistence_and_reuse(lhc, tmp_path):
         third = ctx2.insertion(dev(c.S), dev(c.psi), 0, 3, c.r, c.k, prec="mixed")
         ctx2.sync()
         assert torch.equal(gi, third)
+
+
+@pytest.mark.gpu
+def test_autotune_stops_on_a_wait_that_gave_up(lhc):
+    """A candidate whose kernels gave up a bounded wait would time as the fastest (every
+    later wait gives up at once).  With the device error word set (the library's
+    bounded-wait self-test, no fault), a tuned call must stop with LHC_ETIMEOUT and record
+    no shape; after the sync reports the error, the same call tunes and runs."""
+    torch = pytest.importorskip("torch")
+    import _cases as CS
+    from oracle.momenta import momenta
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    c = CS.Case(9, 4, 2, momenta(2), seed=1810, r=(1, 2, 3, 0))   # V3 = 729: a key no other test tunes
+    with lhc.Context(0) as ctx:
+        ctx.set_tuning(True)
+        before = len(lhc.tuning_table())
+        ctx.selftest_flag(1000)
+        with pytest.raises(lhc.LhcError) as e:
+            ctx.insertion(dev(c.S), dev(c.psi), 0, 1, c.r, c.k, prec="mixed")
+        assert e.value.status == lhc.ETIMEOUT and "autotune" in str(e.value)
+        assert len(lhc.tuning_table()) == before
+        with pytest.raises(lhc.LhcError):
+            ctx.sync()                                               # reports the flag, clears it
+        gi = ctx.insertion(dev(c.S), dev(c.psi), 0, 1, c.r, c.k, prec="mixed")
+        ctx.sync()
+        assert len(lhc.tuning_table()) == before + 1
+        assert CS.block_err(gi.cpu().numpy(), c.ref_insertion(0, 1), 2) < CS.MIXED_TOL
