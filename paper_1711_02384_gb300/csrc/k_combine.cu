@@ -392,6 +392,16 @@ __global__ void __launch_bounds__(256) comb_gemm_open(const cplx<R> *__restrict_
 
 unsigned blocks(size_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
 
+// The staging kernels may take up to 200 KB of dynamic shared memory (set once per device).
+template <typename R>
+int staging_smem_limits() {
+  static std::atomic<unsigned long long> d0{0}, d1{0}, d2{0};
+  LHC_TRY(ensure_smem_limit(comb_ins_meson<R>, 200 * 1024, d0));
+  LHC_TRY(ensure_smem_limit(comb_ins_baryon<R>, 200 * 1024, d1));
+  LHC_TRY(ensure_smem_limit(comb_spec_meson<R>, 200 * 1024, d2));
+  return LHC_OK;
+}
+
 // Noises staged per pass by the staging kernels, and their shared memory: as many as fit
 // 96 KB next to the 2 ng Gamma matrices (two CTAs per SM), at least one.
 template <typename R>
@@ -403,15 +413,7 @@ int noise_chunk(int ng, int n_r, int *nch, size_t *smem) {
   }
   *nch = (int)std::min<size_t>((size_t)n_r, g_bytes + row <= 96 * 1024 ? (96 * 1024 - g_bytes) / row : 1);
   *smem = g_bytes + (size_t)*nch * row;
-  if (*smem > 48 * 1024) {
-    static bool attr = false;
-    if (!attr) {
-      LHC_CHECK_CUDA(cudaFuncSetAttribute(comb_ins_meson<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      LHC_CHECK_CUDA(cudaFuncSetAttribute(comb_ins_baryon<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      LHC_CHECK_CUDA(cudaFuncSetAttribute(comb_spec_meson<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      attr = true;
-    }
-  }
+  if (*smem > 48 * 1024) LHC_TRY(staging_smem_limits<R>());
   return LHC_OK;
 }
 
@@ -424,12 +426,8 @@ int spec_open_smem(int ng, size_t *smem) {
     return LHC_EINVAL;
   }
   if (*smem > 48 * 1024) {
-    static bool attr = false;
-    if (!attr) {
-      LHC_CHECK_CUDA(
-          cudaFuncSetAttribute(comb_spec_baryon_open<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      attr = true;
-    }
+    static std::atomic<unsigned long long> done{0};
+    LHC_TRY(ensure_smem_limit(comb_spec_baryon_open<R>, 200 * 1024, done));
   }
   return LHC_OK;
 }
@@ -479,15 +477,7 @@ int launch_combine(int kind, const double2 *spec, int np, const double2 *ins, in
   }
   const int nch = (int)std::min<size_t>((size_t)n_r, g_bytes + row <= 96 * 1024 ? (96 * 1024 - g_bytes) / row : 1);
   const size_t smem = g_bytes + (size_t)nch * row;
-  if (smem > 48 * 1024) {
-    static bool attr[4] = {false, false, false, false};
-    if (!attr[0]) {
-      LHC_CHECK_CUDA(cudaFuncSetAttribute(comb_ins_meson<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      LHC_CHECK_CUDA(cudaFuncSetAttribute(comb_ins_baryon<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      LHC_CHECK_CUDA(cudaFuncSetAttribute(comb_spec_meson<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      attr[0] = true;
-    }
-  }
+  if (smem > 48 * 1024) LHC_TRY(staging_smem_limits<R>());
   if (kind == LHC_MESON) {
     comb_spec_meson<R><<<np, 256, smem, st>>>(spec, np, n_r, nch, snk, ng, Xs);
     note_launch();

@@ -690,12 +690,8 @@ template <int MODE, int NH>
 int launch_fused_t(const FusedParams &p, int nt, cudaStream_t st) {
   constexpr size_t smem = fused_smem<MODE, NH>();
   static_assert(smem <= 232448, "shared memory per CTA");
-  static bool attr = false;
-  if (!attr) {
-    LHC_CHECK_CUDA(cudaFuncSetAttribute(fused_meson<float2, MODE, NH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)std::max<size_t>(smem, 120 * 1024)));
-    attr = true;
-  }
+  static std::atomic<unsigned long long> done{0};
+  LHC_TRY(ensure_smem_limit(fused_meson<float2, MODE, NH>, (int)std::max<size_t>(smem, 120 * 1024), done));
   dim3 grid(p.c.nct, p.c.nsplit, nt * p.c.nrc);
   // at least 120 KB so that one CTA runs per SM (the tensor memory is allocated whole)
   fused_meson<float2, MODE, NH><<<grid, kThreads, std::max<size_t>(smem, 120 * 1024), st>>>(p);
@@ -719,12 +715,8 @@ int launch_fused_nh(int NH, const FusedParams &p, int nt, cudaStream_t st) {
 template <int MODE, int NH>
 int launch_batch_t(const BatchParams &b, int nctas, cudaStream_t st) {
   constexpr size_t smem = fused_smem<MODE, NH>();
-  static bool attr = false;
-  if (!attr) {
-    LHC_CHECK_CUDA(cudaFuncSetAttribute(fused_batch<float2, MODE, NH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)std::max<size_t>(smem, 120 * 1024)));
-    attr = true;
-  }
+  static std::atomic<unsigned long long> done{0};
+  LHC_TRY(ensure_smem_limit(fused_batch<float2, MODE, NH>, (int)std::max<size_t>(smem, 120 * 1024), done));
   fused_batch<float2, MODE, NH><<<nctas, kThreads, std::max<size_t>(smem, 120 * 1024), st>>>(b);
   note_launch();
   return LHC_OK;

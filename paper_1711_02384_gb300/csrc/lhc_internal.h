@@ -38,6 +38,21 @@ void set_error(const char *fmt, ...);
     if (s_ != LHC_OK) return s_;      \
   } while (0)
 
+// Raises a kernel's dynamic shared-memory limit to `bytes` once per device.  `done` holds
+// one bit per device ordinal; it is atomic, so calls from several host threads (the job
+// server's scheduler and a caller) are safe, and a repeated call from a racing thread is
+// harmless.
+template <typename K>
+int ensure_smem_limit(K *kernel, int bytes, std::atomic<unsigned long long> &done) {
+  int dev = 0;
+  LHC_CHECK_CUDA(cudaGetDevice(&dev));
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return LHC_OK;
+  LHC_CHECK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.fetch_or(bit, std::memory_order_acq_rel);
+  return LHC_OK;
+}
+
 // ---------------------------------------------------------------- problem shapes
 constexpr int kInsCols = 192;       // (alpha~, beta~, beta, a) per noise
 constexpr int kMesCols = 192;       // (beta', alpha', alpha, a) per noise
