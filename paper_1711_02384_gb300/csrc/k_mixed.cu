@@ -1030,18 +1030,21 @@ static int encode_map(CUtensorMap *m, int rank, const void *base, const uint64_t
   }
   for (int i = 0; i + 1 < rank; ++i) sb[i] = strides[i];
   // the driver function is looked up through the runtime, so that the library itself
-  // loads on machines without a driver (and links no libcuda)
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
+  // loads on machines without a driver (and links no libcuda); the lookup runs once, and
+  // the static's initialization is thread-safe
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
         q != cudaDriverEntryPointSuccess || !fn) {
       cudaGetLastError();
-      set_error("the driver does not provide cuTensorMapEncodeTiled");
-      return LHC_ECUDA;
+      return nullptr;
     }
-    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!encode) {
+    set_error("the driver does not provide cuTensorMapEncodeTiled");
+    return LHC_ECUDA;
   }
   CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, (cuuint32_t)rank, const_cast<void *>(base), d, sb, b, es,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
