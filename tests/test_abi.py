@@ -79,3 +79,14 @@ def test_server_calls_validate_without_a_gpu(lib):
     assert lib.lhc_submit(None, None, None) == 1          # no server for a NULL context -> EINVAL
     assert lib.lhc_poll(None, 1, None) == 7               # LHC_ENOTFOUND
     assert lib.lhc_serve_start(None, 4) == 1
+
+
+@pytest.mark.parametrize("n2max,cmax", [(3, 1), (4, -1), (8, -1), (9, 3), (16, -1)])
+def test_momenta_host_helper_matches_oracle(lib, n2max, cmax):
+    """a0 on the host: the library's momentum list (C++) equals the oracle's (numpy), the
+    same vectors in the same order (|k|^2, then kx, ky, kz ascending)."""
+    from oracle.momenta import momenta
+    from paper_1711_02384_gb300 import lhc
+    ref = np.asarray(momenta(n2max, None if cmax < 0 else cmax), dtype=np.int32)
+    got = np.asarray(lhc.momenta(n2max, cmax), dtype=np.int32)
+    assert got.shape == ref.shape and np.array_equal(got, ref)
