@@ -38,8 +38,11 @@
  * as its input: the library tracks host ranges that output copies in flight will write
  * and orders the copies.  Pinned host memory gives overlap; pageable memory is copied
  * synchronously by CUDA.  The caller owns every buffer it passes; the library never
- * frees them.  The library owns its workspace and its cached phase tables,
- * both counted against the context's HBM budget.
+ * frees them.  The library owns its workspace, its cached phase tables and the
+ * staging slots, all counted against the context's HBM budget.  The eight slots share
+ * one size, 1.25 times the largest host-buffer call so far (its staged inputs and
+ * output), and grow together when a larger call arrives: with a tight budget, prefer
+ * device buffers for the largest calls.
  *
  * Errors: every call returns an lhc_status; nothing is thrown across the ABI.
  * Invalid arguments return LHC_EINVAL before anything is launched.
@@ -95,7 +98,8 @@ const char *lhc_last_error(void);
 int lhc_version(void);
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the device
- * memory the library itself allocates (workspace, phase tables); 0 = no bound. */
+ * memory the library itself allocates (workspace, phase tables, staging slots);
+ * 0 = no bound. */
 int lhc_create(lhc_ctx *ctx, int device, size_t hbm_budget_bytes);
 
 /* Destroy a context: synchronizes the device, then frees everything it owns. */
