@@ -12,7 +12,8 @@ serve     a Poisson stream of three-point jobs on 16^3x32 .. 48^3x96 lattices th
 mom1      the meson 24^3x48 step at 1 momentum vs 93 momenta (the paper's observation that
           many more momenta cost little extra)
 allmom    every momentum of a 16^3 slice (4096): the projection as a discrete Fourier
-          transform (FP64) against the direct FP64 and mixed projections
+          transform (FP64, and FP32 in the mixed path) against the direct FP64 and mixed
+          projections
 paper     the paper's own measurement on its lattice shape: 32^3 x 96, source at t = 30,
           sinks 10 slices before and after it, 50 noises on both sink slices, 93 momenta at
           sink and insertion, meson and baryon spectators, one insertion call over both
@@ -382,8 +383,8 @@ def run_allmom(args, dev, g):
     r = (3, 5, 7, 0)
     units = (NT + 1) * V3 * NR * nq
     out = {}
-    for name, prec, mode, steps in (("dft_fp64", "fp64", "dft", args.steps), ("gemm_mixed", "mixed", "gemm", args.steps),
-                                    ("gemm_fp64", "fp64", "gemm", 1)):
+    for name, prec, mode, steps in (("dft_fp64", "fp64", "dft", args.steps), ("dft_mixed", "mixed", "dft", args.steps),
+                                    ("gemm_mixed", "mixed", "gemm", args.steps), ("gemm_fp64", "fp64", "gemm", 1)):
         ctx.set_projection(mode)
 
         def step():
@@ -403,7 +404,8 @@ def run_allmom(args, dev, g):
                                  "l2": "inputs of every step larger than L2 (129 MB)"},
                       "runs": out,
                       "dft_vs_gemm_fp64": out["gemm_fp64"]["ms_per_step"] / out["dft_fp64"]["ms_per_step"],
-                      "dft_vs_gemm_mixed": out["gemm_mixed"]["ms_per_step"] / out["dft_fp64"]["ms_per_step"]}))
+                      "dft_vs_gemm_mixed": out["gemm_mixed"]["ms_per_step"] / out["dft_fp64"]["ms_per_step"],
+                      "mixed_dft_vs_mixed_gemm": out["gemm_mixed"]["ms_per_step"] / out["dft_mixed"]["ms_per_step"]}))
 
 
 # --------------------------------------------------------------------------- paper

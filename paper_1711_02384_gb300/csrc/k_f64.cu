@@ -2,6 +2,7 @@
 // reading) in FP64, written to a workspace in site chunks, then the momentum
 // projection sum_x P[q][x] U[x][col] as an FP64 complex GEMM on CUDA cores.
 // This is the comparator path and the 1e-12 parity reference on the GPU.
+#include "conv.cuh"
 #include "lhc_internal.h"
 
 namespace lhc {
@@ -27,14 +28,41 @@ __device__ __forceinline__ void cfma_cb(double2 &acc, double2 a, double2 b) {
   acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
   acc.y = fma(a.y, b.x, fma(-a.x, b.y, acc.y));
 }
-__device__ __forceinline__ double sgn(int mask, int s) { return ((mask >> s) & 1) ? -1.0 : 1.0; }
+// The same in FP32, for the contractions of the mixed path's all-momenta mode: inputs
+// are rounded to FP32 (complex128 by the integer IEEE conversion, off the FP64 pipe)
+// and the three-colour sums run in FP32.
+__device__ __forceinline__ float2 ldf(const float2 *p) { return *p; }
+__device__ __forceinline__ float2 ldf(const double2 *p) {
+  const double2 v = *p;
+  return make_float2(f64_to_f32_rne(v.x), f64_to_f32_rne(v.y));
+}
+__device__ __forceinline__ void cfma(float2 &acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
+  acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+}
+__device__ __forceinline__ void cfmac(float2 &acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x));
+  acc.y = fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y));
+}
+__device__ __forceinline__ void cfma_cb(float2 &acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x));
+  acc.y = fmaf(a.y, b.x, fmaf(-a.x, b.y, acc.y));
+}
+// load with conversion to the accumulation type OT (double2 or float2)
+template <typename OT, typename CT>
+__device__ __forceinline__ OT ldo(const CT *p) {
+  if constexpr (sizeof(OT) == sizeof(double2))
+    return ld2(p);
+  else
+    return ldf(p);
+}
 
 // Insertion (Eq. 10) before the momentum sum:
 // U[x][i][(at,bt,b,a)] = g5(at) sum_{a~} conj(psi_i(x)[at,a~]) S3(x)[(bt,a~),(b,a)]
-template <typename CT>
-__global__ void ins_contract_f64(const CT *__restrict__ S, const CT *__restrict__ psi,
-                                 size_t psi_stride, int n_r, int s0, int ns, int g5mask,
-                                 double2 *__restrict__ U) {
+template <typename CT, typename OT>
+__global__ void ins_contract(const CT *__restrict__ S, const CT *__restrict__ psi,
+                             size_t psi_stride, int n_r, int s0, int ns, int g5mask,
+                             OT *__restrict__ U) {
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t total = (size_t)ns * n_r * 192;
   if (idx >= total) return;
@@ -45,19 +73,19 @@ __global__ void ins_contract_f64(const CT *__restrict__ S, const CT *__restrict_
   int at = col / 48, bt = (col / 12) & 3, b = (col / 3) & 3, a = col % 3;
   const CT *s = S + (size_t)x * 144;
   const CT *p = psi + (size_t)i * psi_stride + (size_t)x * 12;
-  double2 acc = make_double2(0.0, 0.0);
+  OT acc{0, 0};
 #pragma unroll
-  for (int ac = 0; ac < 3; ++ac) cfmac(acc, ld2(p + at * 3 + ac), ld2(s + (bt * 3 + ac) * 12 + b * 3 + a));
-  double g = sgn(g5mask, at);
-  U[idx] = make_double2(g * acc.x, g * acc.y);
+  for (int ac = 0; ac < 3; ++ac) cfmac(acc, ldo<OT>(p + at * 3 + ac), ldo<OT>(s + (bt * 3 + ac) * 12 + b * 3 + a));
+  if ((g5mask >> at) & 1) acc = OT{-acc.x, -acc.y};
+  U[idx] = acc;
 }
 
 // Meson spectator (Eq. 9) before the momentum sum, G1(r,x') = g5 S1(x')^dagger g5:
 // V[x][i][(bp,ap,al,a)] = g5(bp) g5(ap) g5(al) sum_{a'} eta_i(x)[bp,a'] conj(S1(x)[(ap,a'),(al,a)])
-template <typename CT>
-__global__ void spec_meson_contract_f64(const CT *__restrict__ S, const CT *__restrict__ eta,
-                                        size_t eta_stride, int n_r, int s0, int ns, int g5mask,
-                                        double2 *__restrict__ U) {
+template <typename CT, typename OT>
+__global__ void spec_meson_contract(const CT *__restrict__ S, const CT *__restrict__ eta,
+                                    size_t eta_stride, int n_r, int s0, int ns, int g5mask,
+                                    OT *__restrict__ U) {
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t total = (size_t)ns * n_r * 192;
   if (idx >= total) return;
@@ -68,11 +96,11 @@ __global__ void spec_meson_contract_f64(const CT *__restrict__ S, const CT *__re
   int bp = col / 48, ap = (col / 12) & 3, al = (col / 3) & 3, a = col % 3;
   const CT *s = S + (size_t)x * 144;
   const CT *e = eta + (size_t)i * eta_stride + (size_t)x * 12;
-  double2 acc = make_double2(0.0, 0.0);
+  OT acc{0, 0};
 #pragma unroll
-  for (int ac = 0; ac < 3; ++ac) cfma_cb(acc, ld2(e + bp * 3 + ac), ld2(s + (ap * 3 + ac) * 12 + al * 3 + a));
-  double g = sgn(g5mask, bp) * sgn(g5mask, ap) * sgn(g5mask, al);
-  U[idx] = make_double2(g * acc.x, g * acc.y);
+  for (int ac = 0; ac < 3; ++ac) cfma_cb(acc, ldo<OT>(e + bp * 3 + ac), ldo<OT>(s + (ap * 3 + ac) * 12 + al * 3 + a));
+  if (((g5mask >> bp) ^ (g5mask >> ap) ^ (g5mask >> al)) & 1) acc = OT{-acc.x, -acc.y};
+  U[idx] = acc;
 }
 
 // Baryon spectator before the momentum sum:
@@ -80,10 +108,10 @@ __global__ void spec_meson_contract_f64(const CT *__restrict__ S, const CT *__re
 // D = sum eps_{a'b'c'} eps_{abc} GA[(a1p,a'),(a1,a)] GB[(a2p,b'),(a2,b)]; with
 // p=c'+1, q=c'+2, u=c+1, v=c+2 (mod 3) the four nonzero terms are
 // GA[p,u]GB[q,v] - GA[p,v]GB[q,u] - GA[q,u]GB[p,v] + GA[q,v]GB[p,u].
-template <typename CT>
-__global__ void spec_baryon_contract_f64(const CT *__restrict__ GA, const CT *__restrict__ GB,
-                                         const CT *__restrict__ eta, size_t eta_stride, int n_r,
-                                         int s0, int ns, int g5mask, double2 *__restrict__ U) {
+template <typename CT, typename OT>
+__global__ void spec_baryon_contract(const CT *__restrict__ GA, const CT *__restrict__ GB,
+                                     const CT *__restrict__ eta, size_t eta_stride, int n_r,
+                                     int s0, int ns, int g5mask, OT *__restrict__ U) {
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t total = (size_t)ns * n_r * 3072;
   if (idx >= total) return;
@@ -97,24 +125,23 @@ __global__ void spec_baryon_contract_f64(const CT *__restrict__ GA, const CT *__
   const CT *B = GB + (size_t)x * 144;
   const CT *e = eta + (size_t)i * eta_stride + (size_t)x * 12;
   int u = (c + 1) % 3, v = (c + 2) % 3;
-  double2 acc = make_double2(0.0, 0.0);
+  OT acc{0, 0};
 #pragma unroll
   for (int cp = 0; cp < 3; ++cp) {
     int p = (cp + 1) % 3, q = (cp + 2) % 3;
-    auto ga = [&](int r, int s) { return ld2(A + (a1p * 3 + r) * 12 + a1 * 3 + s); };
-    auto gb = [&](int r, int s) { return ld2(B + (a2p * 3 + r) * 12 + a2 * 3 + s); };
-    double2 d = make_double2(0.0, 0.0), t;
+    auto ga = [&](int r, int s) { return ldo<OT>(A + (a1p * 3 + r) * 12 + a1 * 3 + s); };
+    auto gb = [&](int r, int s) { return ldo<OT>(B + (a2p * 3 + r) * 12 + a2 * 3 + s); };
+    OT d{0, 0}, t{0, 0};
     cfma(d, ga(p, u), gb(q, v));
-    t = make_double2(0.0, 0.0);
     cfma(t, ga(p, v), gb(q, u));
     cfma(t, ga(q, u), gb(p, v));
     d.x -= t.x;
     d.y -= t.y;
     cfma(d, ga(q, v), gb(p, u));
-    cfma(acc, ld2(e + bp * 3 + cp), d);
+    cfma(acc, ldo<OT>(e + bp * 3 + cp), d);
   }
-  double g = sgn(g5mask, bp);
-  U[idx] = make_double2(g * acc.x, g * acc.y);
+  if ((g5mask >> bp) & 1) acc = OT{-acc.x, -acc.y};
+  U[idx] = acc;
 }
 
 // out[q][col] (+)= sum_{x < ns} P[q][s0 + x] U[x][col]   (complex FP64 GEMM)
@@ -193,20 +220,20 @@ __global__ void phase_f64_kernel(double2 *P, const int *k, int nq, int L, int rx
   P[idx] = make_double2(w.x, sign * w.y);
 }
 
-template <typename CT>
-void launch_contract(const SliceJob &j, int s0, int ns, double2 *U, cudaStream_t st) {
+template <typename CT, typename OT>
+void launch_contract(const SliceJob &j, int s0, int ns, OT *U, cudaStream_t st) {
   const CT *S = static_cast<const CT *>(j.S);
   const CT *v = static_cast<const CT *>(j.vec);
   int cols = j.part == PART_SPEC_BARYON ? kBarCols : 192;
   size_t total = (size_t)ns * j.n_r * cols;
   unsigned grid = (unsigned)((total + 255) / 256);
   if (j.part == PART_INS)
-    ins_contract_f64<CT><<<grid, 256, 0, st>>>(S, v, j.vec_stride, j.n_r, s0, ns, j.g5mask, U);
+    ins_contract<CT, OT><<<grid, 256, 0, st>>>(S, v, j.vec_stride, j.n_r, s0, ns, j.g5mask, U);
   else if (j.part == PART_SPEC_MESON)
-    spec_meson_contract_f64<CT><<<grid, 256, 0, st>>>(S, v, j.vec_stride, j.n_r, s0, ns, j.g5mask, U);
+    spec_meson_contract<CT, OT><<<grid, 256, 0, st>>>(S, v, j.vec_stride, j.n_r, s0, ns, j.g5mask, U);
   else
-    spec_baryon_contract_f64<CT><<<grid, 256, 0, st>>>(S, static_cast<const CT *>(j.SB), v,
-                                                       j.vec_stride, j.n_r, s0, ns, j.g5mask, U);
+    spec_baryon_contract<CT, OT><<<grid, 256, 0, st>>>(S, static_cast<const CT *>(j.SB), v, j.vec_stride, j.n_r,
+                                                       s0, ns, j.g5mask, U);
   note_launch();
 }
 
@@ -214,9 +241,18 @@ void launch_contract(const SliceJob &j, int s0, int ns, double2 *U, cudaStream_t
 
 int contract_f64(const SliceJob &j, int s0, int ns, double2 *U, cudaStream_t st) {
   if (j.dtype == LHC_C128)
-    launch_contract<double2>(j, s0, ns, U, st);
+    launch_contract<double2, double2>(j, s0, ns, U, st);
   else
-    launch_contract<float2>(j, s0, ns, U, st);
+    launch_contract<float2, double2>(j, s0, ns, U, st);
+  LHC_CHECK_CUDA(cudaGetLastError());
+  return LHC_OK;
+}
+
+int contract_f32(const SliceJob &j, int s0, int ns, float2 *U, cudaStream_t st) {
+  if (j.dtype == LHC_C128)
+    launch_contract<double2, float2>(j, s0, ns, U, st);
+  else
+    launch_contract<float2, float2>(j, s0, ns, U, st);
   LHC_CHECK_CUDA(cudaGetLastError());
   return LHC_OK;
 }
@@ -245,9 +281,9 @@ int run_slice_f64(lhc_ctx ctx, const SliceJob &j, const double2 *phase, cudaStre
       double bytes = (double)ns * (144.0 * nS + 12.0 * j.n_r) * es + (double)ns * cols * 16.0;
       ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT, bytes);
       if (j.dtype == LHC_C128)
-        launch_contract<double2>(j, s0, ns, U, st);
+        launch_contract<double2, double2>(j, s0, ns, U, st);
       else
-        launch_contract<float2>(j, s0, ns, U, st);
+        launch_contract<float2, double2>(j, s0, ns, U, st);
     }
     {
       ProfScope ps(ctx, st, LHC_KERNEL_PROJECT, 8.0 * j.nq * (double)cols * ns);

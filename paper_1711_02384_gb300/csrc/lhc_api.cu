@@ -665,7 +665,7 @@ int run_part(lhc_ctx ctx, const PartCall &c, cudaStream_t st) {
     }
     if (any_host) LHC_TRY(stage_ready(ctx, slot, st));
     if (dft) {
-      LHC_TRY(run_part_fft(ctx, jobs.data() + g0, g1 - g0, c.k, c.nq, c.r, c.sign, st));
+      LHC_TRY(run_part_fft(ctx, jobs.data() + g0, g1 - g0, c.k, c.nq, c.r, c.sign, c.prec, st));
     } else if (c.prec == LHC_MIXED) {
       // the call's launch shape for every group: each slice computed as in one launch
       LHC_TRY(run_part_mixed(ctx, jobs.data() + g0, g1 - g0, c.k, c.nq, c.r, c.sign, st, c.nt));

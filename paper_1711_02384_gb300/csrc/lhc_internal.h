@@ -170,11 +170,12 @@ int run_slice_f64(lhc_ctx ctx, const SliceJob &job, const double2 *phase, cudaSt
 
 // FP64 site contraction of sites s0 .. s0+ns-1 into U[site - s0][i][cols] (k_f64.cu)
 int contract_f64(const SliceJob &j, int s0, int ns, double2 *U, cudaStream_t st);
+int contract_f32(const SliceJob &j, int s0, int ns, float2 *U, cudaStream_t st);
 
 // all-momenta mode: FP64 contraction, three line DFTs over the slice, gather (k_fft.cu)
 bool use_fft(lhc_ctx ctx, int prec, int V3, int nq);
 int run_part_fft(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int nq, const int r[4], int sign,
-                 cudaStream_t st);
+                 int prec, cudaStream_t st);
 
 // mixed path: all slices of one call in one set of launches (k_mixed.cu)
 int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int nq, const int r[4], int sign,

@@ -86,9 +86,13 @@ def test_momentum_lists(ctx, name, k):
     representatives than one chunk (51 and 62: two chunks; 173: four), all against the
     oracle."""
     c = CS.Case(4, 4, 2, k, seed=1450, r=(3, 1, 2, 0))
-    gi = ctx.insertion(dev(c.S), dev(c.psi), 0, 2, c.r, c.k, prec="mixed").cpu().numpy()
-    gs = ctx.spectator(dev(c.S), dev(c.eta(2)), 2, c.r, c.k, prec="mixed").cpu().numpy()
-    ctx.sync()
+    ctx.set_projection("gemm")   # the tensor-core projection (on 4^3 many of these lists would take the DFT)
+    try:
+        gi = ctx.insertion(dev(c.S), dev(c.psi), 0, 2, c.r, c.k, prec="mixed").cpu().numpy()
+        gs = ctx.spectator(dev(c.S), dev(c.eta(2)), 2, c.r, c.k, prec="mixed").cpu().numpy()
+        ctx.sync()
+    finally:
+        ctx.set_projection("auto")
     assert report(f"ins {name}", CS.block_err(gi, c.ref_insertion(0, 2), 2)) < CS.MIXED_TOL
     assert report(f"spec {name}", CS.block_err(gs, c.ref_spectator_meson(2), 1)) < CS.MIXED_TOL
 
