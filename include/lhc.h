@@ -358,12 +358,13 @@ int lhc_batch(lhc_ctx ctx, const lhc_call *calls, int ncalls, void *stream);
  * FP64 and transforms along x, y and z with L-point sums (3L complex multiply-adds per
  * value, against nq for the direct projection, for any L). It then gathers the
  * requested momenta (any list, order or duplicates), each times exp(-+i p.r) for the
- * source position. The result is FP64 for both precisions.
- * LHC_PROJ_AUTO (the default) uses it for LHC_FP64 calls with nq >= L^3 / 2, where it
- * is far cheaper than the FP64 projection. LHC_MIXED calls keep the tensor-core
- * projection, which GB300's FP64 rate makes competitive up to about L = 24.
- * LHC_PROJ_GEMM never uses the transform, LHC_PROJ_DFT always. The paper projects
- * directly (it uses at most 93 momenta). */
+ * source position. LHC_FP64 calls contract and transform in FP64 (within 1e-12);
+ * LHC_MIXED calls contract and transform in FP32 (within 1e-6 per correlator). The
+ * output is complex128 either way.
+ * LHC_PROJ_AUTO (the default) uses it for calls with nq >= L^3 / 2, where it is far
+ * cheaper than the direct projection in either precision. LHC_PROJ_GEMM never uses
+ * the transform, LHC_PROJ_DFT always. The paper projects directly (it uses at most 93
+ * momenta). */
 typedef enum { LHC_PROJ_AUTO = 0, LHC_PROJ_GEMM = 1, LHC_PROJ_DFT = 2 } lhc_projection;
 int lhc_set_projection(lhc_ctx ctx, int mode);
 
