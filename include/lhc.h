@@ -354,9 +354,9 @@ int lhc_batch(lhc_ctx ctx, const lhc_call *calls, int ncalls, void *stream);
 
 /* ---- Momentum projection by discrete Fourier transform (all-momenta mode).
  * The projection of Eqs. 9 and 10 over every momentum of a slice is a 3-D discrete
- * Fourier transform of the contracted values. In this mode the library contracts in
- * FP64 and transforms along x, y and z with L-point sums (3L complex multiply-adds per
- * value, against nq for the direct projection, for any L). It then gathers the
+ * Fourier transform of the contracted values. In this mode the library contracts and
+ * transforms along x, y and z with L-point sums (3L complex multiply-adds per value,
+ * against nq for the direct projection, for any L). It then gathers the
  * requested momenta (any list, order or duplicates), each times exp(-+i p.r) for the
  * source position. LHC_FP64 calls contract and transform in FP64 (within 1e-12);
  * LHC_MIXED calls contract and transform in FP32 (within 1e-6 per correlator). The
