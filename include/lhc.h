@@ -343,10 +343,13 @@ typedef struct {
 } lhc_call;
 /* Runs ncalls calls in precision LHC_MIXED with one fused-kernel launch per part kind
  * and momentum-chunk width, for up to 64 calls per launch. The per-call staging and
- * reduce kernels stay separate launches. The results are bitwise those of the same
- * calls made one by one: each CTA does the work it does in its call's own launch, with
- * the same launch shape, taken from the tuning table or the heuristic (a batch never
- * tunes; tune its shapes with single calls first). Device buffers only. The calls'
+ * reduce kernels stay separate launches. A batch always projects on the tensor cores,
+ * whatever lhc_set_projection says. The results are bitwise those of the same calls
+ * made one by one in LHC_PROJ_GEMM mode: each CTA does the work it does in its call's
+ * own launch, with the same launch shape, taken from the tuning table or the heuristic
+ * (a batch never tunes; tune its shapes with single calls first). A call that asks
+ * for at least half of a slice's momenta takes the transform when made alone in
+ * LHC_PROJ_AUTO mode; the two agree within the mixed path's tolerance. Device buffers only. The calls'
  * outputs must not overlap their inputs or each other. Asynchronous on `stream`;
  * capturable in a CUDA graph once the phase tables exist (after a first run). The
  * paper has no counterpart: it ran one contraction at a time. */

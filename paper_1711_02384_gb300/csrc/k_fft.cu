@@ -102,9 +102,10 @@ __global__ void dft_gather_kernel(const T *__restrict__ F, const int *__restrict
 
 }  // namespace
 
-// Automatic choice: the FP64 transform replaces the FP64 projection for large momentum
-// sets (GB300's FP64 rate makes the direct FP64 projection the slowest part there); the
-// mixed path's tensor-core projection stays unless the transform is asked for.
+// Automatic choice: the transform replaces the direct projection once a call asks for at
+// least half of the slice's momenta.  In FP64 the direct projection is the slowest part
+// there (GB300's FP64 rate); in the mixed path the FP32 transform's 3L multiply-adds per
+// value cost less than the tensor-core projection with its split and drain at that size.
 bool use_fft(lhc_ctx ctx, int prec, int V3, int nq) {
   (void)prec;   // both precisions switch at half of the slice's momenta
   if (ctx->proj_mode == LHC_PROJ_DFT) return true;

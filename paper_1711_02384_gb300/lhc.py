@@ -254,7 +254,8 @@ class Context:
         """Mixed-precision calls in one fused launch per part kind: each call a dict with
         part ("ins", "spec" or "baryon"), S, vec, optional GB, t_lo, t_hi (t_lo = t_hi =
         t_sink for spectators), r, k and optional out (device tensors).  Returns the
-        outputs, bitwise those of the same calls made one by one."""
+        outputs, bitwise those of the same calls made one by one in "gemm" projection mode
+        (a batch always projects on the tensor cores)."""
         arr = (Call * len(calls))()
         keep, outs = [], []
         for a, c in zip(arr, calls):

@@ -1,5 +1,7 @@
 """Parity of the mixed-precision path (FP32 contraction, split-FP16 tcgen05 projection,
-FP64 reduction) against the FP64 oracle: per-correlator relative error < 1e-6."""
+FP64 reduction) against the FP64 oracle: per-correlator relative error < 1e-6.  The
+all-momenta transform that replaces the projection for large momentum lists in the
+automatic mode is covered by the DFT tests."""
 import numpy as np
 import pytest
 
@@ -14,6 +16,7 @@ pytestmark = pytest.mark.gpu
 def ctx():
     from paper_1711_02384_gb300 import lhc
     c = lhc.Context(0)
+    c.set_projection("gemm")   # this module covers the tensor-core projection at every momentum count
     yield c
     c.sync()
     c.close()
@@ -86,13 +89,9 @@ def test_momentum_lists(ctx, name, k):
     representatives than one chunk (51 and 62: two chunks; 173: four), all against the
     oracle."""
     c = CS.Case(4, 4, 2, k, seed=1450, r=(3, 1, 2, 0))
-    ctx.set_projection("gemm")   # the tensor-core projection (on 4^3 many of these lists would take the DFT)
-    try:
-        gi = ctx.insertion(dev(c.S), dev(c.psi), 0, 2, c.r, c.k, prec="mixed").cpu().numpy()
-        gs = ctx.spectator(dev(c.S), dev(c.eta(2)), 2, c.r, c.k, prec="mixed").cpu().numpy()
-        ctx.sync()
-    finally:
-        ctx.set_projection("auto")
+    gi = ctx.insertion(dev(c.S), dev(c.psi), 0, 2, c.r, c.k, prec="mixed").cpu().numpy()
+    gs = ctx.spectator(dev(c.S), dev(c.eta(2)), 2, c.r, c.k, prec="mixed").cpu().numpy()
+    ctx.sync()
     assert report(f"ins {name}", CS.block_err(gi, c.ref_insertion(0, 2), 2)) < CS.MIXED_TOL
     assert report(f"spec {name}", CS.block_err(gs, c.ref_spectator_meson(2), 1)) < CS.MIXED_TOL
 
