@@ -365,7 +365,7 @@ def main():
             st_done[b].record(st)
             side_done[b].record(side)
 
-        for _ in range(2):                    # both buffer parities; staging slots sized
+        for _ in range(max(3, args.warmup)):  # both buffer parities; staging slots sized
             step_host()
         torch.cuda.synchronize(dev)
         ne = max(1, min(args.steps, 10))
