@@ -38,7 +38,10 @@
  * as its input: the library tracks host ranges that output copies in flight will write
  * and orders the copies.  Pinned host memory gives overlap; pageable memory is copied
  * synchronously by CUDA.  The caller owns every buffer it passes; the library never
- * frees them.  The library owns its workspace, its cached phase tables and the
+ * frees them.  The first call with a new momentum list, lattice extent or source
+ * position builds its phase table (or, in the all-momenta mode, its device copy of the
+ * list) with blocking copies; later calls with the same list copy nothing from the host
+ * but their host buffers.  The library owns its workspace, its cached phase tables and the
  * staging slots, all counted against the context's HBM budget.  The eight slots share
  * one size, 1.25 times the largest host-buffer call so far (its staged inputs and
  * output), and grow together when a larger call arrives: with a tight budget, prefer
@@ -366,8 +369,9 @@ int lhc_batch(lhc_ctx ctx, const lhc_call *calls, int ncalls, void *stream);
  * output is complex128 either way.
  * LHC_PROJ_AUTO (the default) uses it for calls with nq >= L^3 / 2, where it is far
  * cheaper than the direct projection in either precision. LHC_PROJ_GEMM never uses
- * the transform, LHC_PROJ_DFT always. The paper projects directly (it uses at most 93
- * momenta). */
+ * the transform, LHC_PROJ_DFT always. Asynchronous on `stream` once the call's momentum
+ * list has been seen (its device copy is cached with the phase tables). The paper
+ * projects directly (it uses at most 93 momenta). */
 typedef enum { LHC_PROJ_AUTO = 0, LHC_PROJ_GEMM = 1, LHC_PROJ_DFT = 2 } lhc_projection;
 int lhc_set_projection(lhc_ctx ctx, int mode);
 

@@ -115,6 +115,39 @@ bool use_fft(lhc_ctx ctx, int prec, int V3, int nq) {
 
 namespace {
 
+// The device copies of a call's momentum list and of the L-th roots of unity (rounded
+// once from FP64 to T), cached with the phase tables per (L, momentum list, precision).
+// Built with synchronous copies on first use; later calls with the same list copy
+// nothing from the host, so they stay asynchronous and can be captured in a graph.
+template <typename T>
+int get_dft_table(lhc_ctx ctx, int L, const int *k, int nq, const int **kd, const T **roots) {
+  const PhaseKey key{L, nq, 0, sizeof(T) == sizeof(double2) ? 4 : 3, 0, 0, 0, hash_k(k, nq)};
+  const size_t off_roots = (12 * (size_t)nq + 255) & ~(size_t)255;
+  const PhaseEntry *hit = phase_take(ctx, key);
+  if (!hit) {
+    PhaseEntry e;
+    LHC_TRY(dev_alloc(ctx, e.buf, off_roots + (size_t)L * sizeof(T)));
+    std::vector<T> hroots(L);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int m = 0; m < L; ++m)
+      hroots[m] = T{static_cast<decltype(T::x)>(std::cos(two_pi * m / L)),
+                    static_cast<decltype(T::x)>(std::sin(two_pi * m / L))};
+    char *base = static_cast<char *>(e.buf.p);
+    cudaError_t c = cudaMemcpy(base, k, 12 * (size_t)nq, cudaMemcpyHostToDevice);
+    if (c == cudaSuccess) c = cudaMemcpy(base + off_roots, hroots.data(), (size_t)L * sizeof(T), cudaMemcpyHostToDevice);
+    if (c != cudaSuccess) {
+      dev_free(ctx, e.buf);
+      set_error("DFT table upload: %s", cudaGetErrorString(c));
+      return LHC_ECUDA;
+    }
+    phase_insert(ctx, key, e);
+    hit = phase_take(ctx, key);
+  }
+  *kd = static_cast<const int *>(hit->buf.p);
+  *roots = reinterpret_cast<const T *>(static_cast<const char *>(hit->buf.p) + off_roots);
+  return LHC_OK;
+}
+
 template <typename T>
 int run_fft_t(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int nq, const int r[4], int sign,
               cudaStream_t st) {
@@ -124,21 +157,11 @@ int run_fft_t(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int nq, c
   // noises per chunk: the values of a whole slice for that many noises within 2 GiB
   const size_t per_noise = (size_t)V3 * cols * sizeof(T);
   const int nch = (int)std::max<size_t>(1, std::min<size_t>(j0.n_r, ((size_t)2 << 30) / per_noise));
-  const size_t ubytes = (size_t)nch * per_noise;
-  const size_t off_k = (ubytes + 255) & ~(size_t)255, off_roots = (off_k + 12 * (size_t)nq + 255) & ~(size_t)255;
-  LHC_TRY(ensure(ctx, ctx->ws, off_roots + (size_t)L * sizeof(T)));
-  char *ws = static_cast<char *>(ctx->ws.p);
-  T *U = reinterpret_cast<T *>(ws);
-  int *kd = reinterpret_cast<int *>(ws + off_k);
-  T *roots = reinterpret_cast<T *>(ws + off_roots);
-  std::vector<T> hroots(L);
-  const double two_pi = 6.283185307179586476925286766559;
-  for (int m = 0; m < L; ++m)   // the roots rounded once from FP64
-    hroots[m] = T{static_cast<decltype(T::x)>(std::cos(two_pi * m / L)), static_cast<decltype(T::x)>(std::sin(two_pi * m / L))};
-  LHC_CHECK_CUDA(cudaMemcpyAsync(kd, k, 12 * (size_t)nq, cudaMemcpyHostToDevice, st));
-  LHC_CHECK_CUDA(cudaMemcpyAsync(roots, hroots.data(), (size_t)L * sizeof(T), cudaMemcpyHostToDevice, st));
-  // the host arrays must outlive the copies
-  LHC_CHECK_CUDA(cudaStreamSynchronize(st));
+  const int *kd = nullptr;
+  const T *roots = nullptr;
+  LHC_TRY(get_dft_table(ctx, L, k, nq, &kd, &roots));   // before the workspace: it may allocate
+  LHC_TRY(ensure(ctx, ctx->ws, (size_t)nch * per_noise));
+  T *U = static_cast<T *>(ctx->ws.p);
   const int rx = ((r[0] % L) + L) % L, ry = ((r[1] % L) + L) % L, rz = ((r[2] % L) + L) % L;
   const size_t smem = ((size_t)L * kDftCols + L) * sizeof(T);
   if (smem > 48 * 1024)

@@ -964,12 +964,9 @@ static int get_phase_cs(lhc_ctx ctx, int L, const int *k, int nq, const int r[4]
   const size_t tbytes = (size_t)nrc * nkb * 2 * 2 * NH * 32;
   // rmap: first[nrep + 1] followed by q_list[nq]
   const size_t off_map = (tbytes + 255) & ~(size_t)255;
-  auto it = ctx->phases.find(key);
-  if (it != ctx->phases.end()) {
-    ctx->phase_lru.remove(key);
-    ctx->phase_lru.push_front(key);
-    *table = static_cast<const __half *>(it->second.buf.p);
-    *rmap = reinterpret_cast<const int *>(static_cast<const char *>(it->second.buf.p) + off_map);
+  if (const PhaseEntry *hit = phase_take(ctx, key)) {
+    *table = static_cast<const __half *>(hit->buf.p);
+    *rmap = reinterpret_cast<const int *>(static_cast<const char *>(hit->buf.p) + off_map);
     return LHC_OK;
   }
   const size_t off_k = (off_map + sizeof(int) * (size_t)(nrep + 1 + nq) + 255) & ~(size_t)255;
@@ -992,8 +989,7 @@ static int get_phase_cs(lhc_ctx ctx, int L, const int *k, int nq, const int r[4]
   note_launch();
   LHC_CHECK_CUDA(cudaGetLastError());
   e.nq_pad = nrc * NH;
-  ctx->phases[key] = e;
-  ctx->phase_lru.push_front(key);
+  phase_insert(ctx, key, e);
   *table = reinterpret_cast<const __half *>(base);
   *rmap = reinterpret_cast<const int *>(base + off_map);
   return LHC_OK;

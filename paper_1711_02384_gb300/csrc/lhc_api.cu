@@ -58,23 +58,44 @@ int g5mask_of(const lhc_ctx ctx) {
   return m;
 }
 
-static void evict_one_phase(lhc_ctx ctx) {
-  if (ctx->phase_lru.empty()) return;
-  PhaseKey key = ctx->phase_lru.back();
-  ctx->phase_lru.pop_back();
-  auto it = ctx->phases.find(key);
-  if (it != ctx->phases.end()) {
-    cudaDeviceSynchronize();
-    dev_free(ctx, it->second.buf);
-    ctx->phases.erase(it);
+// Frees the least recently used phase table that the current call has not taken; false
+// when there is none.
+static bool evict_one_phase(lhc_ctx ctx) {
+  for (auto k = ctx->phase_lru.rbegin(); k != ctx->phase_lru.rend(); ++k) {
+    auto it = ctx->phases.find(*k);
+    if (it != ctx->phases.end() && it->second.used_in == ctx->call_seq) continue;
+    if (it != ctx->phases.end()) {
+      cudaDeviceSynchronize();
+      dev_free(ctx, it->second.buf);
+      ctx->phases.erase(it);
+    }
+    ctx->phase_lru.erase(std::next(k).base());
+    return true;
   }
+  return false;
+}
+
+const PhaseEntry *phase_take(lhc_ctx ctx, const PhaseKey &key) {
+  auto it = ctx->phases.find(key);
+  if (it == ctx->phases.end()) return nullptr;
+  ctx->phase_lru.remove(key);
+  ctx->phase_lru.push_front(key);
+  it->second.used_in = ctx->call_seq;
+  return &it->second;
+}
+
+void phase_insert(lhc_ctx ctx, const PhaseKey &key, const PhaseEntry &e) {
+  PhaseEntry &d = ctx->phases[key];
+  d = e;
+  d.used_in = ctx->call_seq;
+  ctx->phase_lru.push_front(key);
 }
 
 int dev_alloc(lhc_ctx ctx, DevBuf &b, size_t bytes) {
   b = DevBuf{};
   if (bytes == 0) return LHC_OK;
-  while (ctx->budget && ctx->used + bytes > ctx->budget && !ctx->phase_lru.empty())
-    evict_one_phase(ctx);
+  while (ctx->budget && ctx->used + bytes > ctx->budget && evict_one_phase(ctx)) {
+  }
   if (ctx->budget && ctx->used + bytes > ctx->budget)
     return fail(LHC_EBUDGET, "allocation of %zu bytes exceeds the HBM budget (%zu of %zu in use)",
                 bytes, ctx->used, ctx->budget);
@@ -108,11 +129,8 @@ int get_phase_f64(lhc_ctx ctx, int L, const int *k, int nq, const int r[4], int 
                   cudaStream_t st, const double2 **out) {
   PhaseKey key{L, nq, sign, 0, ((r[0] % L) + L) % L, ((r[1] % L) + L) % L, ((r[2] % L) + L) % L,
                 hash_k(k, nq)};
-  auto it = ctx->phases.find(key);
-  if (it != ctx->phases.end()) {
-    ctx->phase_lru.remove(key);
-    ctx->phase_lru.push_front(key);
-    *out = static_cast<const double2 *>(it->second.buf.p);
+  if (const PhaseEntry *hit = phase_take(ctx, key)) {
+    *out = static_cast<const double2 *>(hit->buf.p);
     return LHC_OK;
   }
   size_t V3 = (size_t)L * L * L;
@@ -134,8 +152,7 @@ int get_phase_f64(lhc_ctx ctx, int L, const int *k, int nq, const int r[4], int 
                    L, key.rx, key.ry, key.rz, sign, reinterpret_cast<const double2 *>(base + off_roots),
                    st);
   LHC_CHECK_CUDA(cudaGetLastError());
-  ctx->phases[key] = e;
-  ctx->phase_lru.push_front(key);
+  phase_insert(ctx, key, e);
   *out = reinterpret_cast<const double2 *>(base);
   return LHC_OK;
 }
@@ -236,7 +253,8 @@ static int stage_grow(lhc_ctx ctx, size_t bytes) {
   const size_t want = bytes + bytes / 4;
   const size_t held = ctx->stage_bytes * (size_t)lhc_ctx_s::kStageSlots;
   const size_t need = want * (size_t)lhc_ctx_s::kStageSlots;
-  while (ctx->budget && ctx->used - held + need > ctx->budget && !ctx->phase_lru.empty()) evict_one_phase(ctx);
+  while (ctx->budget && ctx->used - held + need > ctx->budget && evict_one_phase(ctx)) {
+  }
   if (ctx->budget && ctx->used - held + need > ctx->budget)
     return fail(LHC_EBUDGET, "%d staging slots of %zu bytes exceed the HBM budget (%zu of %zu in use)",
                 lhc_ctx_s::kStageSlots, want, ctx->used - held, ctx->budget);
@@ -362,6 +380,7 @@ static void stage_destroy(lhc_ctx ctx) {
 static int begin_call(lhc_ctx ctx, cudaStream_t st) {
   LHC_CHECK_CUDA(cudaSetDevice(ctx->device));
   std::lock_guard<std::mutex> g(g_sync_mu);
+  ++ctx->call_seq;   // the caller holds ctx->mu
   CtxSync &s = g_sync[ctx];
   if (!s.ev) LHC_CHECK_CUDA(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
   if (s.used && s.last != st) LHC_CHECK_CUDA(cudaStreamWaitEvent(st, s.ev, 0));

@@ -106,6 +106,7 @@ struct ProfScope {
 struct PhaseEntry {
   DevBuf buf;
   int nq_pad = 0;
+  unsigned long long used_in = 0;   // the last call (lhc_ctx_s::call_seq) that took this table
 };
 
 }  // namespace lhc
@@ -142,6 +143,7 @@ struct lhc_ctx_s {
   std::vector<cudaEvent_t> event_pool;
   std::map<lhc::PhaseKey, lhc::PhaseEntry> phases;
   std::list<lhc::PhaseKey> phase_lru;     // front = most recent
+  unsigned long long call_seq = 0;        // counts calls; the current call's tables are never evicted
   int num_sms = 0;
   bool prof_on = false;
   int *dev_err = nullptr;                 // sticky device error word (bounded waits that gave up)
@@ -160,7 +162,11 @@ int ensure(lhc_ctx ctx, DevBuf &b, size_t bytes);   // grows b (synchronizes the
 int g5mask_of(const lhc_ctx ctx);
 uint64_t hash_k(const int *k, int nq);
 
-// phase tables
+// phase tables.  phase_take() marks a cached entry as used by the current call (LRU
+// front); phase_insert() adds a new one the same way.  Eviction under the HBM budget skips
+// every entry the current call has taken: its pointers are already in the call's launches.
+const PhaseEntry *phase_take(lhc_ctx ctx, const PhaseKey &key);
+void phase_insert(lhc_ctx ctx, const PhaseKey &key, const PhaseEntry &e);
 // fmt 0: complex128 [nq][V3], P[q][x] = exp(sign*2*pi*i*((k.(x-r)) mod L)/L)
 int get_phase_f64(lhc_ctx ctx, int L, const int *k, int nq, const int r[4], int sign,
                   cudaStream_t st, const double2 **out);
