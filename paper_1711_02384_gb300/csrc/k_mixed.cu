@@ -184,6 +184,22 @@ __device__ __forceinline__ void add2(float &a0, float &a1, float b0, float b1) {
 }
 
 // fp16 hi/lo split of two floats, packed as half2 pairs
+// Packed FP32 pairs for fma.rn.f32x2: (lo, hi) in one 64-bit register pair.
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 unpack2(unsigned long long v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+// d = a * b + d elementwise on the two FP32 lanes, each rounded once
+__device__ __forceinline__ void fma2(unsigned long long &d, unsigned long long a, unsigned long long b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
+
 __device__ __forceinline__ void split2(float v0, float v1, uint32_t &hi, uint32_t &lo) {
   __half2 h = __floats2half2_rn(v0, v1);
   float2 hf = __half22float2(h);
@@ -489,86 +505,77 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
         // k-step kstep = NPK it + kofs uses input stage and A stage kstep % 6 = kofs + 3 (it & 1),
         // in round kstep / 6 = it / 2
         const int si = kofs + NPK * (it & 1), ui = it >> 1;
-        // The first warp of the group waits for each barrier; the four warps block on the
-        // group's named barrier and follow its verdict together, so a wait that gives up (a
-        // loader stopped, or the limit ran out) ends the loop of all four at once.
-        volatile int *vin = verdict + 2 + 4 * kofs, *vempty = vin + 2;
-        if (wq == 0 && lane == 0) vin[it & 1] = tc::mbar_wait(&inFull[si], ui & 1, err, 6) ? 1 : 0;
+        // The first warp of the group waits for the input stage and, after the first round,
+        // for the MMA to be done with the A stage (its k-step NSTAGE back); the four warps
+        // block on the group's named barrier and follow its verdict together, so a wait
+        // that gives up (a loader stopped, or the limit ran out) ends the loop of all four
+        // at once.
+        volatile int *vin = verdict + 2 + 4 * kofs;
+        const int pr = si >> 1;
+        if (wq == 0 && lane == 0)
+          vin[it & 1] = (tc::mbar_wait(&inFull[si], ui & 1, err, 6) &&
+                         (ui == 0 || tc::mbar_wait(&empty[pr], (ui - 1) & 1, err, 8)))
+                            ? 1
+                            : 0;
         tc::named_bar_sync(2 + kofs, 128);
         if (!vin[it & 1]) break;
         const float2 *Ms = reinterpret_cast<const float2 *>(stM(si));
         const float2 *Vs = reinterpret_cast<const float2 *>(stV(si)) + x * 12;
-        float2 acc[2][8];
-  #pragma unroll
-        for (int jx = 0; jx < 2; ++jx)
-  #pragma unroll
-          for (int iv = 0; iv < 8; ++iv) acc[jx][iv] = make_float2(0.f, 0.f);
-        // the matrix values of both columns and all three colours (scaled for the split
-        // unless the data is unit-scale), then per (noise, spin) the vector's three colours,
-        // contiguous in the box, with one 16-byte and one 8-byte load; each accumulator
-        // still sums the colours in the order 0, 1, 2
-        float2 sv[3][2];
-  #pragma unroll
-        for (int c = 0; c < 3; ++c)
-  #pragma unroll
-          for (int jx = 0; jx < 2; ++jx) {
-            const float2 m = Ms[mo[jx] + c * (MODE == 2 ? 16 : 12)];
-            if constexpr (decltype(scaled)::value)
-              sv[c][jx] = make_float2(m.x * sc, m.y * sc);   // the split scale, folded into the matrix value
-            else
-              sv[c][jx] = m;
-          }
-  #pragma unroll
-        for (int iv = 0; iv < 8; ++iv) {
-          const float2 *pb = Vs + (iv >> 2) * 16 * 12 + (iv & 3) * 3;   // noise iv/4, spin iv%4
-          float2 pv[3];
-          if ((iv & 1) == 0) {   // colours 0, 1 start on a 16-byte boundary
-            const float4 q = *reinterpret_cast<const float4 *>(pb);
-            pv[0] = make_float2(q.x, q.y);
-            pv[1] = make_float2(q.z, q.w);
-            pv[2] = pb[2];
-          } else {               // colours 1, 2 do
-            pv[0] = pb[0];
-            const float4 q = *reinterpret_cast<const float4 *>(pb + 1);
-            pv[1] = make_float2(q.x, q.y);
-            pv[2] = make_float2(q.z, q.w);
-          }
-  #pragma unroll
-          for (int c = 0; c < 3; ++c)
-  #pragma unroll
-            for (int jx = 0; jx < 2; ++jx) {
-              float2 &a = acc[jx][iv];
-              const float2 p = pv[c], m = sv[c][jx];
-              if (MODE == 0) {          // conj(psi) * S
-                a.x = fmaf(p.x, m.x, fmaf(p.y, m.y, a.x));
-                a.y = fmaf(p.x, m.y, fmaf(-p.y, m.x, a.y));
-              } else if (MODE == 1) {   // eta * conj(S)
-                a.x = fmaf(p.x, m.x, fmaf(p.y, m.y, a.x));
-                a.y = fmaf(p.y, m.x, fmaf(-p.x, m.y, a.y));
-              } else {                  // eta * D
-                a.x = fmaf(p.x, m.x, fmaf(-p.y, m.y, a.x));
-                a.y = fmaf(p.x, m.y, fmaf(p.y, m.x, a.y));
-              }
-            }
-        }
-        // the input stage is read: hand it back to the input loader
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&inEmpty[si]);
-        const int s = si, pr = s >> 1, u = ui;
-        if (u > 0) {
-          // the MMA must be done with this A stage (from NSTAGE k-steps ago)
-          if (wq == 0 && lane == 0) vempty[it & 1] = tc::mbar_wait(&empty[pr], (u - 1) & 1, err, 8) ? 1 : 0;
-          tc::named_bar_sync(2 + kofs, 128);
-          if (!vempty[it & 1]) break;
-        }
-        char *a_st = stA(s);
+        char *a_st = stA(si);
+        // One column at a time.  The colour sum of each (noise, spin) row runs on packed
+        // FP32 pairs: with the vector value p in its natural pair (p.x, p.y) and the
+        // matrix value m,
+        //   A += p * (m.x, ±m.x),  B += p * (±m.y, ±m.y),  Re = A.x + B.y,  Im = A.y + B.x.
+        // The one minus sign sits in A.y for conj(psi) S, in B.x for eta conj(S) and in
+        // B.y for eta D.  The matrix pairs are formed once per column and k-step (and carry
+        // the split scale); each accumulator sums the colours in the order 0, 1, 2.
   #pragma unroll
         for (int jx = 0; jx < 2; ++jx) {
+          unsigned long long ma[3], mb[3];
+  #pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            float2 m = Ms[mo[jx] + c * (MODE == 2 ? 16 : 12)];
+            if constexpr (decltype(scaled)::value) m = make_float2(m.x * sc, m.y * sc);
+            ma[c] = pack2(m.x, MODE == 0 ? -m.x : m.x);
+            mb[c] = MODE == 1 ? pack2(-m.y, m.y) : pack2(m.y, MODE == 2 ? -m.y : m.y);
+          }
+          unsigned long long A[8], B[8];
+  #pragma unroll
+          for (int iv = 0; iv < 8; ++iv) A[iv] = B[iv] = 0ull;
+  #pragma unroll
+          for (int iv = 0; iv < 8; ++iv) {
+            // noise iv / 4, spin iv % 4: the three colours with one 16-byte and one 8-byte load
+            const unsigned long long *pb =
+                reinterpret_cast<const unsigned long long *>(Vs + (iv >> 2) * 16 * 12 + (iv & 3) * 3);
+            unsigned long long pv[3];
+            if ((iv & 1) == 0) {   // colours 0, 1 start on a 16-byte boundary
+              const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(pb);
+              pv[0] = q.x;
+              pv[1] = q.y;
+              pv[2] = pb[2];
+            } else {               // colours 1, 2 do
+              pv[0] = pb[0];
+              const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(pb + 1);
+              pv[1] = q.x;
+              pv[2] = q.y;
+            }
+  #pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              fma2(A[iv], pv[c], ma[c]);
+              fma2(B[iv], pv[c], mb[c]);
+            }
+          }
+          if (jx == 1) {   // the input stage is read: hand it back to the input loader
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&inEmpty[si]);
+          }
           uint32_t rh[4], rl[4], ih[4], il[4];
   #pragma unroll
-          for (int pr = 0; pr < 4; ++pr) {
-            split2(acc[jx][2 * pr].x, acc[jx][2 * pr + 1].x, rh[pr], rl[pr]);
-            split2(acc[jx][2 * pr].y, acc[jx][2 * pr + 1].y, ih[pr], il[pr]);
+          for (int q = 0; q < 4; ++q) {
+            const float2 a0 = unpack2(A[2 * q]), b0 = unpack2(B[2 * q]);
+            const float2 a1 = unpack2(A[2 * q + 1]), b1 = unpack2(B[2 * q + 1]);
+            split2(a0.x + b0.y, a1.x + b1.y, rh[q], rl[q]);
+            split2(a0.y + b0.x, a1.y + b1.x, ih[q], il[q]);
           }
           // row group s = sp + 8 jx, its 8 rows (noise, spin) contiguous at k = site x
           const uint32_t off = (uint32_t)((sp + 8 * jx) * 144 + (x >> 3) * 2304 + (x & 7) * 16);
