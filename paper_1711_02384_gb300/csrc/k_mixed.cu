@@ -183,7 +183,6 @@ __device__ __forceinline__ void add2(float &a0, float &a1, float b0, float b1) {
   asm("mov.b64 {%0, %1}, %2;" : "=f"(a0), "=f"(a1) : "l"(a));
 }
 
-// fp16 hi/lo split of two floats, packed as half2 pairs
 // Packed FP32 pairs for fma.rn.f32x2: (lo, hi) in one 64-bit register pair.
 __device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
   unsigned long long r;
@@ -200,6 +199,7 @@ __device__ __forceinline__ void fma2(unsigned long long &d, unsigned long long a
   asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
 }
 
+// fp16 hi/lo split of two floats, packed as half2 pairs
 __device__ __forceinline__ void split2(float v0, float v1, uint32_t &hi, uint32_t &lo) {
   __half2 h = __floats2half2_rn(v0, v1);
   float2 hf = __half22float2(h);
