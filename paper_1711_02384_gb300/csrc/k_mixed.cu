@@ -249,8 +249,9 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
            *tfull = bars + 2 * NPAIR + 2 * NIN, *tempty = tfull + 2, *done = tfull + 4;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
   // Verdicts of waits that one leader thread performs for a group of warps, which block on
-  // a named barrier meanwhile: [0, 2) drain (by chunk parity), then per producer group
-  // (k-step offset) two slots for the input wait and two for the A-stage wait.
+  // a named barrier meanwhile: [0, 2) drain (by chunk parity), then four slots per
+  // producer group (k-step offset), of which the first two hold the verdict of the
+  // joint input and A-stage wait (by iteration parity).
   volatile int *verdict = reinterpret_cast<volatile int *>(tmem_slot + 1);
   auto stA = [&](int s) { return smem + s * St::ab; };
   auto stB = [&](int s) { return smem + s * St::ab + St::A; };
