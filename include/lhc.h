@@ -198,6 +198,8 @@ int lhc_selftest_flag(lhc_ctx ctx, int limit_us, void *stream);
  * (lhc_create) covers the resident propagators, the workspace every slot holds and the
  * job's additional workspace (an upper bound from its shapes); jobs that can never fit are
  * refused at submission with LHC_EBUDGET.  Admission is first-fit in submission order.
+ * Slots project in the automatic mode (lhc_set_projection): a job with nq >= L^3 / 2
+ * takes the all-momenta transform, and its bound is that of the transform.
  * Results do not depend on what else runs: the kernels sum in a fixed order.  Timestamps
  * (steady clock, seconds) give submit -> start -> poll-visible completion latencies. */
 typedef enum { LHC_JOB_INSERTION = 0, LHC_JOB_SPECTATOR = 1, LHC_JOB_THREEPT = 2 } lhc_job_type;

@@ -113,6 +113,16 @@ bool use_fft(lhc_ctx ctx, int prec, int V3, int nq) {
   return 2 * (long long)nq >= V3;
 }
 
+// Upper bound of the device memory one all-momenta call allocates: the workspace of a
+// noise chunk (the values of a whole slice for as many noises as fit 2 GiB, at least one)
+// and the cached momentum list with its roots.
+size_t fft_call_bytes(Part part, int prec, int L, int n_r, int nq) {
+  const size_t V3 = (size_t)L * L * L, cols = part == PART_SPEC_BARYON ? kBarCols : 192;
+  const size_t per_noise = V3 * cols * (prec == LHC_MIXED ? sizeof(float2) : sizeof(double2));
+  const size_t nch = std::max<size_t>(1, std::min<size_t>(n_r, ((size_t)2 << 30) / per_noise));
+  return nch * per_noise + 12 * (size_t)nq + (size_t)L * sizeof(double2) + 2 * 256;
+}
+
 namespace {
 
 // The device copies of a call's momentum list and of the L-th roots of unity (rounded

@@ -180,6 +180,7 @@ int contract_f32(const SliceJob &j, int s0, int ns, float2 *U, cudaStream_t st);
 
 // all-momenta mode: FP64 contraction, three line DFTs over the slice, gather (k_fft.cu)
 bool use_fft(lhc_ctx ctx, int prec, int V3, int nq);
+size_t fft_call_bytes(Part part, int prec, int L, int n_r, int nq);   // its allocation bound
 int run_part_fft(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int nq, const int r[4], int sign,
                  int prec, cudaStream_t st);
 

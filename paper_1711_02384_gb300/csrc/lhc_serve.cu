@@ -95,15 +95,19 @@ size_t job_need(const lhc_job &j, const Prop &p) {
   const int V3 = p.lat.L * p.lat.L * p.lat.L;
   size_t ins = 0, spec = 0;
   const bool fp64 = j.prec == LHC_FP64;
+  // a slot's context projects in the automatic mode: the transform for half the momenta or more
+  const bool dft = 2 * (long long)j.nq >= V3;
   if (j.type != LHC_JOB_SPECTATOR) {
     int nt = j.t_hi - j.t_lo + 1;
-    ins = fp64 ? ((size_t)1 << 30) + (size_t)j.nq * V3 * 16 + 4096
-               : lhc::mixed_call_bytes(lhc::PART_INS, p.lat.dtype, V3, j.n_r, nt, j.nq);
+    ins = dft    ? lhc::fft_call_bytes(lhc::PART_INS, j.prec, p.lat.L, j.n_r, j.nq)
+          : fp64 ? ((size_t)1 << 30) + (size_t)j.nq * V3 * 16 + 4096
+                 : lhc::mixed_call_bytes(lhc::PART_INS, p.lat.dtype, V3, j.n_r, nt, j.nq);
   }
   if (j.type != LHC_JOB_INSERTION) {
     auto part = j.kind == LHC_BARYON ? lhc::PART_SPEC_BARYON : lhc::PART_SPEC_MESON;
-    spec = fp64 ? ((size_t)1 << 30) + (size_t)j.nq * V3 * 16 + 4096
-                : lhc::mixed_call_bytes(part, p.lat.dtype, V3, j.n_r, 1, j.nq);
+    spec = dft    ? lhc::fft_call_bytes(part, j.prec, p.lat.L, j.n_r, j.nq)
+           : fp64 ? ((size_t)1 << 30) + (size_t)j.nq * V3 * 16 + 4096
+                  : lhc::mixed_call_bytes(part, p.lat.dtype, V3, j.n_r, 1, j.nq);
   }
   // one workspace (the larger call) plus both phase tables, with 25 % growth slack
   return (size_t)((std::max(ins, spec) + std::min(ins, spec) / 4) * 1.25);
