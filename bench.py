@@ -92,18 +92,27 @@ class Clocks:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device_index):
+    def __init__(self, device_index, window="timed steps"):
         self.idx = device_index
+        self.window = window
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.p = None
 
-    def start(self):
+    def start(self, ready_s=2.0):
+        """Starts sampling every 100 ms and waits (at most ready_s) for the first sample,
+        so that the steps that follow are covered from their start."""
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+            return
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < ready_s and self.p.poll() is None:
+            if os.path.getsize(self.f.name) > 0:
+                break
+            time.sleep(0.01)
 
     def stop(self):
         if self.p is None:
@@ -128,7 +137,7 @@ class Clocks:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(rows)}
+                "reasons": sorted(reasons), "samples": len(rows), "window": self.window}
 
 
 # --------------------------------------------------------------------------- replicas
@@ -262,11 +271,13 @@ def main():
     # launch shapes are tuned on one stream first: candidates timed next to other work
     # would be picked for the wrong conditions
     step_on([ctx], [st])
+    # clocks are sampled from the warm-up on: a timed region of a few tens of ms is
+    # shorter than the sampling interval
+    clocks = Clocks(local, window="warm-up and timed steps")
+    clocks.start()
     for _ in range(args.warmup):
         step()
     barrier()
-    clocks = Clocks(local)
-    clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     n_launch0 = lhc.launch_count()
     e0.record(st)
