@@ -286,8 +286,9 @@ class Context:
         return outs
 
     def set_projection(self, mode: str):
-        """Momentum projection: "auto" (a DFT over the slice when nq >= L^3 / 2), "gemm"
-        (always the direct projection) or "dft" (always the all-momenta transform)."""
+        """Momentum projection of single calls: "auto" (a DFT over the slice when
+        nq >= L^3 / 2), "gemm" (always the direct projection) or "dft" (always the
+        all-momenta transform).  batch() always projects on the tensor cores."""
         _check(lib().lhc_set_projection(self._h, PROJECTIONS[mode]))
 
     def set_tuning(self, enable: bool, path=None):
