@@ -371,7 +371,9 @@ int lhc_batch(lhc_ctx ctx, const lhc_call *calls, int ncalls, void *stream);
  * output is complex128 either way.
  * LHC_PROJ_AUTO (the default) uses it for calls with nq >= L^3 / 2, where it is far
  * cheaper than the direct projection in either precision. LHC_PROJ_GEMM never uses
- * the transform, LHC_PROJ_DFT always. Asynchronous on `stream` once the call's momentum
+ * the transform, LHC_PROJ_DFT always. The mode governs single calls (and the job
+ * server's slots use LHC_PROJ_AUTO); lhc_batch always projects on the tensor cores.
+ * Asynchronous on `stream` once the call's momentum
  * list has been seen (its device copy is cached with the phase tables). The paper
  * projects directly (it uses at most 93 momenta). */
 typedef enum { LHC_PROJ_AUTO = 0, LHC_PROJ_GEMM = 1, LHC_PROJ_DFT = 2 } lhc_projection;
