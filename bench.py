@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="leave out the plain FP64 GPU comparator")
+    ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the FP64 comparator")
+    ap.add_argument("--serve-jobs", type=int, default=100,
+                    help="jobs of the served stream reported beside the headline (0 leaves it out)")
     ap.add_argument("--streams", type=int, default=3,
                     help="contexts and streams the step's three t_f sets are spread over (their kernels overlap)")
     ap.add_argument("--no-tune", action="store_true",
@@ -87,23 +91,41 @@ def gamma_sets():
 
 # --------------------------------------------------------------------------- clocks
 
+def nvsmi_id(local):
+    """The id under which nvidia-smi knows CUDA device `local`: its PCI bus id (or, where
+    torch does not report one, its UUID).  nvidia-smi ignores CUDA_VISIBLE_DEVICES, so the
+    CUDA ordinal can name another GPU of the machine than the one being timed."""
+    import torch
+    p = torch.cuda.get_device_properties(local)
+    bus, slot = getattr(p, "pci_bus_id", None), getattr(p, "pci_device_id", None)
+    if bus is not None and slot is not None:
+        return f"{int(getattr(p, 'pci_domain_id', 0) or 0):08X}:{int(bus):02X}:{int(slot):02X}.0"
+    u = getattr(p, "uuid", None)
+    if u is not None:
+        u = str(u)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    return str(local)
+
+
 class Clocks:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 25
 
-    def __init__(self, device_index, window="timed steps"):
-        self.idx = device_index
+    def __init__(self, gpu_id, window="timed steps"):
+        """gpu_id: nvidia-smi's id of the timed GPU (nvsmi_id)."""
+        self.idx = gpu_id
         self.window = window
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.p = None
 
     def start(self, ready_s=2.0):
-        """Starts sampling every 100 ms and waits (at most ready_s) for the first sample,
-        so that the steps that follow are covered from their start."""
+        """Starts sampling every INTERVAL_MS and waits (at most ready_s) for the first
+        sample, so that the steps that follow are covered from their start."""
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                       "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -116,7 +138,7 @@ class Clocks:
 
     def stop(self):
         if self.p is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "gpu_id": self.idx}
         self.p.terminate()
         self.p.wait()
         self.f.flush()
@@ -137,7 +159,8 @@ class Clocks:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(rows), "window": self.window}
+                "reasons": sorted(reasons), "samples": len(rows), "window": self.window,
+                "interval_ms": self.INTERVAL_MS, "gpu_id": self.idx}
 
 
 # --------------------------------------------------------------------------- replicas
@@ -160,18 +183,42 @@ def job_value(units_per_step, steps, world, ms):
 
 # --------------------------------------------------------------------------- reference arm / cpu baseline
 
+SAMPLE = ("insertion slice 5 + spectator slice 10 of the t_f=10 set (16 noises, 93 momenta) and the "
+          "combine of that slice for the 16 Gamma structures")
+
+
 def oracle_sample(S, psis, etas, k):
-    """The FP64 oracle as it stands on a bounded sample of the workload: the
-    insertion on slice 5 and the spectator on the sink slice, for t_f = 10 (all
-    16 noises, all 93 momenta).  Returns (units, seconds)."""
+    """The FP64 oracle as it stands on a bounded sample of the workload: the insertion
+    on slice 5 and the spectator on the sink slice, for t_f = 10 (all 16 noises, all 93
+    momenta), and the combine of that slice for the step's 16 Gamma structures.
+    Returns (units, seconds, (insertion, spectator, correlators))."""
     from oracle import contractions as OC
     g5 = np.diag([1.0, 1.0, -1.0, -1.0]).astype(complex)
     r3 = np.zeros(3, dtype=int)
+    g_snk, g_ins, g_src = gamma_sets()
     t0 = time.perf_counter()
-    OC.insertion(S[5:6], psis[1][:, 5:6], g5, r3, k, L)
-    OC.spectator_meson(S[TFS[1]], etas[1], g5, r3, k, L)
+    ins = OC.insertion(S[5:6], psis[1][:, 5:6], g5, r3, k, L)
+    spec = OC.spectator_meson(S[TFS[1]], etas[1], g5, r3, k, L)
+    corr = OC.combine_meson(spec, ins[0], g_snk, g_ins, g_src)
     dt = time.perf_counter() - t0
-    return 2 * L ** 3 * N_R * len(k), dt
+    return 2 * L ** 3 * N_R * len(k), dt, (ins[0], spec, corr)
+
+
+def parity_errors(ins, spec, corr, ref):
+    """Errors of the GPU outputs of the sampled slices against the oracle's, per
+    correlator: for the insertion and spectator parts the largest normwise error of a
+    block (one momentum over all open components and noises); for the combine the
+    largest |C_gpu - C_ref| of a correlator over the largest |C_ref| of its row (the same
+    Gamma structure and sink momentum, all insertion momenta)."""
+    ri, rs, rc = ref
+
+    def blocks(got, want):
+        got, want = got.reshape(want.shape[0], -1), want.reshape(want.shape[0], -1)
+        return float(np.max(np.linalg.norm(got - want, axis=1) / np.linalg.norm(want, axis=1)))
+
+    row = np.max(np.abs(rc), axis=-1, keepdims=True)
+    return {"insertion": blocks(ins, ri), "spectator": blocks(spec, rs),
+            "combine": float(np.max(np.abs(corr - rc) / row))}
 
 
 def run_reference(args):
@@ -185,12 +232,12 @@ def run_reference(args):
         oracle_sample(S, psis, etas, k)
     tot_u, tot_t = 0, 0.0
     for _ in range(args.steps):
-        u, t = oracle_sample(S, psis, etas, k)
+        u, t, _ = oracle_sample(S, psis, etas, k)
         tot_u += u
         tot_t += t
     v = tot_u / tot_t
     cores = os.cpu_count()
-    sample = "insertion slice 5 + spectator slice 10 of the t_f=10 set, 16 noises, 93 momenta, per step"
+    sample = SAMPLE + ", per step"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
@@ -271,9 +318,9 @@ def main():
     # launch shapes are tuned on one stream first: candidates timed next to other work
     # would be picked for the wrong conditions
     step_on([ctx], [st])
-    # clocks are sampled from the warm-up on: a timed region of a few tens of ms is
-    # shorter than the sampling interval
-    clocks = Clocks(local, window="warm-up and timed steps")
+    # clocks are sampled every 25 ms from the warm-up through the end-to-end steps: the
+    # timed region alone (20 steps, about 60 ms) would hold only a few samples
+    clocks = Clocks(nvsmi_id(local), window="warm-up, timed and end-to-end steps of the mixed path")
     clocks.start()
     for _ in range(args.warmup):
         step()
@@ -285,7 +332,6 @@ def main():
         step()
     e1.record(st)
     barrier()
-    clk = clocks.stop()
     for c in ctxs:   # a kernel that gave up a bounded wait raises here instead of giving a number
         c.sync()
     n_launches = lhc.launch_count() - n_launch0
@@ -324,6 +370,9 @@ def main():
         kms_i, kn_i, _ = ctx.profile_read(kid)
         if kn_i:
             kernels[name] = {"ms_per_step": kms_i, "launches_per_step": kn_i}
+    # the sampled slices' outputs of the path timed above, for the parity check against the
+    # oracle (the end-to-end leg below reuses the output buffers)
+    got = {args.prec: (outs_ins[1][5].cpu().numpy(), outs_spec[1].cpu().numpy(), outs_c[1][5].cpu().numpy())}
 
     # End to end, inputs on the host: every step uploads the propagator slices 0..12 once
     # (a plain device copy on a copy stream: the six calls of the step share them), passes
@@ -397,12 +446,56 @@ def main():
                           "solutions and noise as pinned host "
                           "buffers through the library; open-spin outputs and correlators read back"}
 
+    clk = clocks.stop()
+
+    # The plain FP64 GPU path on the same workload, one context on one stream (a step
+    # takes about a second): the comparator the mixed path is measured against.
+    fp64 = None
+    if args.prec == "mixed" and not args.no_fp64 and rank == 0:
+        def step64():
+            for j, tf in enumerate(TFS):
+                ctx.insertion(S, psis[j], 0, tf, r, k, prec="fp64", out=outs_ins[j], stream=st.cuda_stream)
+                ctx.spectator(S, etas[j], tf, r, k, prec="fp64", out=outs_spec[j], stream=st.cuda_stream)
+                ctx.combine(outs_spec[j], outs_ins[j], G[0], G[1], G[2], prec="fp64", out=outs_c[j],
+                            stream=st.cuda_stream)
+        step64()
+        torch.cuda.synchronize(dev)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(st)
+        for _ in range(args.fp64_steps):
+            step64()
+        f1.record(st)
+        torch.cuda.synchronize(dev)
+        ctx.sync()
+        ms64 = f0.elapsed_time(f1) / args.fp64_steps
+        fp64 = {"value": upstep / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64, "steps": args.fp64_steps,
+                "warmup": 1, "ratio_mixed_over_fp64": value / (upstep / (ms64 / 1e3)),
+                "path": "plain FP64 GPU path (FP64 contraction, FP64 projection, FP64 combine), one stream"}
+        got["fp64"] = (outs_ins[1][5].cpu().numpy(), outs_spec[1].cpu().numpy(), outs_c[1][5].cpu().numpy())
+
+    # A served stream of three-point jobs through the job server (resident propagators,
+    # continuous batching): latency percentiles beside the served throughput.
+    serve = None
+    if args.serve_jobs > 0 and rank == 0:
+        import bench_workloads
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(5001)
+        serve = bench_workloads.serve_stream(dev, gen, "mixed", njobs=args.serve_jobs)
+        serve["config"] = (f"{args.serve_jobs} Poisson-arriving meson 3pt jobs on resident complex64 propagators "
+                           "of 16^3x32, 24^3x48, 32^3x64, 48^3x96, N_r in {8,16,32}, |k|^2<=4..16, "
+                           "4 slots, 150 GB budget, arrivals at 0.7 x measured capacity")
+
+    # cpu_baseline: the FP64 oracle as it stands, timed on a bounded sample of the
+    # workload; its outputs are also the reference of the parity check of that sample.
     cpu = None
+    parity = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         from oracle.momenta import momenta
-        u, t = oracle_sample(S_h, psis_h, etas_h, momenta(N2MAX))
-        cpu = {"value": u / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": "insertion slice 5 + spectator slice 10 of the t_f=10 set, 16 noises, 93 momenta"}
+        u, t, ref = oracle_sample(S_h, psis_h, etas_h, momenta(N2MAX))
+        cpu = {"value": u / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": SAMPLE}
+        parity = {p: parity_errors(*g, ref) for p, g in got.items()}
+        parity["sample"] = SAMPLE
+        parity["tolerance"] = {"mixed": 1e-6, "fp64": 1e-12}
 
     if rank == 0:
         print(json.dumps({
@@ -419,7 +512,8 @@ def main():
                            f"part {r[0]} nt {r[4]}: NH {r[6]} x {r[5]} reps, {r[7]} splits"
                            for r in lhc.tuning_table() if r[2] == L ** 3 and r[3] == N_R)},
             "clocks": clk, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": n_launches, "kernels": kernels,
+            "gpu_launches": n_launches, "kernels": kernels, "fp64_gpu": fp64, "parity": parity,
+            "serve": serve,
         }))
     for c in ctxs:
         c.close()

@@ -60,7 +60,7 @@ def _timed(step, steps, warmup, dev, stream=None, ctx=None):
     for _ in range(warmup):
         step()
     torch.cuda.synchronize(dev)
-    clocks = B.Clocks(dev.index)
+    clocks = B.Clocks(B.nvsmi_id(dev.index))
     clocks.start()
     st = stream or torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -223,10 +223,18 @@ def run_batched(args, dev, g):
 
 # --------------------------------------------------------------------------- serve
 
-def run_serve(args, dev, g):
-    lat_shapes = [(16, 32), (24, 48), (32, 64), (48, 96)]
+def serve_stream(dev, g, prec, njobs=200, lat_shapes=((16, 32), (24, 48), (32, 64), (48, 96)),
+                 fp64_small=0, seed=5000):
+    """A Poisson stream of meson three-point jobs (spectator + insertion) through the job
+    server: resident complex64 propagators on every lattice of `lat_shapes`, N_r in
+    {8, 16, 32}, |k|^2 <= 4..16, t_f - t_0 in {8, 10, 12}, 4 slots, 150 GB budget.  The
+    capacity is measured first (all jobs submitted at once), then the jobs arrive at 0.7 x
+    capacity.  Returns the served throughput, the latency percentiles (submit to
+    poll-visible completion), the most jobs that ran at once (from the jobs' start and
+    done times), and with fp64_small > 0 the plain FP64 path one job at a time on that
+    many jobs of the two smaller lattices, beside the mixed path on the same jobs."""
     NRMAX = 32
-    ctx = lhc.Context(0, hbm_budget=150 << 30)
+    ctx = lhc.Context(dev.index, hbm_budget=150 << 30)
     ctx.serve_start(slots=4)
     lats = []
     for L, T in lat_shapes:
@@ -235,46 +243,43 @@ def run_serve(args, dev, g):
         lats.append(dict(L=L, T=T, V3=V3, S=S, h=ctx.prop_register(S),
                          psi=_rand((NRMAX, T, V3, 12), torch.complex64, dev, g),
                          eta=_rand((NRMAX, V3, 12), torch.complex64, dev, g)))
-    rng = np.random.default_rng(5000)
-    njobs = 200
+    rng = np.random.default_rng(seed)
     specs = []
     for _ in range(njobs):
-        li = int(rng.integers(4))
+        li = int(rng.integers(len(lats)))
         specs.append(dict(li=li, n_r=int(rng.choice([8, 16, 32])), n2=int(rng.integers(4, 17)),
                           dt=int(rng.choice([8, 10, 12]))))
     kcache = {}
+    for sp in specs:
+        kcache.setdefault(sp["n2"], lhc.momenta(sp["n2"]))
 
     def units(sp):
         return lats[sp["li"]]["V3"] * sp["n_r"] * len(kcache[sp["n2"]]) * (sp["dt"] + 2)
 
-    for sp in specs:
-        kcache.setdefault(sp["n2"], lhc.momenta(sp["n2"]))
-
-    def submit(sp, prec):
+    def submit(sp, p):
         la = lats[sp["li"]]
         k = kcache[sp["n2"]]
         nq = len(k)
         oi = torch.empty((sp["dt"] + 1, nq, sp["n_r"], 192), dtype=torch.complex128, device=dev)
         os_ = torch.empty((nq, sp["n_r"], 192), dtype=torch.complex128, device=dev)
-        jid = ctx.submit(lhc.JOB_THREEPT, la["h"], k, prec=prec, psi=la["psi"], eta=la["eta"], n_r=sp["n_r"],
+        jid = ctx.submit(lhc.JOB_THREEPT, la["h"], k, prec=p, psi=la["psi"], eta=la["eta"], n_r=sp["n_r"],
                          t_lo=0, t_hi=sp["dt"], t_sink=sp["dt"], out_ins=oi, out_spec=os_)
         return jid, (oi, os_)
 
     # warm-up: one job per (lattice, momentum set) shape builds phase tables and workspaces
-    seen = set()
-    warm = []
+    seen, warm = set(), []
     for sp in specs:
         key = (sp["li"], sp["n2"])
         if key not in seen:
             seen.add(key)
-            warm.append(submit(sp, args.prec))
+            warm.append(submit(sp, prec))
     for jid, _ in warm:
         ctx.wait(jid, 600000)
     torch.cuda.synchronize(dev)
 
     # capacity: everything submitted at once
     t0 = time.perf_counter()
-    sub = [submit(sp, args.prec) for sp in specs]
+    sub = [submit(sp, prec) for sp in specs]
     for jid, _ in sub:
         ctx.wait(jid, 600000)
     cap_s = time.perf_counter() - t0
@@ -285,50 +290,62 @@ def run_serve(args, dev, g):
     # Poisson arrivals at 70 % of capacity
     lam = 0.7 * cap_jobs
     gaps = rng.exponential(1.0 / lam, njobs)
-    clocks = B.Clocks(dev.index)
+    clocks = B.Clocks(B.nvsmi_id(dev.index), window="served stream")
     clocks.start()
     n0 = lhc.launch_count()
     t0 = time.perf_counter()
-    live = []
-    t_next = t0
+    live, t_next = [], t0
     for sp, gap in zip(specs, gaps):
         t_next += gap
         while time.perf_counter() < t_next:
             time.sleep(min(0.0005, max(0.0, t_next - time.perf_counter())))
-        live.append(submit(sp, args.prec))
+        live.append(submit(sp, prec))
     for jid, _ in live:
         ctx.wait(jid, 600000)
     stream_s = time.perf_counter() - t0
     clk = clocks.stop()
     n_launch = lhc.launch_count() - n0
-    lat_ms = []
+    lat_ms, spans = [], []
     for jid, _ in live:
         ts, tst, td = ctx.job_times(jid)
         lat_ms.append((td - ts) * 1e3)
+        spans.append((tst, td))
     del live
-
-    # plain FP64, one job at a time, on the jobs of the two smaller lattices (FP64 on the
-    # larger ones takes minutes per job); the mixed path one at a time on the same jobs
-    small = [sp for sp in specs if sp["li"] <= 1][:6]
-    res = {}
-    for prec in ("fp64", args.prec):
-        t0 = time.perf_counter()
-        for sp in small:
-            jid, _ = submit(sp, prec)
-            ctx.wait(jid, 600000)
-        res[prec] = sum(units(sp) for sp in small) / (time.perf_counter() - t0)
+    # the most jobs running at once: +1 at each start, -1 at each completion
+    ev = sorted([(a, 1) for a, _ in spans] + [(b, -1) for _, b in spans], key=lambda e: (e[0], e[1]))
+    run = peak = 0
+    for _, d in ev:
+        run += d
+        peak = max(peak, run)
+    out = {"value": total_units / stream_s, "unit": UNIT, "jobs": njobs, "stream_s": stream_s,
+           "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                          "max": float(np.max(lat_ms))},
+           "capacity": {"jobs_per_s": cap_jobs, "value": total_units / cap_s},
+           "arrival_rate_jobs_per_s": lam, "max_concurrent_jobs": peak, "clocks": clk, "gpu_launches": n_launch,
+           "lattices": [f"{L}^3x{T}" for L, T in lat_shapes]}
+    if fp64_small:
+        # plain FP64, one job at a time, on jobs of the two smaller lattices (FP64 on the
+        # larger ones takes minutes per job); the mixed path one at a time on the same jobs
+        small = [sp for sp in specs if sp["li"] <= 1][:fp64_small]
+        res = {}
+        for p in ("fp64", prec):
+            t0 = time.perf_counter()
+            for sp in small:
+                jid, _ = submit(sp, p)
+                ctx.wait(jid, 600000)
+            res[p] = sum(units(sp) for sp in small) / (time.perf_counter() - t0)
+        out["one_at_a_time_small_jobs"] = {"fp64": res["fp64"], prec: res[prec], "unit": UNIT, "jobs": len(small)}
     ctx.close()
-    _line(args, B.METRIC + " (served stream)", total_units / stream_s, stream_s * 1e3 / njobs,
+    return out
+
+
+def run_serve(args, dev, g):
+    sv = serve_stream(dev, g, args.prec, njobs=200, fp64_small=6)
+    _line(args, B.METRIC + " (served stream)", sv["value"], sv["stream_s"] * 1e3 / sv["jobs"],
           "served: 200 Poisson-arriving meson 3pt jobs (spectator + insertion) on 16^3x32, 24^3x48, 32^3x64, "
           "48^3x96 complex64 resident propagators, N_r in {8,16,32}, |k|^2<=4..16, t_f-t_0 in {8,10,12}, "
           "4 slots, 150 GB budget, arrival rate 0.7 x measured capacity",
-          {"clocks": clk, "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
-                                          "p99": float(np.percentile(lat_ms, 99)),
-                                          "max": float(np.max(lat_ms))},
-           "capacity": {"jobs_per_s": cap_jobs, "value": total_units / cap_s},
-           "one_at_a_time_small_jobs": {"fp64": res["fp64"], args.prec: res[args.prec], "unit": UNIT,
-                                        "jobs": len(small)},
-           "arrival_rate_jobs_per_s": lam, "gpu_launches": n_launch})
+          {k: v for k, v in sv.items() if k not in ("value", "unit", "stream_s")})
 
 
 # --------------------------------------------------------------------------- mom1

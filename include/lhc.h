@@ -242,6 +242,11 @@ int lhc_poll(lhc_ctx ctx, uint64_t job_id, int *state);
 int lhc_wait(lhc_ctx ctx, uint64_t job_id, int timeout_ms);
 int lhc_cancel(lhc_ctx ctx, uint64_t job_id);   /* queued jobs only, else LHC_EBUSY */
 int lhc_job_times(lhc_ctx ctx, uint64_t job_id, double *t_submit, double *t_start, double *t_done);
+/* Device times of a finished job, in ms after an event the server recorded when it started:
+ * when its slot's stream reached the job's first launch and when it finished the last, from
+ * CUDA timing events on that stream.  Jobs whose intervals intersect had work in flight on
+ * the device at the same time.  LHC_EBUSY until the job is done (LHC_JOB_DONE). */
+int lhc_job_device_times(lhc_ctx ctx, uint64_t job_id, double *ms_start, double *ms_done);
 int lhc_serve_stats(lhc_ctx ctx, size_t *bytes_in_use, int *queued, int *running);
 
 /* Allocation-free variant of lhc_combine (the paper has no counterpart; this is a
@@ -249,8 +254,9 @@ int lhc_serve_stats(lhc_ctx ctx, size_t *bytes_in_use, int *queued, int *running
  * a process whose device memory is owned by another allocator (for example an analysis
  * framework's caching pool that has reserved almost all of HBM), or host code that must
  * not stall, since cudaMalloc/cudaFree can synchronize the device.  Same arguments and
- * results as lhc_combine, but no context, and every buffer must be device memory
- * (host buffers give LHC_EINVAL).  The intermediate tensors live in a fixed 32 MiB
+ * results as lhc_combine, but no context, and every buffer must be device memory of
+ * the current device or managed memory (host buffers and buffers of another GPU give
+ * LHC_EINVAL).  The intermediate tensors live in a fixed 32 MiB
  * scratch array inside the library image, which every GPU that loads the library
  * holds until the process exits; the call itself never allocates.  A call needs
  * ng*(np+nq)*12*n_r*16 bytes of it for one insertion slice (larger combines give
@@ -374,8 +380,9 @@ int lhc_batch(lhc_ctx ctx, const lhc_call *calls, int ncalls, void *stream);
  * the transform, LHC_PROJ_DFT always. The mode governs single calls (and the job
  * server's slots use LHC_PROJ_AUTO); lhc_batch always projects on the tensor cores.
  * Asynchronous on `stream` once the call's momentum
- * list has been seen (its device copy is cached with the phase tables). The paper
- * projects directly (it uses at most 93 momenta). */
+ * list has been seen (its device copy is cached with the phase tables); the first call
+ * with a list uploads it with blocking copies, so make that call before any stream
+ * capture. The paper projects directly (it uses at most 93 momenta). */
 typedef enum { LHC_PROJ_AUTO = 0, LHC_PROJ_GEMM = 1, LHC_PROJ_DFT = 2 } lhc_projection;
 int lhc_set_projection(lhc_ctx ctx, int mode);
 

@@ -50,12 +50,6 @@ def _spin_mul(m4, f):
     return np.moveaxis(np.tensordot(m4, f, axes=([1], [4])), 0, 4)
 
 
-def shift_propagator(S: np.ndarray, d) -> np.ndarray:
-    """S(x - d) as an array over x, for an integer displacement d = (dx, dy, dz, dt)."""
-    dx, dy, dz, dt = (int(v) for v in d)
-    return np.roll(S, shift=(dt, dz, dy, dx), axis=(0, 1, 2, 3))
-
-
 def random_su3(rng: np.random.Generator, n: int) -> np.ndarray:
     """n Haar-like random SU(3) matrices (QR of a complex Gaussian, phase-fixed)."""
     z = (rng.standard_normal((n, 3, 3)) + 1j * rng.standard_normal((n, 3, 3))) / np.sqrt(2)

@@ -59,13 +59,17 @@ int scratch_for_current_device(double2 **out) {
   return LHC_OK;
 }
 
-bool on_device(const void *p) {
+// Device memory of the current device, or managed memory.  A buffer of another GPU is
+// refused: the scratch address belongs to the current device, and the kernels would
+// otherwise read the buffer as peer memory (or fail where peer access is off).
+bool on_device(const void *p, int dev) {
   cudaPointerAttributes a;
   if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -85,10 +89,17 @@ extern "C" int lhc_combine_noalloc(int kind, const void *spec, int np, const voi
     lhc::set_error("unknown precision %d", prec);
     return LHC_EINVAL;
   }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    lhc::set_error("cudaGetDevice failed");
+    return LHC_ECUDA;
+  }
   const void *bufs[6] = {spec, ins, snk, ins_g, src, out};
   for (const void *b : bufs)
-    if (!on_device(b)) {
-      lhc::set_error("lhc_combine_noalloc takes device buffers only (it cannot stage host memory)");
+    if (!on_device(b, dev)) {
+      lhc::set_error("lhc_combine_noalloc takes buffers of the current device only (it cannot stage host "
+                     "memory or read another GPU's)");
       return LHC_EINVAL;
     }
   // scratch use: Xs (ng*np*12*n_r) once, then Xi (ng*nq*12*n_r) per insertion slice of a chunk

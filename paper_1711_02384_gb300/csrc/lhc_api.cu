@@ -59,13 +59,15 @@ int g5mask_of(const lhc_ctx ctx) {
 }
 
 // Frees the least recently used phase table that the current call has not taken; false
-// when there is none.
+// when there is none.  Only earlier calls of this context can still read the table, and
+// the current call's stream is ordered after all of them, so synchronizing that stream
+// suffices: other contexts (the job server's slots) keep running.
 static bool evict_one_phase(lhc_ctx ctx) {
   for (auto k = ctx->phase_lru.rbegin(); k != ctx->phase_lru.rend(); ++k) {
     auto it = ctx->phases.find(*k);
     if (it != ctx->phases.end() && it->second.used_in == ctx->call_seq) continue;
     if (it != ctx->phases.end()) {
-      cudaDeviceSynchronize();
+      cudaStreamSynchronize(ctx->cur_stream);
       dev_free(ctx, it->second.buf);
       ctx->phases.erase(it);
     }
@@ -120,7 +122,9 @@ void dev_free(lhc_ctx ctx, DevBuf &b) {
 
 int ensure(lhc_ctx ctx, DevBuf &b, size_t bytes) {
   if (b.bytes >= bytes) return LHC_OK;
-  LHC_CHECK_CUDA(cudaDeviceSynchronize());   // nothing in flight may still use the old buffer
+  // nothing in flight may still use the old buffer: this context's work is ordered on the
+  // current call's stream (see begin_call), so that stream, not the device, is waited for
+  LHC_CHECK_CUDA(cudaStreamSynchronize(ctx->cur_stream));
   dev_free(ctx, b);
   return dev_alloc(ctx, b, bytes + bytes / 4);
 }
@@ -381,6 +385,7 @@ static int begin_call(lhc_ctx ctx, cudaStream_t st) {
   LHC_CHECK_CUDA(cudaSetDevice(ctx->device));
   std::lock_guard<std::mutex> g(g_sync_mu);
   ++ctx->call_seq;   // the caller holds ctx->mu
+  ctx->cur_stream = st;
   CtxSync &s = g_sync[ctx];
   if (!s.ev) LHC_CHECK_CUDA(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
   if (s.used && s.last != st) LHC_CHECK_CUDA(cudaStreamWaitEvent(st, s.ev, 0));

@@ -144,6 +144,9 @@ struct lhc_ctx_s {
   std::map<lhc::PhaseKey, lhc::PhaseEntry> phases;
   std::list<lhc::PhaseKey> phase_lru;     // front = most recent
   unsigned long long call_seq = 0;        // counts calls; the current call's tables are never evicted
+  // the stream of the current call; the context's calls are ordered across streams (each
+  // call's stream waits for the previous call), so it covers all earlier work of the context
+  cudaStream_t cur_stream = nullptr;
   int num_sms = 0;
   bool prof_on = false;
   int *dev_err = nullptr;                 // sticky device error word (bounded waits that gave up)
@@ -157,7 +160,7 @@ namespace lhc {
 // memory accounting
 int dev_alloc(lhc_ctx ctx, DevBuf &b, size_t bytes);
 void dev_free(lhc_ctx ctx, DevBuf &b);
-int ensure(lhc_ctx ctx, DevBuf &b, size_t bytes);   // grows b (synchronizes the device first)
+int ensure(lhc_ctx ctx, DevBuf &b, size_t bytes);   // grows b (synchronizes the current call's stream first)
 
 int g5mask_of(const lhc_ctx ctx);
 uint64_t hash_k(const int *k, int nq);

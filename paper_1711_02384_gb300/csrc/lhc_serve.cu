@@ -44,7 +44,10 @@ struct Job {
   size_t need = 0;      // workspace upper bound
   int slot = -1;
   double t_submit = 0, t_start = 0, t_done = 0;
-  cudaEvent_t ev = nullptr;
+  // device times (ms after the server's epoch event) at which the slot's stream reached
+  // the job's first launch and finished its last, from timing events on that stream
+  double d_start = -1, d_done = -1;
+  cudaEvent_t ev0 = nullptr, ev = nullptr;
 };
 
 struct Slot {
@@ -71,6 +74,7 @@ struct lhc_server_s {
   std::condition_variable cv, done_cv;
   std::thread worker;
   bool stop = false;
+  cudaEvent_t epoch = nullptr;   // recorded once at start: the origin of the jobs' device times
 };
 
 namespace {
@@ -119,7 +123,8 @@ int launch_job(lhc_server_s *s, Slot &sl, Job *jb) {
   const Prop &p = s->props.at(j.prop);
   const void *gb = j.prop_b ? s->props.at(j.prop_b).ptr : nullptr;
   int st = LHC_OK;
-  if (j.type != LHC_JOB_SPECTATOR)
+  if (cudaEventRecord(jb->ev0, sl.stream) != cudaSuccess) st = LHC_ECUDA;
+  if (st == LHC_OK && j.type != LHC_JOB_SPECTATOR)
     st = lhc_insertion(sl.sub, &p.lat, p.ptr, j.psi, j.n_r, j.t_lo, j.t_hi, j.r, jb->k.data(), j.nq, j.prec,
                        j.out_ins, sl.stream);
   if (st == LHC_OK && j.type != LHC_JOB_INSERTION)
@@ -139,6 +144,14 @@ void worker_main(lhc_server_s *s) {
       if (cudaEventQuery(sl.job->ev) == cudaErrorNotReady) continue;
       Job *jb = sl.job;
       int st = lhc_sync(sl.sub, sl.stream);   // the stream is idle; reads the device error word
+      float a = 0.f, b = 0.f;
+      if (cudaEventElapsedTime(&a, s->epoch, jb->ev0) == cudaSuccess &&
+          cudaEventElapsedTime(&b, s->epoch, jb->ev) == cudaSuccess) {
+        jb->d_start = a;
+        jb->d_done = b;
+      } else {
+        cudaGetLastError();
+      }
       jb->status = st;
       if (st != LHC_OK) jb->msg = lhc_last_error();
       jb->state = st == LHC_OK ? LHC_JOB_DONE : LHC_JOB_FAILED;
@@ -213,6 +226,9 @@ int lhc_serve_start(lhc_ctx ctx, int slots) {
     lhc_set_gamma5(sl.sub, ctx->g5);
     LHC_CHECK_CUDA(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking));
   }
+  LHC_CHECK_CUDA(cudaEventCreate(&s->epoch));
+  LHC_CHECK_CUDA(cudaEventRecord(s->epoch, s->slots[0].stream));
+  LHC_CHECK_CUDA(cudaEventSynchronize(s->epoch));
   g_servers[ctx] = s;
   s->worker = std::thread(worker_main, s);
   return LHC_OK;
@@ -240,8 +256,10 @@ int lhc_serve_stop(lhc_ctx ctx) {
   }
   for (auto &kv : s->jobs) {
     if (kv.second->ev) cudaEventDestroy(kv.second->ev);
+    if (kv.second->ev0) cudaEventDestroy(kv.second->ev0);
     delete kv.second;
   }
+  if (s->epoch) cudaEventDestroy(s->epoch);
   delete s;
   return LHC_OK;
 }
@@ -335,10 +353,11 @@ int lhc_submit(lhc_ctx ctx, const lhc_job *job, uint64_t *job_id) {
                    job_need(*job, pit->second), s->prop_bytes, s->budget);
     return LHC_EBUDGET;
   }
-  if (cudaEventCreateWithFlags(&jb->ev, cudaEventDisableTiming) != cudaSuccess) {
+  if (cudaEventCreate(&jb->ev0) != cudaSuccess || cudaEventCreate(&jb->ev) != cudaSuccess) {
     cudaGetLastError();
+    if (jb->ev0) cudaEventDestroy(jb->ev0);
     delete jb;
-    lhc::set_error("cannot create the job's completion event");
+    lhc::set_error("cannot create the job's timing events");
     return LHC_ECUDA;
   }
   jb->id = s->next_id++;
@@ -412,6 +431,22 @@ int lhc_job_times(lhc_ctx ctx, uint64_t job_id, double *t_submit, double *t_star
   if (t_submit) *t_submit = it->second->t_submit;
   if (t_start) *t_start = it->second->t_start;
   if (t_done) *t_done = it->second->t_done;
+  return LHC_OK;
+}
+
+int lhc_job_device_times(lhc_ctx ctx, uint64_t job_id, double *ms_start, double *ms_done) {
+  lhc_server_s *s = server_of(ctx);
+  if (!s) return LHC_ENOTFOUND;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(job_id);
+  if (it == s->jobs.end()) return LHC_ENOTFOUND;
+  const Job *jb = it->second;
+  if (jb->state != LHC_JOB_DONE) {
+    lhc::set_error("job %llu has no device times (not finished, or not run)", (unsigned long long)job_id);
+    return LHC_EBUSY;
+  }
+  if (ms_start) *ms_start = jb->d_start;
+  if (ms_done) *ms_done = jb->d_done;
   return LHC_OK;
 }
 

@@ -100,6 +100,7 @@ def lib():
         L.lhc_cancel.argtypes = [vp, u64]
         dp = ctypes.POINTER(ctypes.c_double)
         L.lhc_job_times.argtypes = [vp, u64, dp, dp, dp]
+        L.lhc_job_device_times.argtypes = [vp, u64, dp, dp]
         L.lhc_serve_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t), ip, ip]
         L.lhc_profile.argtypes = [vp, ci]
         L.lhc_profile_read.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double),
@@ -119,7 +120,7 @@ def lib():
                      "lhc_spectator", "lhc_combine", "lhc_profile", "lhc_profile_read", "lhc_sync", "lhc_release_workspace",
                      "lhc_selftest_timeout", "lhc_selftest_flag", "lhc_serve_start", "lhc_serve_stop", "lhc_prop_register",
                      "lhc_prop_release", "lhc_submit", "lhc_poll", "lhc_wait", "lhc_cancel", "lhc_job_times",
-                     "lhc_serve_stats"):
+                     "lhc_job_device_times", "lhc_serve_stats"):
             getattr(L, name).restype = ci
         _lib = L
     return _lib
@@ -475,6 +476,12 @@ class Context:
         a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         _check(lib().lhc_job_times(self._h, ctypes.c_uint64(jid), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return a.value, b.value, c.value
+
+    def job_device_times(self, jid):
+        """(ms_start, ms_done) of a finished job on the device, after the server's epoch event."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(lib().lhc_job_device_times(self._h, ctypes.c_uint64(jid), ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def serve_stats(self):
         b, q, r = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()

@@ -1,9 +1,17 @@
 """Shared helpers of the GPU parity tests: seeded inputs, oracle references and
 the per-correlator error measure.
 
-Error measure (the paper fixes none): a correlator block is one (slice, momentum)
-over all open spin-colour components and all noises; its error is
-||x_gpu - x_ref||_2 / ||x_ref||_2, and a test reports the maximum over blocks.
+Error measures (the paper fixes none):
+
+* spectator and insertion parts: a block is one (slice, momentum) over all open
+  spin-colour components and all noises; its error is ||x_gpu - x_ref||_2 / ||x_ref||_2,
+  and a test reports the maximum over blocks (``block_err``);
+* correlators of the combine: each scalar C[..][p][q] is checked on its own.  Its
+  error is |C_gpu - C_ref| divided by the largest |C_ref| of its row (the same
+  leading indices and sink momentum p, all insertion momenta q) (``corr_err``).  A
+  single wrong (p, q) entry therefore fails even where one norm over the whole
+  [np x nq] matrix would hide it, and the scale does not vanish where the terms of one
+  correlator happen to cancel.
 """
 import numpy as np
 
@@ -27,6 +35,15 @@ def block_err(got, ref, block_axes):
     num = np.linalg.norm(got - ref, axis=1)
     den = np.linalg.norm(ref, axis=1)
     return float(np.max(num / np.maximum(den, 1e-300)))
+
+
+def corr_err(got, ref):
+    """max over correlators of |got - ref| / max_q |ref|: the last axis is the insertion
+    momentum q, and the scale of a correlator is the largest |ref| of its row."""
+    got, ref = np.asarray(got), np.asarray(ref)
+    assert got.shape == ref.shape, (got.shape, ref.shape)
+    scale = np.max(np.abs(ref), axis=-1, keepdims=True)
+    return float(np.max(np.abs(got - ref) / np.maximum(scale, 1e-300)))
 
 
 class Case:

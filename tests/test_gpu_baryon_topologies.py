@@ -34,5 +34,5 @@ def test_exchange_topology_by_index_permutation(prec, tol):
     I_ref = c.ref_insertion(1, 1)[0]
     B_ab = OC.spectator_baryon(c.S[t], c.SB[t], c.eta(t), g5, c.r[:3], c.k, c.L)
     B_ba = OC.spectator_baryon(c.SB[t], c.S[t], c.eta(t), g5, c.r[:3], c.k, c.L)   # quark lines exchanged
-    assert CS.block_err(direct, OC.combine_baryon(B_ab, I_ref, ws, gi, wc), 1) < tol
-    assert CS.block_err(exch, OC.combine_baryon(B_ba, I_ref, ws, gi, wc), 1) < tol
+    assert CS.corr_err(direct, OC.combine_baryon(B_ab, I_ref, ws, gi, wc)) < tol
+    assert CS.corr_err(exch, OC.combine_baryon(B_ba, I_ref, ws, gi, wc)) < tol

@@ -47,10 +47,10 @@ def test_open_combine_contracts_to_combine(ctx, parts, prec, tol):
             got = np.einsum("tpqab,ba->tpq", op[:, a, b], gc)
             ref = np.stack([OC.combine_meson(spec, ins[t], gs[a:a + 1], gi[b:b + 1], gc[None])[0]
                             for t in range(ins.shape[0])])
-            assert CS.block_err(got, ref, 1) < tol
+            assert CS.corr_err(got, ref) < tol
             lib = ctx.combine(dev(spec), dev(ins), dev(gs[a:a + 1]), dev(gi[b:b + 1]), dev(gc[None]),
                               prec=prec).cpu().numpy()[:, 0]
-            assert CS.block_err(got, lib, 1) < (1e-12 if prec == "fp64" else 2 * tol)
+            assert CS.corr_err(got, lib) < (1e-12 if prec == "fp64" else 2 * tol)
 
 
 def test_dirac_basis_sweep(ctx, parts):
@@ -64,7 +64,7 @@ def test_dirac_basis_sweep(ctx, parts):
     rng = np.random.default_rng(2104)
     for s, i, c in rng.integers(0, 16, size=(12, 3)):
         ref = OC.combine_meson(spec, ins[0], g16[s:s + 1], g16[i:i + 1], g16[c:c + 1])[0]
-        assert np.linalg.norm(C[s, i, c] - ref) <= 1e-12 * np.linalg.norm(ref)
+        assert CS.corr_err(C[s, i, c], ref) < CS.FP64_TOL
 
 
 @pytest.fixture(scope="module")
@@ -91,10 +91,10 @@ def test_open_baryon_combine_contracts_to_combine(ctx, baryon_parts, prec, tol):
                 got = np.einsum("tpqxyz,xyz->tpq", op[:, a, b], w)
                 ref = np.stack([OC.combine_baryon(spec, ins[t], ws[a:a + 1], gi[b:b + 1], w[None])[0]
                                 for t in range(ins.shape[0])])
-                assert CS.block_err(got, ref, 1) < tol
+                assert CS.corr_err(got, ref) < tol
                 lib = ctx.combine(dev(spec), dev(ins), dev(ws[a:a + 1]), dev(gi[b:b + 1]), dev(w[None]),
                                   prec=prec).cpu().numpy()[:, 0]
-                assert CS.block_err(got, lib, 1) < (1e-12 if prec == "fp64" else 2 * tol)
+                assert CS.corr_err(got, lib) < (1e-12 if prec == "fp64" else 2 * tol)
 
 
 def test_open_baryon_single_slice_and_ragged(ctx, baryon_parts):
@@ -110,4 +110,4 @@ def test_open_baryon_single_slice_and_ragged(ctx, baryon_parts):
     # W[a1'][a2'][b'] = xyz, Gamma_ins = uv, B[p][a1',a1,a2',a2,b',c] = pxjyhzc, I[q][u,v,b,c]
     ref = np.einsum("xyz,uv,pxjyhzc,quvbc->pqjhb", ws[0], gi[0],
                     spec1[:, 0].reshape(3, 4, 4, 4, 4, 4, 3), ins1[:, 0].reshape(5, 4, 4, 4, 3))
-    assert np.abs(op[0, 0] - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert CS.corr_err(np.moveaxis(op[0, 0], 1, -1), np.moveaxis(ref, 1, -1)) < CS.FP64_TOL

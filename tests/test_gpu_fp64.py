@@ -102,14 +102,14 @@ def test_combine(ctx, kind):
     got = ctx.combine(dev(spec), dev(ins), dev(snk), dev(gi), dev(src)).cpu().numpy()
     fn = OC.combine_meson if kind == "meson" else OC.combine_baryon
     ref = fn(spec, ins, snk, gi, src)
-    assert CS.block_err(got, ref, 1) < CS.FP64_TOL
+    assert CS.corr_err(got, ref) < CS.FP64_TOL
 
 
 @pytest.mark.parametrize("kind", ["meson", "baryon"])
 @pytest.mark.parametrize("prec,tol", [("fp64", CS.FP64_TOL), ("mixed", CS.MIXED_TOL)])
 def test_combine_batched(ctx, kind, prec, tol):
     """nt insertion slices in one call; the mixed combine (FP32 per-noise sums, FP64
-    noise average) within 1e-6 per correlator."""
+    noise average) within 1e-6 per correlator C[t][g][p][q]."""
     from oracle import contractions as OC
     rng = np.random.default_rng(8)
     np_, nq, n_r, ng, nt = 33, 40, 5, 3, 4
@@ -124,4 +124,4 @@ def test_combine_batched(ctx, kind, prec, tol):
     fn = OC.combine_meson if kind == "meson" else OC.combine_baryon
     for t in range(nt):
         ref = fn(spec, ins[t], snk, gi, src)
-        assert CS.block_err(got[t], ref, 1) < tol
+        assert CS.corr_err(got[t], ref) < tol

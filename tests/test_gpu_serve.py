@@ -69,6 +69,51 @@ def test_mix_equals_alone_and_oracle():
         assert queued == 0 and running == 0 and used > 0
 
 
+def max_overlap(spans):
+    """The most intervals [a, b] that contain one point in time."""
+    ev = sorted([(a, 1) for a, _ in spans] + [(b, -1) for _, b in spans], key=lambda e: (e[0], e[1]))
+    run = peak = 0
+    for _, d in ev:
+        run += d
+        peak = max(peak, run)
+    return peak
+
+
+def test_admitted_jobs_overlap_on_the_device():
+    """Continuous batching: jobs submitted together into four slots have their work in
+    flight on the device at the same time.  Each job's device interval comes from timing
+    events on its slot's stream (lhc_job_device_times); at least two intervals intersect,
+    and so do the host intervals from admission to completion (lhc_job_times).  The mixed
+    results still equal those of the same job run alone, bit for bit."""
+    from oracle.momenta import momenta
+    from paper_1711_02384_gb300 import lhc
+    L, T, n_r = 16, 16, 8
+    S, psi = make_job_inputs(L, T, n_r, 4200)
+    dS, dpsi = dev(S), dev(psi)
+    k = momenta(4)
+    nq = len(k)
+    with lhc.Context(0) as ctx:
+        ctx.serve_start(slots=4)
+        h = ctx.prop_register(dS)
+
+        def submit():
+            out = torch.empty((8, nq, n_r, 192), dtype=torch.complex128, device="cuda")
+            return ctx.submit(lhc.JOB_INSERTION, h, k, psi=dpsi, t_lo=0, t_hi=7, out_ins=out), out
+
+        jid, alone = submit()
+        ctx.wait(jid)
+        jobs = [submit() for _ in range(8)]
+        for jid, out in jobs:
+            ctx.wait(jid)
+            assert torch.equal(out, alone)
+        dev_spans = [ctx.job_device_times(jid) for jid, _ in jobs]
+        host_spans = [ctx.job_times(jid)[1:] for jid, _ in jobs]
+        assert all(0.0 <= a <= b for a, b in dev_spans)
+        print(f"[serve] most jobs in flight at once: device {max_overlap(dev_spans)}, host {max_overlap(host_spans)}")
+        assert max_overlap(dev_spans) >= 2
+        assert max_overlap(host_spans) >= 2
+
+
 def test_budget_refusal_and_polling_and_cancel():
     from oracle.momenta import momenta
     from paper_1711_02384_gb300 import lhc
