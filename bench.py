@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the heuristic launch shapes instead of autotuning them during warm-up")
     ap.add_argument("--workload", default="meson24",
-                    choices=["meson24", "baryon32", "batched", "serve", "mom1", "allmom", "paper", "extras"],
+                    choices=["meson24", "baryon32", "batched", "serve", "mom1", "allmom", "paper", "extras",
+                             "smallcalls"],
                     help="meson24: the headline line; the others measure the further benchmark rows")
     return ap.parse_args()
 

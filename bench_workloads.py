@@ -21,6 +21,8 @@ paper     the paper's own measurement on its lattice shape: 32^3 x 96, source at
           KNL nodes for its whole measurement, as context)
 extras    the open-spin combine's 16 x 16 Dirac sweep, the baryon open combine (source spins
           open) and the free-field solver, timed
+smallcalls  many small calls (48 sources on 16^3 x 32, 4 noises, uneven momentum sets): the
+          persistent batch against the same calls one by one, both from CUDA graphs
 
 Inputs are seeded random device tensors (torch): these rows measure throughput; parity
 is the tests' job.  Each row prints one JSON line.
@@ -525,10 +527,82 @@ def run_extras(args, dev, g):
                       "runs": out}))
 
 
+# --------------------------------------------------------------------------- smallcalls
+
+def run_smallcalls(args, dev, g):
+    """Many small calls: 48 source positions on a 16^3 x 32 lattice, each an insertion over
+    3 slices and a meson spectator with 4 noises and its own momentum set (|k|^2 <= 1..8,
+    7 to 93 momenta, chunk widths 8 to 48).  A single call launches fewer CTAs than the GPU
+    has SMs, so one by one the GPU stays partly empty; the batch runs each part kind's calls
+    in one persistent launch.  Both forms are captured in CUDA graphs and replayed."""
+    from paper_1711_02384_gb300 import inputs
+    L, T, NR, NSRC = 16, 32, 4, 48
+    V3 = L ** 3
+    src = inputs.source_positions(4100, L, T, NSRC)
+    rng = np.random.default_rng(4101)
+    S = _rand((T, V3, 12, 12), torch.complex64, dev, g)
+    psi = _rand((NR, T, V3, 12), torch.complex64, dev, g)
+    eta = _rand((NR, V3, 12), torch.complex64, dev, g)
+    ctx = lhc.Context(0)
+    ctx.set_tuning(False)          # the heuristic launch shapes, the same in both forms
+    ctx.set_projection("gemm")     # as the batch: the tensor-core projection for every call
+    calls = []
+    for s_i in range(NSRC):
+        k = lhc.momenta(int(rng.integers(1, 9)))
+        r = [int(v) for v in src[s_i]]
+        nq = len(k)
+        ts = (r[3] + 2) % T
+        calls.append(dict(part="ins", S=S, vec=psi, t_lo=r[3], t_hi=r[3] + 2, r=r, k=k,
+                          out=torch.empty((3, nq, NR, 192), dtype=torch.complex128, device=dev)))
+        calls.append(dict(part="spec", S=S, vec=eta, t_lo=ts, t_hi=ts, r=r, k=k,
+                          out=torch.empty((nq, NR, 192), dtype=torch.complex128, device=dev)))
+    stream = torch.cuda.Stream(dev)
+
+    def one_by_one():
+        for c in calls:
+            if c["part"] == "ins":
+                ctx.insertion(c["S"], c["vec"], c["t_lo"], c["t_hi"], c["r"], c["k"], prec="mixed", out=c["out"],
+                              stream=stream.cuda_stream)
+            else:
+                ctx.spectator(c["S"], c["vec"], c["t_lo"], c["r"], c["k"], prec="mixed", out=c["out"],
+                              stream=stream.cuda_stream)
+
+    def batched():
+        ctx.batch(calls, stream=stream.cuda_stream)
+
+    res = {}
+    with torch.cuda.stream(stream):
+        for name, fn in (("one_by_one", one_by_one), ("batch", batched)):
+            fn()                       # phase tables, workspace
+            stream.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            n0 = lhc.launch_count()
+            with torch.cuda.graph(graph, stream=stream):
+                fn()
+            nk = lhc.launch_count() - n0
+            ms, clk, _ = _timed(lambda: graph.replay(), args.steps, args.warmup, dev, stream=stream, ctx=ctx)
+            res[name] = {"ms_per_step": ms / args.steps, "kernels_per_graph": nk, "clocks": clk}
+            if name == "one_by_one":
+                ref = [c["out"].clone() for c in calls]
+        same = all(torch.equal(c["out"], r) for c, r in zip(calls, ref))
+    units = sum(V3 * NR * len(c["k"]) * (c["t_hi"] - c["t_lo"] + 1) for c in calls)
+    ms = res["batch"]["ms_per_step"]
+    _line(args, B.METRIC, units / (ms / 1e3), ms,
+          "many small calls: 48 sources on 16^3x32, each a 3-slice insertion + meson spectator with 4 noises and "
+          "its own momentum set (|k|^2<=1..8, 7..93 momenta), complex64; the batch (one persistent launch per "
+          "part kind) against the same calls one by one, both replayed from CUDA graphs",
+          {"units_per_step": units, "calls": len(calls), "one_by_one": res["one_by_one"], "batch": res["batch"],
+           "speedup_batch_over_one_by_one": res["one_by_one"]["ms_per_step"] / ms,
+           "batch_equals_one_by_one": same, "gpu_launches": res["batch"]["kernels_per_graph"] * args.steps,
+           "clocks": res["batch"]["clocks"]})
+    ctx.close()
+
+
 def run(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     g = torch.Generator(device=dev)
     g.manual_seed(1711)
     {"baryon32": run_baryon32, "batched": run_batched, "serve": run_serve, "mom1": run_mom1,
-     "allmom": run_allmom, "paper": run_paper, "extras": run_extras}[args.workload](args, dev, g)
+     "allmom": run_allmom, "paper": run_paper, "extras": run_extras,
+     "smallcalls": run_smallcalls}[args.workload](args, dev, g)

@@ -72,6 +72,11 @@ constexpr int kProdWarp0 = 10;
 constexpr int kInWarp = kProdWarp0 + 4 * NPK;
 constexpr uint32_t kTmemCols = 512;
 
+// Threads per block of the staging, maximum and diquark kernels (memory- or
+// instruction-bound elementwise work) and of the reduce.
+constexpr int kSmallThreads = 256;
+constexpr int kReduceThreads = 128;
+
 // K-major, no swizzle: (row, k) -> core matrices of 8 rows x 16 B; 16 k per row block
 __host__ __device__ __forceinline__ uint32_t kmajor_off(int row, int k) {
   return (uint32_t)((row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
@@ -146,6 +151,8 @@ struct FusedCore {
   // batched launches: slice j's time coordinates are (tm0 + j) % tmT, (tv0 + j) % tvT
   // (these fit in the structure's alignment padding)
   int tm0, tmT, tv0, tvT;
+  int NH;     // representatives per CTA (a multiple of 8, at most RCHUNK)
+  int mode;   // the part: 0 insertion, 1 meson spectator, 2 baryon spectator
 };
 
 // One call's launch: the core parameters and, per slice, the time coordinates of its
@@ -209,12 +216,12 @@ __device__ __forceinline__ void split2(float v0, float v1, uint32_t &hi, uint32_
 }
 
 // Shared memory: NSTAGE stages of the A tiles (Ur hi, Ur lo, Ui hi, Ui lo) and the phase
-// tile B (hi and lo of 2 NH rows x 16 sites), then NIN stages of the matrix box M and the
-// vector box V.  Every region size is a multiple of 1024 bytes.
-template <int MODE, int NH>
+// tile B (hi and lo of 2 NH rows x 16 sites; room for NH = RCHUNK), then NIN stages of the
+// matrix box M and the vector box V.  Every region size is a multiple of 1024 bytes.
+template <int MODE>
 struct Stage {
   static constexpr int A = ASTAGE;
-  static constexpr int B = 2 * 2 * NH * 32;
+  static constexpr int B = 2 * 2 * RCHUNK * 32;
   static constexpr int M = MODE == 2 ? 16 * 48 * 8 : 16 * 72 * 8;
   static constexpr int V = 2 * 16 * 12 * 8;
   static constexpr int ab = A + B;
@@ -222,21 +229,33 @@ struct Stage {
   static constexpr int bytes = NSTAGE * ab + NIN * in;
 };
 
+// Running-sum columns per half in registers when a chunk has the most representatives
+// (NH = RCHUNK): tensor memory holds the two accumulator buffers (8 NH columns) and 64
+// columns of each half's running sum.
+constexpr int kNRMax = 2 * RCHUNK - (kTmemCols - 8 * RCHUNK) / 2;
+static_assert(kNRMax == 32 && (kTmemCols - 8 * RCHUNK) / 2 == 64, "tensor-memory split at the widest chunk");
+
 // The work of one CTA: tile ct (noise pair, 16 matrix columns), site split `split`,
 // slice j and representative chunk rc of the call described by p; tm, tv are slice j's
-// time coordinates in the tensor maps.
-template <typename CT, int MODE, int NH>
+// time coordinates in the tensor maps; tbase is the CTA's tensor memory (all 512 columns,
+// allocated by the kernel).  The chunk width p.NH is a launch parameter: every width uses
+// the same code, shared-memory layout and order of operations.  On return every barrier
+// of the body is invalidated, so a persistent CTA can run the body again.
+template <typename CT, int MODE>
 __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, const int split, const int j,
-                                           const int rc, const int tm, const int tv) {
-  static_assert(NH % 8 == 0 && NH <= RCHUNK, "representative chunk");
-  using St = Stage<MODE, NH>;
+                                           const int rc, const int tm, const int tv, const uint32_t tbase) {
+  using St = Stage<MODE>;
+  const int NH = p.NH;
   // NP accumulator columns per half: [cos | sin] x NH representatives; half 0 takes the
   // products with Ur, half 1 those with Ui.
-  constexpr int NP = 2 * NH;
+  const int NP = 2 * NH;
   // tensor memory: D buffers [0, 2NP) and [2NP, 4NP); the rest holds NT columns of each
-  // half's running sum, the remaining NR = NP - NT columns stay in registers
-  constexpr int NT = ((kTmemCols - 4 * NP) / 2 / 16 * 16) < NP ? ((kTmemCols - 4 * NP) / 2 / 16 * 16) : NP;
-  constexpr int NR = NP - NT;
+  // half's running sum (a multiple of 16, at most NP).  Only the widest chunk (NH = 48,
+  // NP = 96) leaves columns over: NT = 64, and NR = kNRMax = 32 columns of each half stay
+  // in registers.  Narrower chunks keep the whole running sum in tensor memory.
+  const int NT = min(((int)kTmemCols - 4 * NP) / 2 / 16 * 16, NP);
+  const bool wide = NT < NP;
+  const int Bbytes = 2 * 2 * NH * 32;   // the phase tile of one k-step
   extern __shared__ __align__(1024) char smem_raw[];
   // TMA destinations want 128-byte alignment: align the stage ring to 1024 explicitly
   char *smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -247,12 +266,11 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
   // wait and one commit per two k-steps keeps the MMA thread's gaps short.
   uint64_t *full = bars, *empty = bars + NPAIR, *inFull = bars + 2 * NPAIR, *inEmpty = bars + 2 * NPAIR + NIN,
            *tfull = bars + 2 * NPAIR + 2 * NIN, *tempty = tfull + 2, *done = tfull + 4;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
   // Verdicts of waits that one leader thread performs for a group of warps, which block on
   // a named barrier meanwhile: [0, 2) drain (by chunk parity), then four slots per
   // producer group (k-step offset), of which the first two hold the verdict of the
   // joint input and A-stage wait (by iteration parity).
-  volatile int *verdict = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  volatile int *verdict = reinterpret_cast<volatile int *>(done + 1) + 1;
   auto stA = [&](int s) { return smem + s * St::ab; };
   auto stB = [&](int s) { return smem + s * St::ab + St::A; };
   auto stM = [&](int s) { return smem + NSTAGE * St::ab + s * St::in; };
@@ -289,22 +307,20 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
     tc::mbar_init(done, 1);
     tc::fence_mbar_init();
   }
-  if (warp == 1) tc::tmem_alloc(tmem_slot, kTmemCols);
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  const uint32_t tbase = *tmem_slot;
 
   if (warp == 0) {
     // ---------------------------------------------------- phase tiles (A/B ring)
     if (lane == 0 && nk > 0) {
-      const char *Bsrc = reinterpret_cast<const char *>(p.B) + ((size_t)rc * p.nkb + kb0) * St::B;
+      const char *Bsrc = reinterpret_cast<const char *>(p.B) + ((size_t)rc * p.nkb + kb0) * Bbytes;
       int issued = 0;
       for (int i = 0; i < nk; ++i) {
         const int s = i % NSTAGE, pr = s >> 1, u = i / NSTAGE;
         if (u > 0 && !tc::mbar_wait(&empty[pr], (u - 1) & 1, err, 1)) break;
-        tc::mbar_arrive_expect_tx(&full[pr], St::B);
-        tc::bulk_g2s(stB(s), Bsrc + (size_t)i * St::B, St::B, &full[pr]);
+        tc::mbar_arrive_expect_tx(&full[pr], Bbytes);
+        tc::bulk_g2s(stB(s), Bsrc + (size_t)i * Bbytes, Bbytes, &full[pr]);
         issued = i + 1;
       }
       for (int i = max(0, issued - NSTAGE); i < issued; i += 2) {   // nothing may still be landing
@@ -343,14 +359,15 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
       // A: MN-major (row m = s*8 + noise*4 + spin), core matrices 8 k x 16 B: the 16 row
       // groups s lie 144 B apart (SBO; the 16 B of padding per group keep the producers'
       // stores free of bank conflicts), the two 8-site k blocks 2304 B apart (LBO)
-      constexpr uint32_t idesc = tc::idesc_f16(MT, NP) | (1u << 15);
+      const uint32_t idesc = tc::idesc_f16(MT, NP) | (1u << 15);
       // Everything between two k-steps' MMAs is on the tensor pipe's critical path (it
       // queues few MMAs), so the loop does no division and builds no descriptor: the
       // descriptors of stage 0 are offset by immediates (the start-address field is
       // bytes / 16 and cannot carry out for shared-memory addresses).
       const uint64_t dA0 = tc::smem_desc(tc::smem_u32(stA(0)), 2304, 144);
       const uint64_t dB0 = tc::smem_desc(tc::smem_u32(stB(0)), 128, 256);
-      constexpr uint64_t kStageStep = St::ab >> 4, kATile = ATILE >> 4, kBHalf = (NP * 32) >> 4;
+      constexpr uint64_t kStageStep = St::ab >> 4, kATile = ATILE >> 4;
+      const uint64_t kBHalf = (uint64_t)(NP * 32) >> 4;
       // k-steps come in pairs (nk is even): stage pair pr holds stages 2 pr and 2 pr + 1
       int i = 0, pr = 0;
       uint32_t ph = 0;   // phase of full[pr] for the pair starting at k-step i
@@ -397,9 +414,9 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
     const int row = qd * 32 + lane;
     const uint32_t lane_base = tbase + ((uint32_t)(qd * 32) << 16);
     const uint32_t rsum = lane_base + (uint32_t)(4 * NP + h * NT);   // this half's running sum in TMEM
-    float acc[NR > 0 ? NR : 1];
+    float acc[kNRMax];   // columns NT .. NP - 1 of the running sum (widest chunk only)
 #pragma unroll
-    for (int n = 0; n < NR; ++n) acc[n] = 0.f;
+    for (int n = 0; n < kNRMax; ++n) acc[n] = 0.f;
     for (int c = 0; c < nchunks; ++c) {
       int b = c & 1, ub = c >> 1;
       // one thread waits, the eight drain warps block on named barrier 1 and follow its
@@ -411,7 +428,8 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
       tc::tc_fence_after();
       const uint32_t t = lane_base + (uint32_t)(b * 2 * NP + h * NP);
 #pragma unroll
-      for (int n0 = 0; n0 < NP; n0 += 16) {
+      for (int n0 = 0; n0 < 2 * RCHUNK; n0 += 16) {
+        if (n0 >= NP) break;   // uniform over the CTA
         float v[16];
         tc::tmem_ld16(t + n0, v);
         if (n0 < NT) {
@@ -428,10 +446,11 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
             }
           }
           tc::tmem_st16(rsum + n0, r);
-        } else {
+        } else if (n0 >= 2 * RCHUNK - kNRMax) {   // register part (NT = 2 RCHUNK - kNRMax here)
           tc::tmem_wait_ld();
+          constexpr int kNT = 2 * RCHUNK - kNRMax;
 #pragma unroll
-          for (int e = 0; e < 16; e += 2) add2(acc[n0 - NT + e], acc[n0 - NT + e + 1], v[e], v[e + 1]);
+          for (int e = 0; e < 16; e += 2) add2(acc[n0 - kNT + e], acc[n0 - kNT + e + 1], v[e], v[e + 1]);
         }
       }
       tc::tmem_wait_st();
@@ -471,10 +490,12 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
           if (mine && rho < rend) out[(size_t)rho * p.ncols * 4 + n / NH] = sgn * r[e];
         }
       }
+      if (wide) {   // NP - NT == kNRMax
 #pragma unroll
-      for (int e = 0; e < NR; ++e) {
-        const int n = NT + e, rho = n % NH;
-        if (mine && rho < rend) out[(size_t)rho * p.ncols * 4 + n / NH] = sgn * acc[e];
+        for (int e = 0; e < kNRMax; ++e) {
+          const int n = NT + e, rho = n % NH;
+          if (mine && rho < rend && n < NP) out[(size_t)rho * p.ncols * 4 + n / NH] = sgn * acc[e];
+        }
       }
     }
   } else {
@@ -598,45 +619,79 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  if (warp == 1) tc::tmem_dealloc(tbase, kTmemCols);
+  // every copy has landed and every MMA has completed (the loaders and the MMA thread
+  // waited for that): nothing arrives on the barriers any more
+  if (threadIdx.x == 0)
+    for (uint64_t *b = bars; b <= done; ++b) tc::mbar_inval(b);
 }
 
-template <typename CT, int MODE, int NH>
+// Tensor memory for the whole CTA: warp 1 allocates all 512 columns (one CTA per SM) and
+// gives up the right to allocate again; the address reaches every thread through shared
+// memory.
+__device__ __forceinline__ uint32_t cta_tmem_alloc(uint32_t *slot) {
+  if ((threadIdx.x >> 5) == 1) tc::tmem_alloc(slot, kTmemCols);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  return *slot;
+}
+
+template <typename CT, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant__ FusedParams p) {
+  __shared__ uint32_t tslot;
+  const uint32_t tbase = cta_tmem_alloc(&tslot);
   const int j = blockIdx.z / p.c.nrc, rc = blockIdx.z % p.c.nrc;
-  fused_body<CT, MODE, NH>(p.c, blockIdx.x, blockIdx.y, j, rc, p.tM[j], p.tV[j]);
+  fused_body<CT, MODE>(p.c, blockIdx.x, blockIdx.y, j, rc, p.tM[j], p.tV[j], tbase);
+  if ((threadIdx.x >> 5) == 1) tc::tmem_dealloc(tbase, kTmemCols);
 }
 
-// Many calls of one part kind and chunk width in one launch: the parameters of up to
-// kMaxBatch calls travel in the kernel's parameter space (a captured graph keeps them),
-// call c owns the CTAs first[c] .. first[c+1]-1, and every CTA does exactly the work it
-// would do in its call's own launch.
+// Many calls in one persistent launch.  The parameters of up to kMaxBatch calls travel in
+// the kernel's parameter space (a captured graph keeps them), and every call's work is
+// numbered as tasks (tile, site split, slice, representative chunk), call c owning tasks
+// first[c] .. first[c+1]-1.  One CTA per SM takes the next task from a device counter
+// (an atomic add, no waiting) until none is left, so calls of every part and chunk width
+// share the launch, and an SM that finishes a short task takes the next one at once.  Each
+// task does exactly what the CTA with its coordinates does in its call's own launch.
 constexpr int kMaxBatch = 64;
 struct BatchParams {
   FusedCore item[kMaxBatch];
   int first[kMaxBatch + 1];
   int n;
+  int *cursor;   // the next task; set to zero before the launch
 };
 static_assert(sizeof(BatchParams) <= 32764, "kernel parameter space");
 
-template <typename CT, int MODE, int NH>
-__global__ void __launch_bounds__(kThreads, 1) fused_batch(const __grid_constant__ BatchParams b) {
-  int lo = 0, hi = b.n;   // the call: first[lo] <= blockIdx.x < first[lo + 1]
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (b.first[mid] <= (int)blockIdx.x)
-      lo = mid;
-    else
-      hi = mid;
+template <typename CT, int MODE>
+__global__ void __launch_bounds__(kThreads, 1) fused_persistent(const __grid_constant__ BatchParams b) {
+  __shared__ int next;
+  __shared__ uint32_t tslot;
+  const uint32_t tbase = cta_tmem_alloc(&tslot);   // once: the permit to allocate is given up
+  const int ntasks = b.first[b.n];
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(b.cursor, 1);
+    __syncthreads();
+    const int task = next;
+    __syncthreads();   // every thread has read the task before thread 0 takes another
+    if (task >= ntasks) break;
+    int lo = 0, hi = b.n;   // the call: first[lo] <= task < first[lo + 1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (b.first[mid] <= task)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    const FusedCore &it = b.item[lo];
+    int local = task - b.first[lo];
+    const int ct = local % it.nct;
+    local /= it.nct;
+    const int split = local % it.nsplit;
+    local /= it.nsplit;
+    const int j = local / it.nrc, rc = local % it.nrc;
+    const int tm = (it.tm0 + j) % it.tmT, tv = (it.tv0 + j) % it.tvT;
+    fused_body<CT, MODE>(it, ct, split, j, rc, tm, tv, tbase);
   }
-  const FusedCore &it = b.item[lo];
-  int local = (int)blockIdx.x - b.first[lo];
-  const int ct = local % it.nct;
-  local /= it.nct;
-  const int split = local % it.nsplit;
-  local /= it.nsplit;
-  const int j = local / it.nrc, rc = local % it.nrc;
-  fused_body<CT, MODE, NH>(it, ct, split, j, rc, (it.tm0 + j) % it.tmT, (it.tv0 + j) % it.tvT);
+  if ((threadIdx.x >> 5) == 1) tc::tmem_dealloc(tbase, kTmemCols);
 }
 
 // out[j][q][col] = sum over splits of the FP32 partials.  The partials are added without
@@ -658,7 +713,8 @@ __device__ __forceinline__ void two_sum(float &hi, float &lo, float v) {
 // -1): Re = Re C - sigma Im S and Im = Im C + sigma Re S are formed as FP32 pairs too
 // (TwoSum of the leading parts, the trailing parts added), and each pair is rounded once
 // to FP64 with one FP64 addition; the FP64 pipe of GB300 does nothing else here.
-__global__ void reduce_f64(const float4 *__restrict__ part, int nsplit, size_t per_split,
+__global__ void __launch_bounds__(kReduceThreads)
+    reduce_f64(const float4 *__restrict__ part, int nsplit, size_t per_split,
                            const int *__restrict__ rep_first, const int *__restrict__ rep_q, int nrep, int sign,
                            int ncols, double2 *__restrict__ out, int nt, size_t out_stride) {
   const size_t n_in = (size_t)nrep * ncols;
@@ -688,59 +744,36 @@ __global__ void reduce_f64(const float4 *__restrict__ part, int nsplit, size_t p
   }
 }
 
-template <int MODE, int NH>
+template <int MODE>
 constexpr size_t fused_smem() {
   // rings + barriers + tensor-memory slot + up to 1023 B to align the rings
-  return (size_t)Stage<MODE, NH>::bytes + (2 * NPAIR + 2 * NIN + 5) * 8 + 16 + 4 * (2 + 4 * NPK) + 1024;
+  return (size_t)Stage<MODE>::bytes + (2 * NPAIR + 2 * NIN + 5) * 8 + 16 + 4 * (2 + 4 * NPK) + 1024;
 }
+static_assert(fused_smem<0>() <= 232448 && fused_smem<1>() <= 232448 && fused_smem<2>() <= 232448,
+              "shared memory per CTA");
 
-template <int MODE, int NH>
-int launch_fused_t(const FusedParams &p, int nt, cudaStream_t st) {
-  constexpr size_t smem = fused_smem<MODE, NH>();
-  static_assert(smem <= 232448, "shared memory per CTA");
+// One call's fused launch; the shared memory (over 120 KB) keeps one CTA per SM, which the
+// whole-tensor-memory allocation needs.
+template <int MODE>
+int launch_fused(const FusedParams &p, int nt, cudaStream_t st) {
+  constexpr size_t smem = fused_smem<MODE>();
+  static_assert(smem > 120 * 1024, "one CTA per SM");
   static std::atomic<unsigned long long> done{0};
-  LHC_TRY(ensure_smem_limit(fused_meson<float2, MODE, NH>, (int)std::max<size_t>(smem, 120 * 1024), done));
+  LHC_TRY(ensure_smem_limit(fused_meson<float2, MODE>, (int)smem, done));
   dim3 grid(p.c.nct, p.c.nsplit, nt * p.c.nrc);
-  // at least 120 KB so that one CTA runs per SM (the tensor memory is allocated whole)
-  fused_meson<float2, MODE, NH><<<grid, kThreads, std::max<size_t>(smem, 120 * 1024), st>>>(p);
+  fused_meson<float2, MODE><<<grid, kThreads, smem, st>>>(p);
   note_launch();
   return LHC_OK;
 }
 
 template <int MODE>
-int launch_fused_nh(int NH, const FusedParams &p, int nt, cudaStream_t st) {
-  switch (NH) {
-    case 8: return launch_fused_t<MODE, 8>(p, nt, st);
-    case 16: return launch_fused_t<MODE, 16>(p, nt, st);
-    case 24: return launch_fused_t<MODE, 24>(p, nt, st);
-    case 32: return launch_fused_t<MODE, 32>(p, nt, st);
-    case 40: return launch_fused_t<MODE, 40>(p, nt, st);
-    case 48: return launch_fused_t<MODE, 48>(p, nt, st);
-    default: set_error("unsupported representative chunk %d", NH); return LHC_EINVAL;
-  }
-}
-
-template <int MODE, int NH>
-int launch_batch_t(const BatchParams &b, int nctas, cudaStream_t st) {
-  constexpr size_t smem = fused_smem<MODE, NH>();
+int launch_persistent(const BatchParams &b, int nctas, cudaStream_t st) {
+  constexpr size_t smem = fused_smem<MODE>();
   static std::atomic<unsigned long long> done{0};
-  LHC_TRY(ensure_smem_limit(fused_batch<float2, MODE, NH>, (int)std::max<size_t>(smem, 120 * 1024), done));
-  fused_batch<float2, MODE, NH><<<nctas, kThreads, std::max<size_t>(smem, 120 * 1024), st>>>(b);
+  LHC_TRY(ensure_smem_limit(fused_persistent<float2, MODE>, (int)smem, done));
+  fused_persistent<float2, MODE><<<nctas, kThreads, smem, st>>>(b);
   note_launch();
   return LHC_OK;
-}
-
-template <int MODE>
-int launch_batch_nh(int NH, const BatchParams &b, int nctas, cudaStream_t st) {
-  switch (NH) {
-    case 8: return launch_batch_t<MODE, 8>(b, nctas, st);
-    case 16: return launch_batch_t<MODE, 16>(b, nctas, st);
-    case 24: return launch_batch_t<MODE, 24>(b, nctas, st);
-    case 32: return launch_batch_t<MODE, 32>(b, nctas, st);
-    case 40: return launch_batch_t<MODE, 40>(b, nctas, st);
-    case 48: return launch_batch_t<MODE, 48>(b, nctas, st);
-    default: set_error("unsupported representative chunk %d", NH); return LHC_EINVAL;
-  }
 }
 
 // number of site splits: fill whole waves of one CTA per SM as well as possible
@@ -791,8 +824,8 @@ __device__ __forceinline__ void block_max_to(unsigned *m, float v) {
 // its four 16-byte loads before converting, so each SM keeps many loads in flight.  The
 // conversion is the integer one (f64_to_f32_rne): with the hardware conversion this
 // copy is bound by the FP64 pipe.
-constexpr int kNarrowChunk = 1024;
-__global__ void __launch_bounds__(256) narrow_c128(NarrowParams p) {
+constexpr int kNarrowChunk = 4 * kSmallThreads;
+__global__ void __launch_bounds__(kSmallThreads) narrow_c128(NarrowParams p) {
   const size_t nS = (size_t)p.V3 * 144, nV = (size_t)p.V3 * 12;
   const size_t cS = (nS + kNarrowChunk - 1) / kNarrowChunk, cV = (nV + kNarrowChunk - 1) / kNarrowChunk;
   size_t b = blockIdx.x;
@@ -827,13 +860,13 @@ __global__ void __launch_bounds__(256) narrow_c128(NarrowParams p) {
   double2 v[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
-    if (e0 + u * 256 < n) v[u] = __ldcs(src + e0 + u * 256);
+    if (e0 + u * kSmallThreads < n) v[u] = __ldcs(src + e0 + u * kSmallThreads);
   float m = 0.f;
 #pragma unroll
   for (int u = 0; u < 4; ++u)
-    if (e0 + u * 256 < n) {
+    if (e0 + u * kSmallThreads < n) {
       const float2 w = make_float2(f64_to_f32_rne(v[u].x), f64_to_f32_rne(v[u].y));
-      dst[e0 + u * 256] = w;
+      dst[e0 + u * kSmallThreads] = w;
       m = fmaxf(m, fmaxf(fabsf(w.x), fabsf(w.y)));
     }
   block_max_to(mx, m);
@@ -847,7 +880,7 @@ struct MaxParams {
   int nb, V3, n_r, with_S;
 };
 
-__global__ void __launch_bounds__(256) max_c64(MaxParams p) {
+__global__ void __launch_bounds__(kSmallThreads) max_c64(MaxParams p) {
   const size_t nS = (size_t)p.V3 * 144, nV = (size_t)p.V3 * 12;
   const size_t cS = (nS + kNarrowChunk - 1) / kNarrowChunk, cV = (nV + kNarrowChunk - 1) / kNarrowChunk;
   size_t b = blockIdx.x;
@@ -874,8 +907,8 @@ __global__ void __launch_bounds__(256) max_c64(MaxParams p) {
   float m = 0.f;
 #pragma unroll
   for (int u = 0; u < 2; ++u)
-    if (e0 + u * 256 < n) {
-      const float4 w = __ldcs(src + e0 + u * 256);
+    if (e0 + u * kSmallThreads < n) {
+      const float4 w = __ldcs(src + e0 + u * kSmallThreads);
       m = fmaxf(m, fmaxf(fmaxf(fabsf(w.x), fabsf(w.y)), fmaxf(fabsf(w.z), fabsf(w.w))));
     }
   block_max_to(mx, m);
@@ -886,18 +919,19 @@ __global__ void __launch_bounds__(256) max_c64(MaxParams p) {
 // with p = c'+1, q = c'+2, u = c+1, v = c+2 (mod 3) the four nonzero terms are
 // GA[p,u]GB[q,v] - GA[p,v]GB[q,u] - GA[q,u]GB[p,v] + GA[q,v]GB[p,u].
 // One CTA per site: the two 12x12 propagators are staged in shared memory.
-__global__ void __launch_bounds__(256) baryon_diquark(const float2 *__restrict__ GA, const float2 *__restrict__ GB,
-                                                      int V3, float2 *__restrict__ D, unsigned *maxD) {
+__global__ void __launch_bounds__(kSmallThreads)
+    baryon_diquark(const float2 *__restrict__ GA, const float2 *__restrict__ GB, int V3, float2 *__restrict__ D,
+                   unsigned *maxD) {
   __shared__ float2 a[144], bm[144];
   const int x = blockIdx.x;
-  for (int e = threadIdx.x; e < 144; e += 256) {
+  for (int e = threadIdx.x; e < 144; e += kSmallThreads) {
     a[e] = GA[(size_t)x * 144 + e];
     bm[e] = GB[(size_t)x * 144 + e];
   }
   __syncthreads();
   float2 *out = D + (size_t)x * 2304;
   float m = 0.f;   // largest |re| or |im| of D (the bound of the fused kernel's split scale)
-  for (int e = threadIdx.x; e < 2304; e += 256) {
+  for (int e = threadIdx.x; e < 2304; e += kSmallThreads) {
     const int cp = e / 768, sidx = e % 768, c = sidx % 3, al = sidx / 3;
     const int a2 = al & 3, a2p = (al >> 2) & 3, a1 = (al >> 4) & 3, a1p = al >> 6;
     const int pp = (cp + 1) % 3, qq = (cp + 2) % 3, u = (c + 1) % 3, v = (c + 2) % 3;
@@ -1140,7 +1174,13 @@ static int prepare_chunk(lhc_ctx ctx, const SliceJob *jobs, int nb, int nq, int 
   // site blocks, rounded up to an even number: the kernel consumes k-steps in pairs (the
   // pad block's phases are zero and its sites lie past the slice, which TMA reads as zero)
   fp.c.nkb = ((V3 + 2 * KSTEP - 1) / (2 * KSTEP)) * 2;
+  if (NH < 8 || NH > RCHUNK || NH % 8 != 0) {
+    set_error("unsupported representative chunk %d", NH);
+    return LHC_EINVAL;
+  }
   fp.c.nrc = nrc;
+  fp.c.NH = NH;
+  fp.c.mode = (int)j0.part;
   fp.c.nrep = reps.nrep();
   fp.c.ncols = ncols;
   fp.c.nsplit = nsplit;
@@ -1178,7 +1218,7 @@ static int prepare_chunk(lhc_ctx ctx, const SliceJob *jobs, int nb, int nq, int 
     np.V3 = V3;
     ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT, (double)nb * V3 * ((baryon ? 288.0 : 144.0) + 12.0 * n_r) * 24);
     const size_t blocks = (size_t)(nb + (baryon ? 1 : 0)) * cS + (size_t)n_r * nb * cV;
-    narrow_c128<<<(unsigned)blocks, 256, 0, st>>>(np);
+    narrow_c128<<<(unsigned)blocks, kSmallThreads, 0, st>>>(np);
     note_launch();
   } else {
     // complex64 inputs are read in place; one read-only pass finds their maxima
@@ -1193,7 +1233,7 @@ static int prepare_chunk(lhc_ctx ctx, const SliceJob *jobs, int nb, int nq, int 
     mp.with_S = baryon ? 0 : 1;   // the baryon's matrix operand is the diquark
     ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT, (double)nb * V3 * ((baryon ? 0.0 : 144.0) + 12.0 * n_r) * 8);
     const size_t blocks = (size_t)(baryon ? 0 : nb) * cS + (size_t)n_r * nb * cV;
-    max_c64<<<(unsigned)blocks, 256, 0, st>>>(mp);
+    max_c64<<<(unsigned)blocks, kSmallThreads, 0, st>>>(mp);
     note_launch();
   }
   // tensor maps of the matrix operand and the vector of this chunk of slices
@@ -1225,7 +1265,7 @@ static int prepare_chunk(lhc_ctx ctx, const SliceJob *jobs, int nb, int nq, int 
     const float2 *GB = narrow ? reinterpret_cast<const float2 *>(ws + lay.off_sb) : static_cast<const float2 *>(j0.SB);
     float2 *D = reinterpret_cast<float2 *>(ws + lay.off_d);
     ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT, (double)V3 * (288.0 + 2304.0) * 8);
-    baryon_diquark<<<V3, 256, 0, st>>>(GA, GB, V3, D, maxD);
+    baryon_diquark<<<V3, kSmallThreads, 0, st>>>(GA, GB, V3, D, maxD);
     note_launch();
     const uint64_t dims[3] = {768, 3, (uint64_t)V3}, strides[2] = {768 * 8, 2304 * 8};
     const uint32_t box[3] = {16, 3, 16};
@@ -1246,16 +1286,20 @@ static int prepare_chunk(lhc_ctx ctx, const SliceJob *jobs, int nb, int nq, int 
 static int finish_chunk(lhc_ctx ctx, const Prepared &pc, cudaStream_t st) {
   const size_t n_in = (size_t)pc.nrep * pc.ncols;
   ProfScope ps(ctx, st, LHC_KERNEL_REDUCE, (double)pc.nb * pc.nsplit * n_in * 16 + (double)pc.nb * pc.n_out * 16);
-  reduce_f64<<<(unsigned)((n_in * pc.nb + 255) / 256), 256, 0, st>>>(pc.fp.c.partial, pc.nsplit, pc.per_split,
-                                                                      pc.rmap, pc.rmap + pc.nrep + 1, pc.nrep, pc.sign,
-                                                                      pc.ncols, pc.out, pc.nb, pc.n_out);
+  reduce_f64<<<(unsigned)((n_in * pc.nb + kReduceThreads - 1) / kReduceThreads), kReduceThreads, 0, st>>>(
+      pc.fp.c.partial, pc.nsplit, pc.per_split, pc.rmap, pc.rmap + pc.nrep + 1, pc.nrep, pc.sign, pc.ncols, pc.out,
+      pc.nb, pc.n_out);
   note_launch();
   LHC_CHECK_CUDA(cudaGetLastError());
   return LHC_OK;
 }
 
 static int kd_default() {
-  int kd = 6;   // k-steps accumulated in tensor memory between drains (truncating accumulation)
+  // k-steps accumulated in tensor memory between drains.  The accumulation truncates, so
+  // the error grows with the interval: measured on the 24^3 workload (16 noises, 93
+  // momenta) intervals 6, 4 and 2 give 4.6e-7, 3.6e-7 and 2.9e-7 per block against the
+  // oracle, for 1% and 11% more time in the fused kernel than interval 6.
+  int kd = 4;
   if (const char *e = getenv("LHC_KD")) kd = std::max(2, (atoi(e) + 1) / 2 * 2);   // even: k-steps come in pairs
   return kd;
 }
@@ -1282,11 +1326,11 @@ static int run_mixed_shape(lhc_ctx ctx, const SliceJob *jobs, int nt, const int 
     {
       ProfScope ps(ctx, st, LHC_KERNEL_FUSED, 8.0 * nb * (double)nq * ncols * j0.V3);
       if (j0.part == PART_INS)
-        LHC_TRY(launch_fused_nh<0>(NH, pc.fp, nb, st));
+        LHC_TRY(launch_fused<0>(pc.fp, nb, st));
       else if (j0.part == PART_SPEC_MESON)
-        LHC_TRY(launch_fused_nh<1>(NH, pc.fp, nb, st));
+        LHC_TRY(launch_fused<1>(pc.fp, nb, st));
       else
-        LHC_TRY(launch_fused_nh<2>(NH, pc.fp, nb, st));
+        LHC_TRY(launch_fused<2>(pc.fp, nb, st));
     }
     LHC_TRY(finish_chunk(ctx, pc, st));
   }
@@ -1405,10 +1449,13 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
   return run_mixed_shape(ctx, jobs, nt, k, nq, r, sign, st, reps, NH, nsplit);
 }
 
-// A batch of mixed calls: every call is prepared (in its own workspace region), the
-// fused kernel runs once per (part kind, chunk width) group of up to kMaxBatch calls, and
-// every call is reduced.  Each CTA does what it does in its call's own launch, with the
-// same launch shape, so the results are bitwise those of the calls made one by one.
+// A batch of mixed calls: every call is prepared (in its own workspace region), the fused
+// work of up to kMaxBatch calls of one part kind, whatever their chunk widths, runs in one
+// persistent launch, and every call is reduced.  Each task does what the CTA with its
+// coordinates does in its call's own launch, with the same launch shape, so the results
+// are bitwise those of the calls made one by one.  Within a launch the calls are ordered
+// by the length of their tasks (k-steps per site split), longest first, so that the short
+// tasks fill the end.
 int run_batch_mixed(lhc_ctx ctx, const std::vector<BatchCall> &calls, cudaStream_t st) {
   const int n = (int)calls.size();
   std::vector<MomentumReps> reps(n);
@@ -1435,55 +1482,65 @@ int run_batch_mixed(lhc_ctx ctx, const std::vector<BatchCall> &calls, cudaStream
     lay[c] = chunk_layout(j0, nt, nsplit[c], (size_t)nrc * NH[c] * ncols);
     off[c + 1] = off[c] + lay[c].bytes;
   }
-  LHC_TRY(ensure(ctx, ctx->ws, off[n]));
+  int count[3] = {0, 0, 0};
+  for (const BatchCall &bc : calls) ++count[bc.jobs[0].part];
+  int nlaunch = 0;
+  for (int m = 0; m < 3; ++m) nlaunch += (count[m] + kMaxBatch - 1) / kMaxBatch;
+  const size_t off_cursor = (off[n] + 255) & ~(size_t)255;   // one task counter per launch
+  LHC_TRY(ensure(ctx, ctx->ws, off_cursor + sizeof(int) * (size_t)nlaunch));
   char *ws = static_cast<char *>(ctx->ws.p);
+  int *cursor = reinterpret_cast<int *>(ws + off_cursor);
   const int kd = kd_default();
   std::vector<Prepared> pc(n);
-  double work[3] = {0, 0, 0};
   for (int c = 0; c < n; ++c) {
     const BatchCall &bc = calls[c];
     LHC_TRY(prepare_chunk(ctx, bc.jobs.data(), (int)bc.jobs.size(), bc.nq, bc.sign, reps[c], phase[c], rmap[c], NH[c],
                           nsplit[c], kd, ws + off[c], lay[c], st, &pc[c]));
-    work[pc[c].mode] += 8.0 * pc[c].nb * (double)bc.nq * pc[c].ncols * bc.jobs[0].V3;
-  }
-  // one fused launch per (part kind, chunk width), kMaxBatch calls at most
-  for (int mode = 0; mode < 3; ++mode) {
-    for (int nh = 8; nh <= RCHUNK; nh += 8) {
-      std::vector<int> group;
-      for (int c = 0; c < n; ++c)
-        if (pc[c].mode == mode && pc[c].NH == nh) group.push_back(c);
-      for (size_t g0 = 0; g0 < group.size(); g0 += kMaxBatch) {
-        std::unique_ptr<BatchParams> bpp(new BatchParams());   // 29 KB: kept off the stack
-        BatchParams &bp = *bpp;
-        bp.n = (int)std::min<size_t>(kMaxBatch, group.size() - g0);
-        bp.first[0] = 0;
-        double w = 0.0;
-        for (int e = 0; e < bp.n; ++e) {
-          const Prepared &q = pc[group[g0 + e]];
-          bp.item[e] = q.fp.c;
-          bp.item[e].tm0 = q.tm0;
-          bp.item[e].tmT = q.tmT;
-          bp.item[e].tv0 = q.tv0;
-          bp.item[e].tvT = q.tvT;
-          for (int j = 0; j < q.nb; ++j)
-            if (q.fp.tM[j] != (q.tm0 + j) % q.tmT || q.fp.tV[j] != (q.tv0 + j) % q.tvT) {
-              set_error("batch: the slices of a call must be consecutive (mod T) in its tensors");
-              return LHC_EINVAL;
-            }
-          bp.first[e + 1] = bp.first[e] + q.fp.c.nct * q.fp.c.nsplit * q.nb * q.fp.c.nrc;
-          w += 8.0 * q.nb * (double)(q.n_out / q.ncols) * q.ncols * q.fp.c.V3;
-        }
-        ProfScope ps(ctx, st, LHC_KERNEL_FUSED, w);
-        if (mode == 0)
-          LHC_TRY(launch_batch_nh<0>(nh, bp, bp.first[bp.n], st));
-        else if (mode == 1)
-          LHC_TRY(launch_batch_nh<1>(nh, bp, bp.first[bp.n], st));
-        else
-          LHC_TRY(launch_batch_nh<2>(nh, bp, bp.first[bp.n], st));
+    const Prepared &q = pc[c];
+    for (int j = 0; j < q.nb; ++j)
+      if (q.fp.tM[j] != (q.tm0 + j) % q.tmT || q.fp.tV[j] != (q.tv0 + j) % q.tvT) {
+        set_error("batch: the slices of a call must be consecutive (mod T) in its tensors");
+        return LHC_EINVAL;
       }
-    }
   }
-  (void)work;
+  // by part kind, longest tasks first (k-steps per site split), ties in call order
+  std::vector<int> order(n);
+  for (int c = 0; c < n; ++c) order[c] = c;
+  auto task_len = [&](int c) { return (pc[c].fp.c.nkb + pc[c].nsplit - 1) / pc[c].nsplit; };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return pc[a].mode != pc[b].mode ? pc[a].mode < pc[b].mode : task_len(a) > task_len(b);
+  });
+  LHC_CHECK_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * (size_t)nlaunch, st));
+  for (int c0 = 0, l = 0; c0 < n; ++l) {
+    const int mode = pc[order[c0]].mode;
+    int c1 = c0;
+    while (c1 < n && c1 - c0 < kMaxBatch && pc[order[c1]].mode == mode) ++c1;
+    std::unique_ptr<BatchParams> bpp(new BatchParams());   // 25 KB: kept off the stack
+    BatchParams &bp = *bpp;
+    bp.n = c1 - c0;
+    bp.cursor = cursor + l;
+    bp.first[0] = 0;
+    double w = 0.0;
+    for (int e = 0; e < bp.n; ++e) {
+      const Prepared &q = pc[order[c0 + e]];
+      bp.item[e] = q.fp.c;
+      bp.item[e].tm0 = q.tm0;
+      bp.item[e].tmT = q.tmT;
+      bp.item[e].tv0 = q.tv0;
+      bp.item[e].tvT = q.tvT;
+      bp.first[e + 1] = bp.first[e] + q.fp.c.nct * q.fp.c.nsplit * q.nb * q.fp.c.nrc;
+      w += 8.0 * q.nb * (double)(q.n_out / q.ncols) * q.ncols * q.fp.c.V3;
+    }
+    ProfScope ps(ctx, st, LHC_KERNEL_FUSED, w);
+    const int nctas = std::min(bp.first[bp.n], ctx->num_sms);
+    if (mode == 0)
+      LHC_TRY(launch_persistent<0>(bp, nctas, st));
+    else if (mode == 1)
+      LHC_TRY(launch_persistent<1>(bp, nctas, st));
+    else
+      LHC_TRY(launch_persistent<2>(bp, nctas, st));
+    c0 = c1;
+  }
   for (int c = 0; c < n; ++c) LHC_TRY(finish_chunk(ctx, pc[c], st));
   LHC_CHECK_CUDA(cudaGetLastError());
   return LHC_OK;

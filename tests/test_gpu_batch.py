@@ -1,7 +1,8 @@
 """Batched calls (lhc_batch): many mixed-precision insertion and spectator calls with
-uneven momentum sets, lattices and parts in one fused launch per part kind; the results
-must equal, bit for bit, those of the same calls made one by one with the tensor-core
-projection, and one of them the oracle."""
+uneven momentum sets, lattices and parts in one persistent fused launch per part kind;
+the results must equal, bit for bit, those of the same calls made one by one with the
+tensor-core projection, also when replayed from a CUDA graph, and the oracle within the
+mixed tolerance."""
 import numpy as np
 import pytest
 
@@ -48,3 +49,61 @@ def test_batch_equals_single_calls():
     c = cases[0]
     assert CS.block_err(got[0].cpu().numpy(), c.ref_insertion(1, 3), 2) < CS.MIXED_TOL
     assert CS.block_err(got[2].cpu().numpy(), c.ref_spectator_baryon(2), 1) < CS.MIXED_TOL
+
+
+def test_persistent_batch_replayed_from_a_cuda_graph():
+    """One persistent launch per part kind over calls with five momentum-chunk widths
+    (7, 33, 57, 93 and 147 momenta: 4, 17, 29, 47 and 74 representatives, chunks of 8,
+    24, 32, 48 and two of 40), two lattices and both input precisions, captured in a CUDA
+    graph and replayed:
+    the replay equals the same calls made one by one bit for bit, and the oracle within
+    the mixed tolerance."""
+    from paper_1711_02384_gb300 import lhc
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    sets = [lhc.momenta(1), lhc.momenta(3), lhc.momenta(5), lhc.momenta(8), lhc.momenta(10)]
+    cases = [CS.Case(6, 6, 3, sets[0], seed=2510, r=(1, 0, 5, 0)),
+             CS.Case(8, 4, 2, sets[3], seed=2511, r=(3, 2, 1, 0), dtype=np.complex64)]
+    calls = []
+    for n, c in enumerate(cases):
+        S, SB, psi, eta = dev(c.S), dev(c.SB), dev(c.psi), dev(c.eta(1))
+        for m, k in enumerate(sets):
+            t_lo = (n + m) % c.T
+            calls.append(dict(part="ins", S=S, vec=psi, t_lo=t_lo, t_hi=t_lo + 1 + m % 2, r=c.r, k=k))
+            calls.append(dict(part="spec", S=S, vec=eta, t_lo=1, t_hi=1, r=c.r, k=k))
+        calls.append(dict(part="baryon", S=S, GB=SB, vec=eta, t_lo=1, t_hi=1, r=c.r, k=sets[2 + n]))
+    stream = torch.cuda.Stream()
+    with lhc.Context(0) as ctx, torch.cuda.stream(stream):
+        ctx.set_projection("gemm")
+        ref = []
+        for c in calls:
+            if c["part"] == "ins":
+                ref.append(ctx.insertion(c["S"], c["vec"], c["t_lo"], c["t_hi"], c["r"], c["k"], prec="mixed",
+                                         stream=stream.cuda_stream))
+            else:
+                ref.append(ctx.spectator(c["S"], c["vec"], c["t_lo"], c["r"], c["k"], prec="mixed", GB=c.get("GB"),
+                                         stream=stream.cuda_stream))
+        outs = ctx.batch(calls, stream=stream.cuda_stream)   # phase tables and workspace for the capture
+        for c, o in zip(calls, outs):
+            c["out"] = o
+        stream.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            ctx.batch(calls, stream=stream.cuda_stream)
+        for o in outs:
+            o.fill_(float("nan"))
+        graph.replay()
+        stream.synchronize()
+        ctx.sync(stream.cuda_stream)
+        for o, r in zip(outs, ref):
+            assert torch.equal(o, r)
+        graph.replay()                                          # a second replay, the same bits
+        stream.synchronize()
+        for o, r in zip(outs, ref):
+            assert torch.equal(o, r)
+    # calls 17 and 21: the 93-momentum insertion over slices 0..2 and the baryon of the
+    # second lattice; call 1: the 7-momentum meson spectator of the first
+    c = cases[1]
+    assert CS.block_err(outs[17].cpu().numpy(), c.ref_insertion(0, 2), 2) < CS.MIXED_TOL
+    assert CS.block_err(outs[21].cpu().numpy(), c.ref_spectator_baryon(1), 1) < CS.MIXED_TOL
+    c = cases[0]
+    assert CS.block_err(outs[1].cpu().numpy(), c.ref_spectator_meson(1), 1) < CS.MIXED_TOL

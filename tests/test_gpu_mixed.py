@@ -77,17 +77,19 @@ def _klists():
     k9 = momenta(9)
     extra = np.array([k for k in k9 if k @ k == 9 and tuple(k) > tuple(-k)])[:4]
     r51 = np.concatenate([momenta(8), extra, -extra])               # 51 representatives: two chunks of 32
+    r36 = np.array([k for k in momenta(8) if tuple(k) > tuple(-k)])[:36]   # one chunk of 40 (36 used)
     return [("unpaired", half), ("shuffled", mixed), ("k=-k mod L", modL), ("four chunks", big),
-            ("51 representatives", r51), ("62 representatives", k9)]
+            ("51 representatives", r51), ("62 representatives", k9), ("36 representatives", r36),
+            ("74 representatives", momenta(10))]                    # two chunks of 40
 
 
 @pytest.mark.parametrize("name,k", _klists(), ids=lambda v: v if isinstance(v, str) else "")
 def test_momentum_lists(ctx, name, k):
     """The projection groups the momenta into pairs {k, -k} and forms both from the same
     cos and sin sums: momentum lists with unpaired momenta, broken pairs, duplicates,
-    an arbitrary order, momenta whose negatives coincide modulo L (L = 4), and more
-    representatives than one chunk (51 and 62: two chunks; 173: four), all against the
-    oracle."""
+    an arbitrary order, momenta whose negatives coincide modulo L (L = 4), every chunk
+    width (36 representatives: one chunk of 40; 51 and 62: two of 32; 74: two of 40;
+    173: four of 48), all against the oracle."""
     c = CS.Case(4, 4, 2, k, seed=1450, r=(3, 1, 2, 0))
     gi = ctx.insertion(dev(c.S), dev(c.psi), 0, 2, c.r, c.k, prec="mixed").cpu().numpy()
     gs = ctx.spectator(dev(c.S), dev(c.eta(2)), 2, c.r, c.k, prec="mixed").cpu().numpy()
