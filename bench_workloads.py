@@ -192,6 +192,13 @@ def run_batched(args, dev, g):
         calls()                      # tunes the launch shapes, builds the phase tables, sizes the workspace
         step_calls()
         torch.cuda.synchronize(dev)
+        # the same calls one by one, captured in a graph of their own, for comparison
+        ctx.set_projection("gemm")   # as the batch: the tensor-core projection for every call
+        g1 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g1, stream=stream):
+            calls()
+        ms1, clk1, _ = _timed(lambda: g1.replay(), args.steps, args.warmup, dev, stream=stream, ctx=ctx)
+        del g1
         graph = torch.cuda.CUDAGraph()
         n0 = lhc.launch_count()
         with torch.cuda.graph(graph, stream=stream):
@@ -216,10 +223,13 @@ def run_batched(args, dev, g):
     _line(args, B.METRIC, units * args.steps / (ms / 1e3), ms / args.steps,
           "batched 32^3x64, 16 sources x t_f-t_0 in {8,10,12}, N_r=16, meson insertion + meson and baryon "
           "spectators, per-job momentum sets |k|^2<=4..16 (33..257), one CUDA graph per step"
-          + (", all 144 calls in one lhc_batch (one fused launch per part kind and chunk width)" if use_batch else ""),
+          + (", all 144 calls in one lhc_batch (one persistent fused launch per part kind and chunk width)"
+             if use_batch else ""),
           {"clocks": clk, "roofline": _roofline(ctx), "units_per_step": units, "jobs": len(jobs),
            "gpu_launches": n_graph * args.steps, "kernels_per_graph": n_graph,
-           "graph_replay_equals_direct_calls": same})
+           "graph_replay_equals_direct_calls": same,
+           "one_by_one": {"ms_per_step": ms1 / args.steps, "clocks": clk1},
+           "speedup_batch_over_one_by_one": (ms1 / ms) if use_batch else None})
     ctx.close()
 
 
@@ -534,7 +544,8 @@ def run_smallcalls(args, dev, g):
     3 slices and a meson spectator with 4 noises and its own momentum set (|k|^2 <= 1..8,
     7 to 93 momenta, chunk widths 8 to 48).  A single call launches fewer CTAs than the GPU
     has SMs, so one by one the GPU stays partly empty; the batch runs each part kind's calls
-    in one persistent launch.  Both forms are captured in CUDA graphs and replayed."""
+    in persistent launches (one per part kind and chunk width).  Both forms are captured in
+    CUDA graphs and replayed."""
     from paper_1711_02384_gb300 import inputs
     L, T, NR, NSRC = 16, 32, 4, 48
     V3 = L ** 3
@@ -590,7 +601,7 @@ def run_smallcalls(args, dev, g):
     _line(args, B.METRIC, units / (ms / 1e3), ms,
           "many small calls: 48 sources on 16^3x32, each a 3-slice insertion + meson spectator with 4 noises and "
           "its own momentum set (|k|^2<=1..8, 7..93 momenta), complex64; the batch (one persistent launch per "
-          "part kind) against the same calls one by one, both replayed from CUDA graphs",
+          "part kind and chunk width) against the same calls one by one, both replayed from CUDA graphs",
           {"units_per_step": units, "calls": len(calls), "one_by_one": res["one_by_one"], "batch": res["batch"],
            "speedup_batch_over_one_by_one": res["one_by_one"]["ms_per_step"] / ms,
            "batch_equals_one_by_one": same, "gpu_launches": res["batch"]["kernels_per_graph"] * args.steps,

@@ -353,9 +353,9 @@ typedef struct {
   void *out;
 } lhc_call;
 /* Runs ncalls calls in precision LHC_MIXED with one persistent fused-kernel launch per
- * part kind, for up to 64 calls per launch, whatever their momentum sets and chunk
- * widths: one CTA per SM takes the calls' tasks (tile, site split, slice, momentum chunk),
- * longest first, from a device counter until none is left. The per-call staging and
+ * part kind and momentum-chunk width, for up to 64 calls per launch: one CTA per SM takes
+ * the calls' tasks (tile, site split, slice, momentum chunk), longest first, from a device
+ * counter until none is left. The per-call staging and
  * reduce kernels stay separate launches. A batch always projects on the tensor cores,
  * whatever lhc_set_projection says. The results are bitwise those of the same calls
  * made one by one in LHC_PROJ_GEMM mode: each CTA does the work it does in its call's

@@ -44,17 +44,40 @@ __device__ __forceinline__ void st(double2 *p, cplx<R> v) {
 }
 
 // Stage one [n_r][cols] block (and the Gamma matrices) of an input in shared memory and
-// let the CTA's threads serve all (g, i, colour) tasks of that block from there.
+// let the CTA's threads serve all (g, i, colour) tasks of that block from there.  Each
+// thread issues its loads four at a time before converting and storing any of them, so
+// a thread waits for one memory latency per four values instead of one per value.
+template <typename R, typename Dst>
+__device__ __forceinline__ void stage_batched(const double2 *src, int n, Dst dst_index, cplx<R> *dst) {
+  constexpr int U = 4;
+  const int step = blockDim.x;
+  for (int e0 = threadIdx.x; e0 < n; e0 += U * step) {
+    double2 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (e0 + u * step < n) v[u] = src[e0 + u * step];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * step;
+      if (e < n) {
+        if constexpr (std::is_same<R, float>::value)
+          dst[dst_index(e)] = cplx<R>{f64_to_f32_rne(v[u].x), f64_to_f32_rne(v[u].y)};
+        else
+          dst[dst_index(e)] = cplx<R>{v[u].x, v[u].y};
+      }
+    }
+  }
+}
 template <typename R>
 __device__ __forceinline__ void stage(cplx<R> *dst, const double2 *src, int n) {
-  for (int e = threadIdx.x; e < n; e += blockDim.x) dst[e] = ld<R>(src + e);
+  stage_batched<R>(src, n, [](int e) { return e; }, dst);
 }
 // The per-noise blocks of 192 values are staged 193 apart: consecutive tasks belong to
 // different noises, and a stride of 192 complex numbers would put them in one bank.
 constexpr int SROW = 193;
 template <typename R>
 __device__ __forceinline__ void stage_rows(cplx<R> *dst, const double2 *src, int n_r) {
-  for (int e = threadIdx.x; e < n_r * 192; e += blockDim.x) dst[(e / 192) * SROW + e % 192] = ld<R>(src + e);
+  stage_batched<R>(src, n_r * 192, [](int e) { return (e / 192) * SROW + e % 192; }, dst);
 }
 
 // CTA per (t, q): Xi[t][g][q][i,al,a] = sum_b Gsrc[g][b][al] sum_{at,bt} Gins[g][at][bt] I[t][q][i][at,bt,b,a]
@@ -259,6 +282,28 @@ struct NoiseSum<float> {
 // static shared memory stays below 48 KB); rows are padded by one element so that the
 // 16 q rows a warp reads fall into distinct banks.
 constexpr int TP = 32, TQ = 48;
+
+// Rows r0 .. r0 + ROWS - 1 (those below nrow), columns k0 .. k0 + kw - 1 of a row-major
+// [nrow][ldk] matrix into a [ROWS][KW] shared tile (zeros outside); a thread issues its
+// loads in groups of three before storing them.
+template <typename R, int ROWS, int COLS, int KW>
+__device__ __forceinline__ void stage_tile(cplx<R> *dst, const cplx<R> *src, size_t ldk, int k0, int r0, int nrow,
+                                           int kw) {
+  constexpr int N = ROWS * COLS, G = 3;
+  for (int e0 = threadIdx.x; e0 < N; e0 += G * 256) {
+    cplx<R> v[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const int e = e0 + 256 * u, r = e / COLS, k = e % COLS;
+      v[u] = (e < N && r0 + r < nrow && k < kw) ? src[(size_t)(r0 + r) * ldk + k0 + k] : cplx<R>{0, 0};
+    }
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const int e = e0 + 256 * u;
+      if (e < N) dst[(e / COLS) * KW + e % COLS] = v[u];
+    }
+  }
+}
 template <typename R>
 __global__ void __launch_bounds__(256) comb_gemm(const cplx<R> *__restrict__ Xs, const cplx<R> *__restrict__ Xi,
                                                  int np, int nq, int n_r, int ng, double inv_n, float inv_n_pow2,
@@ -276,14 +321,10 @@ __global__ void __launch_bounds__(256) comb_gemm(const cplx<R> *__restrict__ Xs,
   NoiseSum<R> acc[2][3];
   for (int i0 = 0; i0 < n_r; i0 += KN) {
     const int kw = 12 * min(KN, n_r - i0);
-    for (int e = threadIdx.x; e < TP * 12 * KN; e += 256) {
-      const int r = e / (12 * KN), k = e % (12 * KN);
-      As[r * KW + k] = (p0 + r < np && k < kw) ? A[(size_t)(p0 + r) * K + 12 * i0 + k] : cplx<R>{0, 0};
-    }
-    for (int e = threadIdx.x; e < TQ * 12 * KN; e += 256) {
-      const int r = e / (12 * KN), k = e % (12 * KN);
-      Bs[r * KW + k] = (q0 + r < nq && k < kw) ? B[(size_t)(q0 + r) * K + 12 * i0 + k] : cplx<R>{0, 0};
-    }
+    // all of a thread's loads of the pass are issued before any is stored (one memory
+    // latency per pass, not one per value)
+    stage_tile<R, TP, 12 * KN, KW>(As, A, K, 12 * i0, p0, np, kw);
+    stage_tile<R, TQ, 12 * KN, KW>(Bs, B, K, 12 * i0, q0, nq, kw);
     __syncthreads();
     // two noises (24 terms) per partial sum; a missing second noise is staged as zeros
     for (int ii = 0; ii < kw / 12; ii += 2) {

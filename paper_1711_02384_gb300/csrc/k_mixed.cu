@@ -238,14 +238,14 @@ static_assert(kNRMax == 32 && (kTmemCols - 8 * RCHUNK) / 2 == 64, "tensor-memory
 // The work of one CTA: tile ct (noise pair, 16 matrix columns), site split `split`,
 // slice j and representative chunk rc of the call described by p; tm, tv are slice j's
 // time coordinates in the tensor maps; tbase is the CTA's tensor memory (all 512 columns,
-// allocated by the kernel).  The chunk width p.NH is a launch parameter: every width uses
-// the same code, shared-memory layout and order of operations.  On return every barrier
-// of the body is invalidated, so a persistent CTA can run the body again.
-template <typename CT, int MODE>
+// allocated by the kernel).  NH is the chunk width (p.NH, compiled in).  Every width uses
+// the same shared-memory layout and order of operations.  On return every barrier of the
+// body is invalidated, so a persistent CTA can run the body again.
+template <typename CT, int MODE, int NH>
 __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, const int split, const int j,
                                            const int rc, const int tm, const int tv, const uint32_t tbase) {
+  static_assert(NH % 8 == 0 && NH >= 8 && NH <= RCHUNK, "representative chunk");
   using St = Stage<MODE>;
-  const int NH = p.NH;
   // NP accumulator columns per half: [cos | sin] x NH representatives; half 0 takes the
   // products with Ur, half 1 those with Ui.
   const int NP = 2 * NH;
@@ -564,27 +564,35 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
           unsigned long long A[8], B[8];
   #pragma unroll
           for (int iv = 0; iv < 8; ++iv) A[iv] = B[iv] = 0ull;
+          // the four spins of one noise at a time (rows iv .. iv + 3): the colour step c of
+          // all eight accumulators is issued together, so eight independent FMAs separate
+          // two steps of one accumulator chain (the order of each chain is unchanged)
   #pragma unroll
-          for (int iv = 0; iv < 8; ++iv) {
-            // noise iv / 4, spin iv % 4: the three colours with one 16-byte and one 8-byte load
-            const unsigned long long *pb =
-                reinterpret_cast<const unsigned long long *>(Vs + (iv >> 2) * 16 * 12 + (iv & 3) * 3);
-            unsigned long long pv[3];
-            if ((iv & 1) == 0) {   // colours 0, 1 start on a 16-byte boundary
-              const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(pb);
-              pv[0] = q.x;
-              pv[1] = q.y;
-              pv[2] = pb[2];
-            } else {               // colours 1, 2 do
-              pv[0] = pb[0];
-              const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(pb + 1);
-              pv[1] = q.x;
-              pv[2] = q.y;
+          for (int i4 = 0; i4 < 8; i4 += 4) {
+            unsigned long long pv[4][3];
+  #pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              // noise (i4 + r) / 4, spin r: the three colours with one 16-byte and one 8-byte load
+              const unsigned long long *pb =
+                  reinterpret_cast<const unsigned long long *>(Vs + (i4 >> 2) * 16 * 12 + r * 3);
+              if ((r & 1) == 0) {   // colours 0, 1 start on a 16-byte boundary
+                const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(pb);
+                pv[r][0] = q.x;
+                pv[r][1] = q.y;
+                pv[r][2] = pb[2];
+              } else {              // colours 1, 2 do
+                pv[r][0] = pb[0];
+                const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(pb + 1);
+                pv[r][1] = q.x;
+                pv[r][2] = q.y;
+              }
             }
   #pragma unroll
             for (int c = 0; c < 3; ++c) {
-              fma2(A[iv], pv[c], ma[c]);
-              fma2(B[iv], pv[c], mb[c]);
+  #pragma unroll
+              for (int r = 0; r < 4; ++r) fma2(A[i4 + r], pv[r][c], ma[c]);
+  #pragma unroll
+              for (int r = 0; r < 4; ++r) fma2(B[i4 + r], pv[r][c], mb[c]);
             }
           }
           if (jx == 1) {   // the input stage is read: hand it back to the input loader
@@ -636,22 +644,25 @@ __device__ __forceinline__ uint32_t cta_tmem_alloc(uint32_t *slot) {
   return *slot;
 }
 
-template <typename CT, int MODE>
+template <typename CT, int MODE, int NH>
 __global__ void __launch_bounds__(kThreads, 1) fused_meson(const __grid_constant__ FusedParams p) {
   __shared__ uint32_t tslot;
   const uint32_t tbase = cta_tmem_alloc(&tslot);
   const int j = blockIdx.z / p.c.nrc, rc = blockIdx.z % p.c.nrc;
-  fused_body<CT, MODE>(p.c, blockIdx.x, blockIdx.y, j, rc, p.tM[j], p.tV[j], tbase);
+  fused_body<CT, MODE, NH>(p.c, blockIdx.x, blockIdx.y, j, rc, p.tM[j], p.tV[j], tbase);
   if ((threadIdx.x >> 5) == 1) tc::tmem_dealloc(tbase, kTmemCols);
 }
 
-// Many calls in one persistent launch.  The parameters of up to kMaxBatch calls travel in
-// the kernel's parameter space (a captured graph keeps them), and every call's work is
-// numbered as tasks (tile, site split, slice, representative chunk), call c owning tasks
-// first[c] .. first[c+1]-1.  One CTA per SM takes the next task from a device counter
-// (an atomic add, no waiting) until none is left, so calls of every part and chunk width
-// share the launch, and an SM that finishes a short task takes the next one at once.  Each
-// task does exactly what the CTA with its coordinates does in its call's own launch.
+// Many calls in one persistent launch.  The parameters of up to kMaxBatch calls of one part
+// kind and chunk width travel in the kernel's parameter space (a captured graph keeps
+// them), and every call's work is numbered as tasks (tile, site split, slice,
+// representative chunk), call c owning tasks first[c] .. first[c+1]-1.  One CTA per SM
+// takes the next task from a device counter (an atomic add, no waiting) until none is
+// left, so an SM that finishes a short task takes the next one at once.  Each task does
+// exactly what the CTA with its coordinates does in its call's own launch.  (The width is
+// a compile-time parameter: a kernel body that handles several widths, by a runtime
+// width or by a switch over compiled widths, needs more than the 80 registers a thread
+// has and spills, and measured slower than the calls one by one.)
 constexpr int kMaxBatch = 64;
 struct BatchParams {
   FusedCore item[kMaxBatch];
@@ -661,7 +672,7 @@ struct BatchParams {
 };
 static_assert(sizeof(BatchParams) <= 32764, "kernel parameter space");
 
-template <typename CT, int MODE>
+template <typename CT, int MODE, int NH>
 __global__ void __launch_bounds__(kThreads, 1) fused_persistent(const __grid_constant__ BatchParams b) {
   __shared__ int next;
   __shared__ uint32_t tslot;
@@ -689,7 +700,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_persistent(const __grid_con
     local /= it.nsplit;
     const int j = local / it.nrc, rc = local % it.nrc;
     const int tm = (it.tm0 + j) % it.tmT, tv = (it.tv0 + j) % it.tvT;
-    fused_body<CT, MODE>(it, ct, split, j, rc, tm, tv, tbase);
+    fused_body<CT, MODE, NH>(it, ct, split, j, rc, tm, tv, tbase);
   }
   if ((threadIdx.x >> 5) == 1) tc::tmem_dealloc(tbase, kTmemCols);
 }
@@ -752,28 +763,54 @@ constexpr size_t fused_smem() {
 static_assert(fused_smem<0>() <= 232448 && fused_smem<1>() <= 232448 && fused_smem<2>() <= 232448,
               "shared memory per CTA");
 
-// One call's fused launch; the shared memory (over 120 KB) keeps one CTA per SM, which the
-// whole-tensor-memory allocation needs.
-template <int MODE>
-int launch_fused(const FusedParams &p, int nt, cudaStream_t st) {
+// One call's fused launch, compiled for its chunk width; the shared memory (over 120 KB)
+// keeps one CTA per SM, which the whole-tensor-memory allocation needs.
+template <int MODE, int NH>
+int launch_fused_t(const FusedParams &p, int nt, cudaStream_t st) {
   constexpr size_t smem = fused_smem<MODE>();
   static_assert(smem > 120 * 1024, "one CTA per SM");
   static std::atomic<unsigned long long> done{0};
-  LHC_TRY(ensure_smem_limit(fused_meson<float2, MODE>, (int)smem, done));
+  LHC_TRY(ensure_smem_limit(fused_meson<float2, MODE, NH>, (int)smem, done));
   dim3 grid(p.c.nct, p.c.nsplit, nt * p.c.nrc);
-  fused_meson<float2, MODE><<<grid, kThreads, smem, st>>>(p);
+  fused_meson<float2, MODE, NH><<<grid, kThreads, smem, st>>>(p);
   note_launch();
   return LHC_OK;
 }
 
 template <int MODE>
-int launch_persistent(const BatchParams &b, int nctas, cudaStream_t st) {
+int launch_fused(const FusedParams &p, int nt, cudaStream_t st) {
+  switch (p.c.NH) {
+    case 8: return launch_fused_t<MODE, 8>(p, nt, st);
+    case 16: return launch_fused_t<MODE, 16>(p, nt, st);
+    case 24: return launch_fused_t<MODE, 24>(p, nt, st);
+    case 32: return launch_fused_t<MODE, 32>(p, nt, st);
+    case 40: return launch_fused_t<MODE, 40>(p, nt, st);
+    case 48: return launch_fused_t<MODE, 48>(p, nt, st);
+    default: set_error("unsupported representative chunk %d", p.c.NH); return LHC_EINVAL;
+  }
+}
+
+template <int MODE, int NH>
+int launch_persistent_t(const BatchParams &b, int nctas, cudaStream_t st) {
   constexpr size_t smem = fused_smem<MODE>();
   static std::atomic<unsigned long long> done{0};
-  LHC_TRY(ensure_smem_limit(fused_persistent<float2, MODE>, (int)smem, done));
-  fused_persistent<float2, MODE><<<nctas, kThreads, smem, st>>>(b);
+  LHC_TRY(ensure_smem_limit(fused_persistent<float2, MODE, NH>, (int)smem, done));
+  fused_persistent<float2, MODE, NH><<<nctas, kThreads, smem, st>>>(b);
   note_launch();
   return LHC_OK;
+}
+
+template <int MODE>
+int launch_persistent(int NH, const BatchParams &b, int nctas, cudaStream_t st) {
+  switch (NH) {
+    case 8: return launch_persistent_t<MODE, 8>(b, nctas, st);
+    case 16: return launch_persistent_t<MODE, 16>(b, nctas, st);
+    case 24: return launch_persistent_t<MODE, 24>(b, nctas, st);
+    case 32: return launch_persistent_t<MODE, 32>(b, nctas, st);
+    case 40: return launch_persistent_t<MODE, 40>(b, nctas, st);
+    case 48: return launch_persistent_t<MODE, 48>(b, nctas, st);
+    default: set_error("unsupported representative chunk %d", NH); return LHC_EINVAL;
+  }
 }
 
 // number of site splits: fill whole waves of one CTA per SM as well as possible
@@ -1450,8 +1487,8 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
 }
 
 // A batch of mixed calls: every call is prepared (in its own workspace region), the fused
-// work of up to kMaxBatch calls of one part kind, whatever their chunk widths, runs in one
-// persistent launch, and every call is reduced.  Each task does what the CTA with its
+// work of up to kMaxBatch calls of one part kind and chunk width runs in one persistent
+// launch, and every call is reduced.  Each task does what the CTA with its
 // coordinates does in its call's own launch, with the same launch shape, so the results
 // are bitwise those of the calls made one by one.  Within a launch the calls are ordered
 // by the length of their tasks (k-steps per site split), longest first, so that the short
@@ -1482,10 +1519,13 @@ int run_batch_mixed(lhc_ctx ctx, const std::vector<BatchCall> &calls, cudaStream
     lay[c] = chunk_layout(j0, nt, nsplit[c], (size_t)nrc * NH[c] * ncols);
     off[c + 1] = off[c] + lay[c].bytes;
   }
-  int count[3] = {0, 0, 0};
-  for (const BatchCall &bc : calls) ++count[bc.jobs[0].part];
+  // persistent launches: at most one per (part, chunk width) and kMaxBatch calls
   int nlaunch = 0;
-  for (int m = 0; m < 3; ++m) nlaunch += (count[m] + kMaxBatch - 1) / kMaxBatch;
+  {
+    std::map<std::pair<int, int>, int> count;
+    for (int c = 0; c < n; ++c) ++count[{(int)calls[c].jobs[0].part, NH[c]}];
+    for (const auto &kv : count) nlaunch += (kv.second + kMaxBatch - 1) / kMaxBatch;
+  }
   const size_t off_cursor = (off[n] + 255) & ~(size_t)255;   // one task counter per launch
   LHC_TRY(ensure(ctx, ctx->ws, off_cursor + sizeof(int) * (size_t)nlaunch));
   char *ws = static_cast<char *>(ctx->ws.p);
@@ -1503,18 +1543,39 @@ int run_batch_mixed(lhc_ctx ctx, const std::vector<BatchCall> &calls, cudaStream
         return LHC_EINVAL;
       }
   }
-  // by part kind, longest tasks first (k-steps per site split), ties in call order
-  std::vector<int> order(n);
-  for (int c = 0; c < n; ++c) order[c] = c;
+  // A call whose own launch fills at least kOwnWaves waves of one CTA per SM gains
+  // nothing from sharing a launch (its tail is a small part of it; measured on 144 calls of
+  // 32^3 x 64: 359 ms in persistent launches against 348 ms one by one), so it keeps its own
+  // fused launch.  The others go to the persistent launches: by part kind and chunk width,
+  // longest tasks first (k-steps per site split), ties in call order.
+  constexpr int kOwnWaves = 4;
+  std::vector<int> order;
+  for (int c = 0; c < n; ++c) {
+    const long long ctas = (long long)pc[c].fp.c.nct * pc[c].fp.c.nsplit * pc[c].nb * pc[c].fp.c.nrc;
+    if (ctas >= (long long)kOwnWaves * ctx->num_sms) {
+      ProfScope ps(ctx, st, LHC_KERNEL_FUSED, 8.0 * pc[c].nb * (double)calls[c].nq * pc[c].ncols * pc[c].fp.c.V3);
+      if (pc[c].mode == 0)
+        LHC_TRY(launch_fused<0>(pc[c].fp, pc[c].nb, st));
+      else if (pc[c].mode == 1)
+        LHC_TRY(launch_fused<1>(pc[c].fp, pc[c].nb, st));
+      else
+        LHC_TRY(launch_fused<2>(pc[c].fp, pc[c].nb, st));
+    } else {
+      order.push_back(c);
+    }
+  }
+  const int nper = (int)order.size();
   auto task_len = [&](int c) { return (pc[c].fp.c.nkb + pc[c].nsplit - 1) / pc[c].nsplit; };
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    return pc[a].mode != pc[b].mode ? pc[a].mode < pc[b].mode : task_len(a) > task_len(b);
+    if (pc[a].mode != pc[b].mode) return pc[a].mode < pc[b].mode;
+    if (pc[a].NH != pc[b].NH) return pc[a].NH > pc[b].NH;
+    return task_len(a) > task_len(b);
   });
-  LHC_CHECK_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * (size_t)nlaunch, st));
-  for (int c0 = 0, l = 0; c0 < n; ++l) {
-    const int mode = pc[order[c0]].mode;
+  if (nper > 0) LHC_CHECK_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * (size_t)nlaunch, st));
+  for (int c0 = 0, l = 0; c0 < nper; ++l) {
+    const int mode = pc[order[c0]].mode, nh = pc[order[c0]].NH;
     int c1 = c0;
-    while (c1 < n && c1 - c0 < kMaxBatch && pc[order[c1]].mode == mode) ++c1;
+    while (c1 < nper && c1 - c0 < kMaxBatch && pc[order[c1]].mode == mode && pc[order[c1]].NH == nh) ++c1;
     std::unique_ptr<BatchParams> bpp(new BatchParams());   // 25 KB: kept off the stack
     BatchParams &bp = *bpp;
     bp.n = c1 - c0;
@@ -1534,11 +1595,11 @@ int run_batch_mixed(lhc_ctx ctx, const std::vector<BatchCall> &calls, cudaStream
     ProfScope ps(ctx, st, LHC_KERNEL_FUSED, w);
     const int nctas = std::min(bp.first[bp.n], ctx->num_sms);
     if (mode == 0)
-      LHC_TRY(launch_persistent<0>(bp, nctas, st));
+      LHC_TRY(launch_persistent<0>(nh, bp, nctas, st));
     else if (mode == 1)
-      LHC_TRY(launch_persistent<1>(bp, nctas, st));
+      LHC_TRY(launch_persistent<1>(nh, bp, nctas, st));
     else
-      LHC_TRY(launch_persistent<2>(bp, nctas, st));
+      LHC_TRY(launch_persistent<2>(nh, bp, nctas, st));
     c0 = c1;
   }
   for (int c = 0; c < n; ++c) LHC_TRY(finish_chunk(ctx, pc[c], st));

@@ -252,8 +252,8 @@ class Context:
         return ms.value, n.value, w.value
 
     def batch(self, calls, stream=None):
-        """Mixed-precision calls in one persistent fused launch per part kind (up to 64
-        calls per launch, any mix of momentum-chunk widths): each call a dict with
+        """Mixed-precision calls in one persistent fused launch per part kind and
+        momentum-chunk width (up to 64 calls per launch): each call a dict with
         part ("ins", "spec" or "baryon"), S, vec, optional GB, t_lo, t_hi (t_lo = t_hi =
         t_sink for spectators), r, k and optional out (device tensors).  Returns the
         outputs, bitwise those of the same calls made one by one in "gemm" projection mode

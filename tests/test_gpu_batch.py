@@ -1,5 +1,6 @@
 """Batched calls (lhc_batch): many mixed-precision insertion and spectator calls with
-uneven momentum sets, lattices and parts in one persistent fused launch per part kind;
+uneven momentum sets, lattices and parts in one persistent fused launch per part kind and
+momentum-chunk width;
 the results must equal, bit for bit, those of the same calls made one by one with the
 tensor-core projection, also when replayed from a CUDA graph, and the oracle within the
 mixed tolerance."""
@@ -52,10 +53,10 @@ def test_batch_equals_single_calls():
 
 
 def test_persistent_batch_replayed_from_a_cuda_graph():
-    """One persistent launch per part kind over calls with five momentum-chunk widths
-    (7, 33, 57, 93 and 147 momenta: 4, 17, 29, 47 and 74 representatives, chunks of 8,
-    24, 32, 48 and two of 40), two lattices and both input precisions, captured in a CUDA
-    graph and replayed:
+    """Persistent launches (one per part kind and chunk width) over calls with five
+    momentum-chunk widths (7, 33, 57, 93 and 147 momenta: 4, 17, 29, 47 and 74
+    representatives, chunks of 8, 24, 32, 48 and two of 40), two lattices and both input
+    precisions, captured in a CUDA graph and replayed:
     the replay equals the same calls made one by one bit for bit, and the oracle within
     the mixed tolerance."""
     from paper_1711_02384_gb300 import lhc
@@ -107,3 +108,30 @@ def test_persistent_batch_replayed_from_a_cuda_graph():
     assert CS.block_err(outs[21].cpu().numpy(), c.ref_spectator_baryon(1), 1) < CS.MIXED_TOL
     c = cases[0]
     assert CS.block_err(outs[1].cpu().numpy(), c.ref_spectator_meson(1), 1) < CS.MIXED_TOL
+
+
+def test_batch_with_a_call_that_fills_the_gpu():
+    """A call whose own launch fills several waves of the GPU (16^3, 32 noises, 8 slices)
+    keeps its own fused launch inside the batch; the small calls beside it share a
+    persistent launch.  Every output equals the same call made alone, bit for bit."""
+    from paper_1711_02384_gb300 import lhc, inputs
+    dev = torch.device("cuda", 0)
+    L, T, NR = 16, 8, 32
+    V3 = L ** 3
+    S = torch.from_numpy(inputs.propagator(2520, L, T).astype(np.complex64)).to(dev)
+    psi = torch.from_numpy(inputs.solutions(2521, L, T, NR).astype(np.complex64)).to(dev)
+    eta = torch.from_numpy(inputs.noise(2522, L, 4, 3).astype(np.complex64)).to(dev)
+    k93, k7 = lhc.momenta(8), lhc.momenta(1)
+    calls = [dict(part="ins", S=S, vec=psi, t_lo=0, t_hi=7, r=(1, 2, 3, 0), k=k93),
+             dict(part="spec", S=S, vec=eta, t_lo=3, t_hi=3, r=(1, 2, 3, 0), k=k7),
+             dict(part="spec", S=S, vec=eta, t_lo=3, t_hi=3, r=(0, 5, 1, 0), k=k93)]
+    with lhc.Context(0) as ctx:
+        ctx.set_projection("gemm")
+        got = ctx.batch(calls)
+        ref = [ctx.insertion(S, psi, 0, 7, calls[0]["r"], k93, prec="mixed"),
+               ctx.spectator(S, eta, 3, calls[1]["r"], k7, prec="mixed"),
+               ctx.spectator(S, eta, 3, calls[2]["r"], k93, prec="mixed")]
+        ctx.sync()
+    assert got[0].shape == (8, len(k93), NR, 192)
+    for g, r in zip(got, ref):
+        assert torch.equal(g, r)
