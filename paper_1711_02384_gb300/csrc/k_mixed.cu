@@ -63,13 +63,24 @@ constexpr int ASTAGE = 4 * ATILE;        // Ur hi, Ur lo, Ui hi, Ui lo
 constexpr int NSTAGE = 6;                // A/B ring (freed by the MMA), used as pairs of stages
 constexpr int NPAIR = NSTAGE / 2;
 constexpr int NIN = 6;                   // input ring (freed by the producers)
-constexpr int NPK = 3;                   // k-steps in flight in the producers (4 warps each)
-// warp roles: 0 phase-tile loader, 1 MMA issue, 2-9 drain, 10-21 producers, 22 input loader
-constexpr int kWarps = 23;
+constexpr int NPK = 4;                   // k-steps in flight in the producers (4 warps each)
+// Warp roles, in warpgroups of four warps (a register budget is set per warpgroup):
+//   warpgroup 0: warp 0 phase-tile loader, 1 MMA issue, 2 input loader, 3 idle
+//   warpgroups 1-2 (warps 4-11): drain; warp w reads the tensor-memory lanes 32 (w % 4) ..
+//   warpgroups 3-6 (warps 12-27): producers, four per k-step, one on each SM sub-partition
+// so every sub-partition holds four producer warps, two drain warps and one other.
+constexpr int kWarps = 28;
 constexpr int kThreads = kWarps * 32;
-constexpr int kDrainWarp0 = 2;
-constexpr int kProdWarp0 = 10;
-constexpr int kInWarp = kProdWarp0 + 4 * NPK;
+constexpr int kInWarp = 2;
+constexpr int kDrainWarp0 = 4;
+constexpr int kProdWarp0 = 12;
+// Registers per thread: 72 at launch (65536 / 896, rounded down to a multiple of 8); the
+// producers then take 80 and warpgroup 0, whose roles are single threads, gives 48 back:
+// 4*32*24 + 8*32*72 + 16*32*80 = 62464 <= 896*72 = 64512.
+constexpr uint32_t kRegLaunch = 72, kRegRole = 24, kRegProd = 80;
+static_assert(kRegLaunch * kThreads <= 65536 &&
+                  kRegRole * 128 + kRegLaunch * 256 + kRegProd * 512 <= kRegLaunch * kThreads,
+              "register budgets of the warpgroups");
 constexpr uint32_t kTmemCols = 512;
 
 // Threads per block of the staging, maximum and diquark kernels (memory- or
@@ -311,6 +322,9 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
   __syncthreads();
   tc::tc_fence_after();
 
+  if (warp < 4) {
+  // warpgroup 0: single-thread roles with a small register budget
+  tc::reg_dec<kRegRole>();
   if (warp == 0) {
     // ---------------------------------------------------- phase tiles (A/B ring)
     if (lane == 0 && nk > 0) {
@@ -408,6 +422,8 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
       while (!tc::mbar_try_wait(done, 0) && clock64() - t0 < tc::kSpinLimit) {
       }
     }
+  }
+  tc::reg_inc<kRegLaunch>();
   } else if (warp < kProdWarp0) {
     // ---------------------------------------------------- drain (quadrant = warp % 4)
     const int qd = warp & 3, h = (warp - kDrainWarp0) >> 2;
@@ -500,6 +516,7 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
     }
   } else {
     // ---------------------------------------------------- producers
+    tc::reg_inc<kRegProd>();
     // Producer warp pw computes k-step kofs of every NPK k-steps for 4 of its 16 sites
     // (quarter wq), all 128 rows (s, noise, spin): lane = (column sp in 0..7, site
     // xq in 0..3) handles the columns s = sp and sp + 8 for 8 (noise, spin) rows.  A
@@ -517,16 +534,15 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
       const int sv = s0 + sp + 8 * jx;
       mo[jx] = MODE == 2 ? x * 48 + sp + 8 * jx : ((x * 2 + (sv / 12 - bt0)) * 3) * 12 + sv % 12;
     }
-    static_assert(NIN == 2 * NPK && NSTAGE == 2 * NPK, "stage indices from the iteration count");
+    static_assert(NIN == NSTAGE && NSTAGE % 2 == 0, "one stage index for the input and A/B rings");
     // The loop is compiled twice: with the split scale and, for unit-scale data (e = 0),
     // without its multiplications.
     auto produce = [&](auto scaled) {
       for (int it = 0; it < nit; ++it) {
         const int kstep = NPK * it + kofs;
         if (kstep >= nk) break;
-        // k-step kstep = NPK it + kofs uses input stage and A stage kstep % 6 = kofs + 3 (it & 1),
-        // in round kstep / 6 = it / 2
-        const int si = kofs + NPK * (it & 1), ui = it >> 1;
+        // k-step kstep uses input stage and A stage kstep % NSTAGE, in round kstep / NSTAGE
+        const int si = kstep % NSTAGE, ui = kstep / NSTAGE;
         // The first warp of the group waits for the input stage and, after the first round,
         // for the MMA to be done with the A stage (its k-step NSTAGE back); the four warps
         // block on the group's named barrier and follow its verdict together, so a wait
@@ -623,6 +639,7 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
       produce(std::false_type{});
     else
       produce(std::true_type{});
+    tc::reg_dec<kRegLaunch>();
   }
   tc::tc_fence_before();
   __syncthreads();
