@@ -368,6 +368,31 @@ typedef struct {
  * paper has no counterpart: it ran one contraction at a time. */
 int lhc_batch(lhc_ctx ctx, const lhc_call *calls, int ncalls, void *stream);
 
+/* ---- Staged propagator slices (mixed path).
+ * A mixed-precision call with complex128 inputs first narrows them to complex64 (the
+ * contraction runs in FP32). Calls that share a propagator (the insertion calls of
+ * several sink times over slices t0..t_f, the spectators on their sink slices) would each
+ * narrow it again. lhc_prop_stage narrows slices t_lo..t_hi (mod T) of the complex128
+ * propagator S [T][L^3][12][12] once, into a complex64 copy held by the library (counted
+ * against ctx's HBM budget) together with each slice's largest |re| or |im|. Every later
+ * LHC_MIXED insertion or meson spectator call, of any context on the same device, whose
+ * propagator slices are consecutive slices of one staged range reads the copy instead of
+ * narrowing S; its results are bitwise the same. Other calls (baryon spectators, FP64,
+ * complex64 inputs, host buffers, slices outside the range) are not affected.
+ * The caller must not change the staged slices of S while they are staged, or must stage
+ * them again (staging the same range of the same S again rewrites the copy in stream
+ * order, with no allocation); the staging context must outlive the calls that read the
+ * copy. The copy is found by S's address: S must stay allocated while staged (unstage it,
+ * or destroy the staging context, before freeing it), or memory later allocated at that
+ * address would be read through the stale copy. Asynchronous on `stream`: calls on other
+ * streams must wait for it (an event).
+ * Staging another range of the same S, and lhc_prop_unstage, synchronize the device
+ * before the old copy is freed. Errors: LHC_EINVAL (not complex128, not device memory,
+ * bad range), LHC_ENOTFOUND (unstage of a pointer not staged). The paper has no
+ * counterpart: its propagators stay in double precision. */
+int lhc_prop_stage(lhc_ctx ctx, const lhc_lattice *lat, const void *S, int t_lo, int t_hi, void *stream);
+int lhc_prop_unstage(lhc_ctx ctx, const void *S);
+
 /* ---- Momentum projection by discrete Fourier transform (all-momenta mode).
  * The projection of Eqs. 9 and 10 over every momentum of a slice is a 3-D discrete
  * Fourier transform of the contracted values. In this mode the library contracts and

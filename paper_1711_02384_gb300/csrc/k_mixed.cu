@@ -63,24 +63,13 @@ constexpr int ASTAGE = 4 * ATILE;        // Ur hi, Ur lo, Ui hi, Ui lo
 constexpr int NSTAGE = 6;                // A/B ring (freed by the MMA), used as pairs of stages
 constexpr int NPAIR = NSTAGE / 2;
 constexpr int NIN = 6;                   // input ring (freed by the producers)
-constexpr int NPK = 4;                   // k-steps in flight in the producers (4 warps each)
-// Warp roles, in warpgroups of four warps (a register budget is set per warpgroup):
-//   warpgroup 0: warp 0 phase-tile loader, 1 MMA issue, 2 input loader, 3 idle
-//   warpgroups 1-2 (warps 4-11): drain; warp w reads the tensor-memory lanes 32 (w % 4) ..
-//   warpgroups 3-6 (warps 12-27): producers, four per k-step, one on each SM sub-partition
-// so every sub-partition holds four producer warps, two drain warps and one other.
-constexpr int kWarps = 28;
+constexpr int NPK = 3;                   // k-steps in flight in the producers (4 warps each)
+// warp roles: 0 phase-tile loader, 1 MMA issue, 2-9 drain, 10-21 producers, 22 input loader
+constexpr int kWarps = 23;
 constexpr int kThreads = kWarps * 32;
-constexpr int kInWarp = 2;
-constexpr int kDrainWarp0 = 4;
-constexpr int kProdWarp0 = 12;
-// Registers per thread: 72 at launch (65536 / 896, rounded down to a multiple of 8); the
-// producers then take 80 and warpgroup 0, whose roles are single threads, gives 48 back:
-// 4*32*24 + 8*32*72 + 16*32*80 = 62464 <= 896*72 = 64512.
-constexpr uint32_t kRegLaunch = 72, kRegRole = 24, kRegProd = 80;
-static_assert(kRegLaunch * kThreads <= 65536 &&
-                  kRegRole * 128 + kRegLaunch * 256 + kRegProd * 512 <= kRegLaunch * kThreads,
-              "register budgets of the warpgroups");
+constexpr int kDrainWarp0 = 2;
+constexpr int kProdWarp0 = 10;
+constexpr int kInWarp = kProdWarp0 + 4 * NPK;
 constexpr uint32_t kTmemCols = 512;
 
 // Threads per block of the staging, maximum and diquark kernels (memory- or
@@ -322,9 +311,6 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
   __syncthreads();
   tc::tc_fence_after();
 
-  if (warp < 4) {
-  // warpgroup 0: single-thread roles with a small register budget
-  tc::reg_dec<kRegRole>();
   if (warp == 0) {
     // ---------------------------------------------------- phase tiles (A/B ring)
     if (lane == 0 && nk > 0) {
@@ -422,8 +408,6 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
       while (!tc::mbar_try_wait(done, 0) && clock64() - t0 < tc::kSpinLimit) {
       }
     }
-  }
-  tc::reg_inc<kRegLaunch>();
   } else if (warp < kProdWarp0) {
     // ---------------------------------------------------- drain (quadrant = warp % 4)
     const int qd = warp & 3, h = (warp - kDrainWarp0) >> 2;
@@ -516,7 +500,6 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
     }
   } else {
     // ---------------------------------------------------- producers
-    tc::reg_inc<kRegProd>();
     // Producer warp pw computes k-step kofs of every NPK k-steps for 4 of its 16 sites
     // (quarter wq), all 128 rows (s, noise, spin): lane = (column sp in 0..7, site
     // xq in 0..3) handles the columns s = sp and sp + 8 for 8 (noise, spin) rows.  A
@@ -534,15 +517,16 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
       const int sv = s0 + sp + 8 * jx;
       mo[jx] = MODE == 2 ? x * 48 + sp + 8 * jx : ((x * 2 + (sv / 12 - bt0)) * 3) * 12 + sv % 12;
     }
-    static_assert(NIN == NSTAGE && NSTAGE % 2 == 0, "one stage index for the input and A/B rings");
+    static_assert(NIN == 2 * NPK && NSTAGE == 2 * NPK, "stage indices from the iteration count");
     // The loop is compiled twice: with the split scale and, for unit-scale data (e = 0),
     // without its multiplications.
     auto produce = [&](auto scaled) {
       for (int it = 0; it < nit; ++it) {
         const int kstep = NPK * it + kofs;
         if (kstep >= nk) break;
-        // k-step kstep uses input stage and A stage kstep % NSTAGE, in round kstep / NSTAGE
-        const int si = kstep % NSTAGE, ui = kstep / NSTAGE;
+        // k-step kstep = NPK it + kofs uses input stage and A stage kstep % 6 = kofs + 3 (it & 1),
+        // in round kstep / 6 = it / 2
+        const int si = kofs + NPK * (it & 1), ui = it >> 1;
         // The first warp of the group waits for the input stage and, after the first round,
         // for the MMA to be done with the A stage (its k-step NSTAGE back); the four warps
         // block on the group's named barrier and follow its verdict together, so a wait
@@ -639,7 +623,6 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
       produce(std::false_type{});
     else
       produce(std::true_type{});
-    tc::reg_dec<kRegLaunch>();
   }
   tc::tc_fence_before();
   __syncthreads();
@@ -855,6 +838,7 @@ struct NarrowParams {
   float2 *Sst, *SBst, *Vst;
   unsigned *maxS, *maxV;   // per slice: largest |re| or |im| of the propagator and of the vectors
   int nb, V3;
+  int withS;           // 0: the propagator slices are staged already (only the vectors here)
 };
 
 // Largest |re| or |im| over a block's values, folded into *m with an atomic max on the
@@ -887,21 +871,22 @@ __global__ void __launch_bounds__(kSmallThreads) narrow_c128(NarrowParams p) {
   float2 *dst;
   size_t n;
   unsigned *mx;
-  if (b < (size_t)p.nb * cS) {
+  const size_t nSb = p.withS ? (size_t)p.nb * cS : 0;
+  if (b < nSb) {
     const int j = (int)(b / cS);
     src = static_cast<const double2 *>(p.slices[j].S);
     dst = p.Sst + (size_t)j * nS;
     n = nS;
     b %= cS;
     mx = p.maxS + j;
-  } else if (p.SB && b < (size_t)(p.nb + 1) * cS) {
+  } else if (p.SB && b < nSb + cS) {
     src = static_cast<const double2 *>(p.SB);
     dst = p.SBst;
     n = nS;
-    b -= (size_t)p.nb * cS;
+    b -= nSb;
     mx = nullptr;   // the baryon's matrix operand is the diquark, bounded separately
   } else {
-    b -= (size_t)(p.nb + (p.SB ? 1 : 0)) * cS;
+    b -= nSb + (p.SB ? cS : 0);
     const size_t iv = b / cV;   // noise * nb + slice
     const int i = (int)(iv / p.nb), j = (int)(iv % p.nb);
     src = static_cast<const double2 *>(p.slices[j].vec) + (size_t)i * p.vec_stride;
@@ -1169,6 +1154,140 @@ static int slice_coords(const void *const *ptrs, int nb, size_t slice_bytes, con
   return LHC_OK;
 }
 
+// ---------------------------------------------------------------- staged propagators
+// Complex64 copies of complex128 propagator slices made once by lhc_prop_stage and read by
+// every later mixed call whose propagator slices all lie in one staged range (any context
+// on the device): the insertion calls of several sink times and the spectators on their
+// sink slices share the propagator, and each would otherwise narrow it again.  Process-
+// wide, keyed by the device and the caller's base pointer.
+struct StagedProp {
+  int device = 0, V3 = 0, T = 0, t_lo = 0, nt = 0;
+  const char *base = nullptr;   // the caller's propagator [T][V3][144] complex128
+  DevBuf copy, maxS;            // [nt][V3][144] complex64; [nt] largest |re| or |im| (float bits)
+  lhc_ctx owner = nullptr;      // the context whose budget holds the copy
+};
+static std::mutex g_staged_mu;
+static std::vector<StagedProp> g_staged;
+
+// The staged copy of slices jobs[0..nb) if they are consecutive slices of one staged range
+// (in the range's order), else no copy.
+struct StagedView {
+  const float2 *copy = nullptr;
+  const unsigned *maxS = nullptr;
+  int idx0 = 0, nt = 0;
+};
+static StagedView find_staged(int device, const SliceJob *jobs, int nb) {
+  StagedView v;
+  const size_t slice = (size_t)jobs[0].V3 * 144 * sizeof(double2);
+  std::lock_guard<std::mutex> g(g_staged_mu);
+  for (const StagedProp &e : g_staged) {
+    if (e.device != device || e.V3 != jobs[0].V3) continue;
+    const char *p0 = static_cast<const char *>(jobs[0].S);
+    if (p0 < e.base || (size_t)(p0 - e.base) % slice != 0 || (size_t)(p0 - e.base) / slice >= (size_t)e.T) continue;
+    const int t0 = (int)((size_t)(p0 - e.base) / slice);
+    const int idx0 = ((t0 - e.t_lo) % e.T + e.T) % e.T;
+    if (idx0 + nb > e.nt) continue;
+    bool ok = true;
+    for (int j = 1; j < nb && ok; ++j)
+      ok = jobs[j].S == e.base + (size_t)((e.t_lo + idx0 + j) % e.T) * slice;
+    if (!ok) continue;
+    v.copy = static_cast<const float2 *>(e.copy.p);
+    v.maxS = static_cast<const unsigned *>(e.maxS.p);
+    v.idx0 = idx0;
+    v.nt = e.nt;
+    return v;
+  }
+  return v;
+}
+
+int stage_propagator(lhc_ctx ctx, const lhc_lattice *lat, const void *S, int t_lo, int nt, cudaStream_t st) {
+  const int V3 = lat->L * lat->L * lat->L, T = lat->T;
+  const char *base = static_cast<const char *>(S);
+  std::lock_guard<std::mutex> g(g_staged_mu);
+  StagedProp *e = nullptr;
+  for (StagedProp &x : g_staged)
+    if (x.device == ctx->device && x.base == base) e = &x;
+  if (e && (e->V3 != V3 || e->T != T || e->t_lo != t_lo || e->nt != nt || e->owner != ctx)) {
+    // another range of the same tensor: the old copy goes (after all work that may read it)
+    LHC_CHECK_CUDA(cudaDeviceSynchronize());
+    dev_free(e->owner, e->copy);
+    dev_free(e->owner, e->maxS);
+    g_staged.erase(g_staged.begin() + (e - g_staged.data()));
+    e = nullptr;
+  }
+  if (!e) {
+    StagedProp x;
+    x.device = ctx->device;
+    x.V3 = V3;
+    x.T = T;
+    x.t_lo = t_lo;
+    x.nt = nt;
+    x.base = base;
+    x.owner = ctx;
+    LHC_TRY(dev_alloc(ctx, x.copy, (size_t)nt * V3 * 144 * sizeof(float2)));
+    int s = dev_alloc(ctx, x.maxS, (size_t)nt * sizeof(unsigned));
+    if (s != LHC_OK) {
+      dev_free(ctx, x.copy);
+      return s;
+    }
+    g_staged.push_back(x);
+    e = &g_staged.back();
+  }
+  // narrow the slices (in stream order: calls that read the copy must follow on `st`, or
+  // wait for it)
+  LHC_CHECK_CUDA(cudaMemsetAsync(e->maxS.p, 0, (size_t)nt * sizeof(unsigned), st));
+  const size_t cS = ((size_t)V3 * 144 + kNarrowChunk - 1) / kNarrowChunk;
+  const size_t slice = (size_t)V3 * 144 * sizeof(double2);
+  for (int j0 = 0; j0 < nt; j0 += kMaxSlices) {
+    NarrowParams np{};
+    np.nb = std::min(kMaxSlices, nt - j0);
+    for (int j = 0; j < np.nb; ++j) np.slices[j] = SlicePtrs{base + (size_t)((t_lo + j0 + j) % T) * slice, nullptr};
+    np.SB = nullptr;
+    np.vec_stride = 0;
+    np.Sst = static_cast<float2 *>(e->copy.p) + (size_t)j0 * V3 * 144;
+    np.SBst = np.Vst = nullptr;
+    np.maxS = static_cast<unsigned *>(e->maxS.p) + j0;
+    np.maxV = nullptr;
+    np.V3 = V3;
+    np.withS = 1;
+    ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT, (double)np.nb * V3 * 144.0 * 24);
+    narrow_c128<<<(unsigned)(np.nb * cS), kSmallThreads, 0, st>>>(np);
+    note_launch();
+  }
+  LHC_CHECK_CUDA(cudaGetLastError());
+  return LHC_OK;
+}
+
+int unstage_propagator(lhc_ctx ctx, const void *S) {
+  std::lock_guard<std::mutex> g(g_staged_mu);
+  for (size_t i = 0; i < g_staged.size(); ++i) {
+    StagedProp &e = g_staged[i];
+    if (e.device == ctx->device && e.base == static_cast<const char *>(S)) {
+      LHC_CHECK_CUDA(cudaDeviceSynchronize());   // nothing in flight may still read the copy
+      dev_free(e.owner, e.copy);
+      dev_free(e.owner, e.maxS);
+      g_staged.erase(g_staged.begin() + i);
+      return LHC_OK;
+    }
+  }
+  set_error("lhc_prop_unstage: this propagator is not staged on device %d", ctx->device);
+  return LHC_ENOTFOUND;
+}
+
+// The copies a context holds go with it (its destruction has synchronized the device).
+void release_staged(lhc_ctx ctx) {
+  std::lock_guard<std::mutex> g(g_staged_mu);
+  for (size_t i = 0; i < g_staged.size();) {
+    if (g_staged[i].owner == ctx) {
+      dev_free(ctx, g_staged[i].copy);
+      dev_free(ctx, g_staged[i].maxS);
+      g_staged.erase(g_staged.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- one call, in steps
 // A mixed call runs, per chunk of at most kMaxSlices slices: sizing, prepare (operand
 // maxima, the complex128 narrowing or the complex64 maximum pass, the baryon diquark, the
@@ -1258,8 +1377,11 @@ static int prepare_chunk(lhc_ctx ctx, const SliceJob *jobs, int nb, int nq, int 
   LHC_CHECK_CUDA(cudaMemsetAsync(maxS, 0, (2 * kMaxSlices + 1) * sizeof(unsigned), st));
   const size_t cS = ((size_t)V3 * 144 + kNarrowChunk - 1) / kNarrowChunk;
   const size_t cV = ((size_t)V3 * 12 + kNarrowChunk - 1) / kNarrowChunk;
+  // propagator slices staged by lhc_prop_stage replace the narrowing of the propagator
+  const StagedView sv = narrow && !baryon ? find_staged(ctx->device, jobs, nb) : StagedView{};
   if (narrow) {
     NarrowParams np;
+    np.withS = sv.copy ? 0 : 1;
     for (int j = 0; j < nb; ++j) np.slices[j] = SlicePtrs{jobs[j].S, jobs[j].vec};
     np.SB = baryon ? j0.SB : nullptr;
     np.vec_stride = j0.vec_stride;
@@ -1270,8 +1392,9 @@ static int prepare_chunk(lhc_ctx ctx, const SliceJob *jobs, int nb, int nq, int 
     np.maxV = maxV;
     np.nb = nb;
     np.V3 = V3;
-    ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT, (double)nb * V3 * ((baryon ? 288.0 : 144.0) + 12.0 * n_r) * 24);
-    const size_t blocks = (size_t)(nb + (baryon ? 1 : 0)) * cS + (size_t)n_r * nb * cV;
+    ProfScope ps(ctx, st, LHC_KERNEL_CONTRACT,
+                 (double)nb * V3 * ((baryon ? 288.0 : sv.copy ? 0.0 : 144.0) + 12.0 * n_r) * 24);
+    const size_t blocks = (size_t)((sv.copy ? 0 : nb) + (baryon ? 1 : 0)) * cS + (size_t)n_r * nb * cV;
     narrow_c128<<<(unsigned)blocks, kSmallThreads, 0, st>>>(np);
     note_launch();
   } else {
@@ -1295,10 +1418,15 @@ static int prepare_chunk(lhc_ctx ctx, const SliceJob *jobs, int nb, int nq, int 
   int Tm, Tv;
   size_t vstride_bytes;
   if (narrow) {
-    Mbase = ws + lay.off_s;
+    Mbase = sv.copy ? reinterpret_cast<const char *>(sv.copy) : ws + lay.off_s;
     Vbase = ws + lay.off_v;
-    for (int j = 0; j < nb; ++j) fp.tM[j] = fp.tV[j] = j;
-    Tm = Tv = nb;
+    for (int j = 0; j < nb; ++j) {
+      fp.tM[j] = sv.copy ? sv.idx0 + j : j;
+      fp.tV[j] = j;
+    }
+    Tm = sv.copy ? sv.nt : nb;
+    Tv = nb;
+    if (sv.copy) fp.c.maxM = sv.maxS + sv.idx0;   // the slice maxima were taken when staging
     vstride_bytes = (size_t)nb * V3 * 12 * sizeof(float2);
   } else {
     const void *mp[kMaxSlices], *vp[kMaxSlices];

@@ -458,6 +458,7 @@ int lhc_destroy(lhc_ctx ctx) {
   lhc_serve_stop(ctx);
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
+  release_staged(ctx);
   dev_free(ctx, ctx->ws);
   stage_destroy(ctx);
   if (ctx->dev_err) cudaFree(ctx->dev_err);
@@ -836,6 +837,28 @@ int lhc_combine_open_baryon(lhc_ctx ctx, const void *spec, int np, const void *i
                             void *stream) {
   return combine_open(ctx, LHC_BARYON, "lhc_combine_open_baryon", spec, np, ins, nq, n_r, nt, wsnk, ngs, ins_g, ngi,
                       prec, out, stream);
+}
+
+int lhc_prop_stage(lhc_ctx ctx, const lhc_lattice *lat, const void *S, int t_lo, int t_hi, void *stream) {
+  if (!ctx) return fail(LHC_EINVAL, "ctx is NULL");
+  LHC_TRY(check_lattice(lat));
+  if (lat->dtype != LHC_C128) return fail(LHC_EINVAL, "lhc_prop_stage: complex128 propagators only");
+  if (!S || ((uintptr_t)S & 15)) return fail(LHC_EINVAL, "lhc_prop_stage: S must be 16-byte aligned");
+  if (!is_device_ptr(S)) return fail(LHC_EINVAL, "lhc_prop_stage: S must be device memory");
+  if (t_hi < t_lo || t_hi - t_lo >= lat->T) return fail(LHC_EINVAL, "bad slice range %d..%d", t_lo, t_hi);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> g(ctx->mu);
+  LHC_TRY(begin_call(ctx, st));
+  int s = stage_propagator(ctx, lat, S, ((t_lo % lat->T) + lat->T) % lat->T, t_hi - t_lo + 1, st);
+  int e = end_call(ctx, st);
+  return s != LHC_OK ? s : e;
+}
+
+int lhc_prop_unstage(lhc_ctx ctx, const void *S) {
+  if (!ctx || !S) return fail(LHC_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> g(ctx->mu);
+  LHC_CHECK_CUDA(cudaSetDevice(ctx->device));
+  return unstage_propagator(ctx, S);
 }
 
 int lhc_set_projection(lhc_ctx ctx, int mode) {

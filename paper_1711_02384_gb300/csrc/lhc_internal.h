@@ -193,6 +193,11 @@ int run_part_mixed(lhc_ctx ctx, const SliceJob *jobs, int nt, const int *k, int 
 
 size_t mixed_call_bytes(Part part, int dtype, int V3, int n_r, int nt, int nq);
 
+// complex64 copies of complex128 propagator slices shared by later mixed calls (k_mixed.cu)
+int stage_propagator(lhc_ctx ctx, const lhc_lattice *lat, const void *S, int t_lo, int nt, cudaStream_t st);
+int unstage_propagator(lhc_ctx ctx, const void *S);
+void release_staged(lhc_ctx ctx);   // the copies the context holds (the device is synchronized)
+
 // a batch of mixed calls with one fused launch per part kind and chunk width (k_mixed.cu)
 struct BatchCall {
   std::vector<SliceJob> jobs;

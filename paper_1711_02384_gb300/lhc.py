@@ -111,11 +111,13 @@ def lib():
         L.lhc_combine_open.argtypes = [vp, vp, ci, vp, ci, ci, ci, vp, ci, vp, ci, ci, vp, vp]
         L.lhc_combine_open_baryon.argtypes = [vp, vp, ci, vp, ci, ci, ci, vp, ci, vp, ci, ci, vp, vp]
         L.lhc_set_projection.argtypes = [vp, ci]
+        L.lhc_prop_stage.argtypes = [vp, lp, vp, ci, ci, vp]
+        L.lhc_prop_unstage.argtypes = [vp, vp]
         L.lhc_batch.argtypes = [vp, ctypes.POINTER(Call), ci, vp]
         L.lhc_set_tuning.argtypes = [vp, ci, ctypes.c_char_p]
         L.lhc_tuning_table.argtypes = [ip, ci, ip]
         L.lhc_tuning_load.argtypes = [ctypes.c_char_p, ip]
-        for name in ("lhc_batch", "lhc_combine_open", "lhc_combine_open_baryon", "lhc_set_projection", "lhc_wilson_apply", "lhc_wilson_solve", "lhc_set_tuning", "lhc_tuning_table", "lhc_tuning_load",
+        for name in ("lhc_prop_stage", "lhc_prop_unstage", "lhc_batch", "lhc_combine_open", "lhc_combine_open_baryon", "lhc_set_projection", "lhc_wilson_apply", "lhc_wilson_solve", "lhc_set_tuning", "lhc_tuning_table", "lhc_tuning_load",
                      "lhc_create", "lhc_destroy", "lhc_set_gamma5", "lhc_momenta", "lhc_insertion",
                      "lhc_spectator", "lhc_combine", "lhc_profile", "lhc_profile_read", "lhc_sync", "lhc_release_workspace",
                      "lhc_selftest_timeout", "lhc_selftest_flag", "lhc_serve_start", "lhc_serve_stop", "lhc_prop_register",
@@ -210,6 +212,7 @@ class Context:
 
     def __init__(self, device: int = 0, hbm_budget: int = 0, gamma5=(1, 1, -1, -1)):
         self._h = ctypes.c_void_p()
+        self._staged = {}   # staged propagators by address, kept alive while staged
         _check(lib().lhc_create(ctypes.byref(self._h), int(device), int(hbm_budget)))
         self.device = device
         self.set_gamma5(gamma5)
@@ -218,6 +221,7 @@ class Context:
         if self._h:
             lib().lhc_destroy(self._h)
             self._h = ctypes.c_void_p()
+        self._staged.clear()
 
     def __del__(self):
         try:
@@ -286,6 +290,21 @@ class Context:
             a.k = kp
         _check(lib().lhc_batch(self._h, arr, len(calls), _stream(calls[0]["S"], stream)))
         return outs
+
+    def stage_propagator(self, S, t_lo, t_hi, stream=None):
+        """Narrow slices t_lo..t_hi of the complex128 propagator S [T][V3][12][12] (device)
+        once; later mixed insertion and meson spectator calls on those slices read the
+        copy (bitwise the same results).  S must not change while staged (or is staged
+        again after a change).  The copy is found by S's address, so the context keeps S
+        alive until unstage_propagator(S) or close()."""
+        T, V3 = S.shape[0], S.shape[1]
+        lat = Lattice(_L_of(V3), T, _dtype_code(S))
+        _check(lib().lhc_prop_stage(self._h, ctypes.byref(lat), _ptr(S), int(t_lo), int(t_hi), _stream(S, stream)))
+        self._staged[S.data_ptr()] = S
+
+    def unstage_propagator(self, S):
+        _check(lib().lhc_prop_unstage(self._h, _ptr(S)))
+        self._staged.pop(S.data_ptr(), None)
 
     def set_projection(self, mode: str):
         """Momentum projection of single calls: "auto" (a DFT over the slice when
