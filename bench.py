@@ -108,6 +108,28 @@ def nvsmi_id(local):
     return str(local)
 
 
+def host_link(dev, stream, h2d_bytes, d2h_bytes, mib=512, reps=3):
+    """This box's pinned-copy rates in each direction (CUDA events around `reps` copies of a
+    `mib` MiB buffer on `stream`), measured right after the end-to-end steps, and the floor
+    that they put on one step's copies: both directions overlap, so the slower of the two."""
+    import torch
+    h = torch.empty(mib << 20, dtype=torch.uint8).pin_memory()
+    d = torch.empty(mib << 20, dtype=torch.uint8, device=dev)
+    rate = {}
+    for name, dst, src in (("h2d_gbs", d, h), ("d2h_gbs", h, d)):
+        with torch.cuda.stream(stream):
+            dst.copy_(src, non_blocking=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+        e1.synchronize()
+        rate[name] = reps * (mib << 20) / (e0.elapsed_time(e1) * 1e6)
+    floor = max(h2d_bytes / rate["h2d_gbs"], d2h_bytes / rate["d2h_gbs"]) / 1e6
+    return {"h2d_gbs": rate["h2d_gbs"], "d2h_gbs": rate["d2h_gbs"], "floor_ms": floor}
+
+
 class Clocks:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -447,11 +469,13 @@ def main():
         h2d += sum(N_R * (tf + 1) * V3 * 12 * 16 + N_R * V3 * 12 * 16 for tf in TFS)   # psi slices, eta
         d2h = sum(((tf + 1) * nq * N_R * 192 + nq * N_R * 192) * 16 for tf in TFS)     # open-spin outputs
         d2h += sum((tf + 1) * 16 * nq * nq * 16 for tf in TFS)                       # correlators
+        link = host_link(dev, side, h2d, d2h)
         e2e = {"value": upstep / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": dt * 1e3,
                "pattern": "propagator slices uploaded once per step (double-buffered, steps overlap); "
                           "solutions and noise as pinned host "
-                          "buffers through the library; open-spin outputs and correlators read back"}
+                          "buffers through the library; open-spin outputs and correlators read back",
+               "link": dict(link, frac_of_floor=link["floor_ms"] / (dt * 1e3))}
 
     clk = clocks.stop()
 
