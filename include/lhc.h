@@ -259,7 +259,7 @@ int lhc_serve_stats(lhc_ctx ctx, size_t *bytes_in_use, int *queued, int *running
  * LHC_EINVAL).  The intermediate tensors live in a fixed 32 MiB
  * scratch array inside the library image, which every GPU that loads the library
  * holds until the process exits; the call itself never allocates.  A call needs
- * ng*(np+nq)*12*n_r*16 bytes of it for one insertion slice (larger combines give
+ * ng*(np+nq)*12*n_r*16 + 4*ng bytes of it for one insertion slice (larger combines give
  * LHC_EINVAL with the size; nt is processed in chunks that fit).  The first call on a
  * device looks up the scratch's device address (cudaGetSymbolAddress), so make that
  * first call before any stream capture.  All calls on a device share the scratch and

@@ -80,61 +80,56 @@ __device__ __forceinline__ void stage_rows(cplx<R> *dst, const double2 *src, int
   stage_batched<R>(src, n_r * 192, [](int e) { return (e / 192) * SROW + e % 192; }, dst);
 }
 
-// CTA per (t, q): Xi[t][g][q][i,al,a] = sum_b Gsrc[g][b][al] sum_{at,bt} Gins[g][at][bt] I[t][q][i][at,bt,b,a]
-// The noises of the block are staged nch at a time (as many as fit the shared memory the
-// host grants), after the Gamma matrices.
-template <typename R>
-__global__ void comb_ins_meson(const double2 *__restrict__ I, int nq, int n_r, int nch, const double2 *__restrict__ Gins,
-                               const double2 *__restrict__ Gsrc, int ng, cplx<R> *__restrict__ Xi) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  cplx<R> *sGi = reinterpret_cast<cplx<R> *>(sm_raw), *sGc = sGi + ng * 16, *sI = sGc + ng * 16;
-  const int tq = blockIdx.x, t = tq / nq, q = tq % nq;
-  stage(sGi, Gins, ng * 16);
-  stage(sGc, Gsrc, ng * 16);
-  for (int i0 = 0; i0 < n_r; i0 += nch) {
-  const int nc = min(nch, n_r - i0);
-  __syncthreads();
-  stage_rows(sI, I + ((size_t)tq * n_r + i0) * 192, nc);
-  __syncthreads();
-  for (int task = threadIdx.x; task < ng * nc * 3; task += blockDim.x) {
-    const int a = task % 3, ii = (task / 3) % nc, g = task / (3 * nc), i = i0 + ii;
-    const cplx<R> *v = sI + ii * SROW, *Gi = sGi + g * 16, *Gc = sGc + g * 16;
-    cplx<R> T[4];
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      T[b] = {0, 0};
-#pragma unroll
-      for (int at = 0; at < 4; ++at)
-#pragma unroll
-        for (int bt = 0; bt < 4; ++bt) cfma(T[b], Gi[at * 4 + bt], v[at * 48 + bt * 12 + b * 3 + a]);
+// Distinct Gamma_ins matrices: umap[g] = the first g' <= g whose matrix equals Gins[g]
+// entry for entry.  The insertion part with Gamma_ins applied is formed once per distinct
+// matrix, and every g reads that of umap[g] (the 16 structures of a sweep at sink and
+// source often share one insertion current).
+__global__ void gamma_reps(const double2 *__restrict__ G, int ng, int *__restrict__ umap) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ng) return;
+  int rep = g;
+  for (int h = 0; h < g && rep == g; ++h) {
+    bool same = true;
+    for (int e = 0; e < 16 && same; ++e) {
+      const double2 x = G[h * 16 + e], y = G[g * 16 + e];
+      same = x.x == y.x && x.y == y.y;
     }
-    cplx<R> *o = Xi + (((size_t)t * ng + g) * nq + q) * 12 * n_r + i * 12 + a;
-#pragma unroll
-    for (int al = 0; al < 4; ++al) {
-      cplx<R> acc{0, 0};
-#pragma unroll
-      for (int b = 0; b < 4; ++b) cfma(acc, Gc[b * 4 + al], T[b]);
-      o[al * 3] = acc;
-    }
+    if (same) rep = h;
   }
-  }
+  umap[g] = rep;
 }
+constexpr int kMaxGamma = 512;
 
-// CTA per (t, q): Xi[t][g][q][i,b,c] = sum_{at,bt} Gins[g][at][bt] I[t][q][i][at,bt,b,c]
+// CTA per (t, q): Xi[t][g][q][i,b,c] = sum_{at,bt} Gins[g][at][bt] I[t][q][i][at,bt,b,c] for
+// the representatives g (umap[g] == g) only: the insertion part with Gamma_ins applied,
+// spins (b, c) left for the spectator side
 template <typename R>
-__global__ void comb_ins_baryon(const double2 *__restrict__ I, int nq, int n_r, int nch, const double2 *__restrict__ Gins,
-                                int ng, cplx<R> *__restrict__ Xi) {
+__global__ void comb_ins_gamma(const double2 *__restrict__ I, int nq, int n_r, int nch, const double2 *__restrict__ Gins,
+                               const int *__restrict__ umap, int ng, cplx<R> *__restrict__ Xi) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
+  __shared__ int reps[kMaxGamma];
+  __shared__ int nrep;
   cplx<R> *sGi = reinterpret_cast<cplx<R> *>(sm_raw), *sI = sGi + 2 * ng * 16;
   const int tq = blockIdx.x, t = tq / nq, q = tq % nq;
+  if (threadIdx.x < 32) {   // the representatives in order, by ballot
+    int n = 0;
+    for (int g0 = 0; g0 < ng; g0 += 32) {
+      const int g = g0 + (int)threadIdx.x;
+      const bool r = g < ng && umap[g] == g;
+      const unsigned m = __ballot_sync(0xffffffffu, r);
+      if (r) reps[n + __popc(m & ((1u << threadIdx.x) - 1u))] = g;
+      n += __popc(m);
+    }
+    if (threadIdx.x == 0) nrep = n;
+  }
   stage(sGi, Gins, ng * 16);
   for (int i0 = 0; i0 < n_r; i0 += nch) {
   const int nc = min(nch, n_r - i0);
   __syncthreads();
   stage_rows(sI, I + ((size_t)tq * n_r + i0) * 192, nc);
   __syncthreads();
-  for (int task = threadIdx.x; task < ng * nc * 3; task += blockDim.x) {
-    const int c = task % 3, ii = (task / 3) % nc, g = task / (3 * nc), i = i0 + ii;
+  for (int task = threadIdx.x; task < nrep * nc * 3; task += blockDim.x) {
+    const int c = task % 3, ii = (task / 3) % nc, g = reps[task / (3 * nc)], i = i0 + ii;
     const cplx<R> *v = sI + ii * SROW, *Gi = sGi + g * 16;
     cplx<R> *o = Xi + (((size_t)t * ng + g) * nq + q) * 12 * n_r + i * 12 + c;
 #pragma unroll
@@ -150,14 +145,18 @@ __global__ void comb_ins_baryon(const double2 *__restrict__ I, int nq, int n_r, 
   }
 }
 
-// CTA per p: Xs[g][p][i,al,a] = sum_{ap,bp} Gsnk[g][ap][bp] S[p][i][bp,ap,al,a]
+// CTA per p: Xs[g][p][i,al,a] = sum_{ap,bp} Gsnk[g][ap][bp] S[p][i][bp,ap,al,a]; with
+// Gsrc given, the source structure is applied here too, on the spectator's side:
+// Xs[g][p][i,b,a] = sum_al Gsrc[g][b][al] (the sum above), so that the insertion part needs
+// Gamma_ins only (sum_{al,b} Xs_al Gsrc[b][al] Ins_b regrouped)
 template <typename R>
 __global__ void comb_spec_meson(const double2 *__restrict__ S, int np, int n_r, int nch, const double2 *__restrict__ Gsnk,
-                                int ng, cplx<R> *__restrict__ Xs) {
+                                const double2 *__restrict__ Gsrc, int ng, cplx<R> *__restrict__ Xs) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  cplx<R> *sG = reinterpret_cast<cplx<R> *>(sm_raw), *sS = sG + 2 * ng * 16;
+  cplx<R> *sG = reinterpret_cast<cplx<R> *>(sm_raw), *sGc = sG + ng * 16, *sS = sG + 2 * ng * 16;
   const int p = blockIdx.x;
   stage(sG, Gsnk, ng * 16);
+  if (Gsrc) stage(sGc, Gsrc, ng * 16);
   for (int i0 = 0; i0 < n_r; i0 += nch) {
   const int nc = min(nch, n_r - i0);
   __syncthreads();
@@ -167,14 +166,27 @@ __global__ void comb_spec_meson(const double2 *__restrict__ S, int np, int n_r, 
     const int a = task % 3, ii = (task / 3) % nc, g = task / (3 * nc), i = i0 + ii;
     const cplx<R> *s = sS + ii * SROW, *G = sG + g * 16;
     cplx<R> *o = Xs + ((size_t)g * np + p) * 12 * n_r + i * 12 + a;
+    cplx<R> x[4];
 #pragma unroll
     for (int al = 0; al < 4; ++al) {
-      cplx<R> acc{0, 0};
+      x[al] = {0, 0};
 #pragma unroll
       for (int ap = 0; ap < 4; ++ap)
 #pragma unroll
-        for (int bp = 0; bp < 4; ++bp) cfma(acc, G[ap * 4 + bp], s[bp * 48 + ap * 12 + al * 3 + a]);
-      o[al * 3] = acc;
+        for (int bp = 0; bp < 4; ++bp) cfma(x[al], G[ap * 4 + bp], s[bp * 48 + ap * 12 + al * 3 + a]);
+    }
+    if (Gsrc) {
+      const cplx<R> *Gc = sGc + g * 16;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        cplx<R> acc{0, 0};
+#pragma unroll
+        for (int al = 0; al < 4; ++al) cfma(acc, Gc[b * 4 + al], x[al]);
+        o[b * 3] = acc;
+      }
+    } else {
+#pragma unroll
+      for (int al = 0; al < 4; ++al) o[al * 3] = x[al];
     }
   }
   }
@@ -306,8 +318,8 @@ __device__ __forceinline__ void stage_tile(cplx<R> *dst, const cplx<R> *src, siz
 }
 template <typename R>
 __global__ void __launch_bounds__(256) comb_gemm(const cplx<R> *__restrict__ Xs, const cplx<R> *__restrict__ Xi,
-                                                 int np, int nq, int n_r, int ng, double inv_n, float inv_n_pow2,
-                                                 double2 *__restrict__ out) {
+                                                 const int *__restrict__ umap, int np, int nq, int n_r, int ng,
+                                                 double inv_n, float inv_n_pow2, double2 *__restrict__ out) {
   constexpr int KN = sizeof(R) == 4 ? 4 : 2, KW = 12 * KN + 1;
   __shared__ cplx<R> As[TP * KW];
   __shared__ cplx<R> Bs[TQ * KW];
@@ -317,7 +329,7 @@ __global__ void __launch_bounds__(256) comb_gemm(const cplx<R> *__restrict__ Xs,
   const int g = tg % ng;
   const size_t K = (size_t)12 * n_r;
   const cplx<R> *A = Xs + ((size_t)g * np) * K;
-  const cplx<R> *B = Xi + ((size_t)tg * nq) * K;
+  const cplx<R> *B = Xi + ((size_t)(tg - g + umap[g]) * nq) * K;   // the insertion part of g's Gamma_ins
   NoiseSum<R> acc[2][3];
   for (int i0 = 0; i0 < n_r; i0 += KN) {
     const int kw = 12 * min(KN, n_r - i0);
@@ -363,7 +375,7 @@ __global__ void __launch_bounds__(256) comb_gemm(const cplx<R> *__restrict__ Xs,
 
 // Open-source-spin combine:
 //   O[t][gs][gi][p][q][e][be] = (1/N) sum_{i,a} Xs[gs][p][i,e,a] Xi[t][gi][q][i,be,a]
-// with Xi the insertion part with Gamma_ins applied (comb_ins_baryon, which applies
+// with Xi the insertion part with Gamma_ins applied (comb_ins_gamma, which applies
 // Gamma_ins only) and Xs the spectator part with the sink structure applied: for a
 // meson e = al (RS = 4 open row spins, comb_spec_meson), for a baryon e = (a1, a2)
 // (RS = 16, comb_spec_baryon_open).  Rows are (p, e), columns (q, be); the tiling is
@@ -371,8 +383,9 @@ __global__ void __launch_bounds__(256) comb_gemm(const cplx<R> *__restrict__ Xs,
 // terms) per partial sum.
 template <typename R, int RS>
 __global__ void __launch_bounds__(256) comb_gemm_open(const cplx<R> *__restrict__ Xs, const cplx<R> *__restrict__ Xi,
-                                                      int np, int nq, int n_r, int ngs, int ngi, double inv_n,
-                                                      float inv_n_pow2, double2 *__restrict__ out) {
+                                                      const int *__restrict__ umap, int np, int nq, int n_r, int ngs,
+                                                      int ngi, double inv_n, float inv_n_pow2,
+                                                      double2 *__restrict__ out) {
   constexpr int KN = sizeof(R) == 4 ? 8 : 4, KW = 3 * KN + 1;
   __shared__ cplx<R> As[TP * KW];
   __shared__ cplx<R> Bs[TQ * KW];
@@ -380,7 +393,7 @@ __global__ void __launch_bounds__(256) comb_gemm_open(const cplx<R> *__restrict_
   const int c0 = blockIdx.x * TQ, r0 = blockIdx.y * TP;
   const int z = blockIdx.z, gi = z % ngi, gs = (z / ngi) % ngs, t = z / (ngi * ngs);
   const cplx<R> *A = Xs + (size_t)gs * np * 3 * RS * n_r;             // [p][i][e][a]
-  const cplx<R> *B = Xi + ((size_t)t * ngi + gi) * nq * 12 * n_r;      // [q][i][be][a]
+  const cplx<R> *B = Xi + ((size_t)t * ngi + umap[gi]) * nq * 12 * n_r;   // [q][i][be][a]
   NoiseSum<R> acc[2][3];
   for (int i0 = 0; i0 < n_r; i0 += KN) {
     const int kn = min(KN, n_r - i0);
@@ -436,9 +449,8 @@ unsigned blocks(size_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
 // The staging kernels may take up to 200 KB of dynamic shared memory (set once per device).
 template <typename R>
 int staging_smem_limits() {
-  static std::atomic<unsigned long long> d0{0}, d1{0}, d2{0};
-  LHC_TRY(ensure_smem_limit(comb_ins_meson<R>, 200 * 1024, d0));
-  LHC_TRY(ensure_smem_limit(comb_ins_baryon<R>, 200 * 1024, d1));
+  static std::atomic<unsigned long long> d1{0}, d2{0};
+  LHC_TRY(ensure_smem_limit(comb_ins_gamma<R>, 200 * 1024, d1));
   LHC_TRY(ensure_smem_limit(comb_spec_meson<R>, 200 * 1024, d2));
   return LHC_OK;
 }
@@ -448,7 +460,7 @@ int staging_smem_limits() {
 template <typename R>
 int noise_chunk(int ng, int n_r, int *nch, size_t *smem) {
   const size_t g_bytes = (size_t)2 * ng * 16 * sizeof(cplx<R>), row = (size_t)SROW * sizeof(cplx<R>);
-  if (g_bytes + row > 200 * 1024) {
+  if (g_bytes + row > 200 * 1024 || ng > kMaxGamma) {
     set_error("combine: %d Gamma structures do not fit shared memory", ng);
     return LHC_EINVAL;
   }
@@ -473,6 +485,9 @@ int spec_open_smem(int ng, size_t *smem) {
   return LHC_OK;
 }
 
+// The distinct Gamma_ins matrices (umap, gamma_reps), then the spectator part with the
+// sink (and, closed, the source) structures applied, the insertion part with Gamma_ins
+// applied once per distinct matrix, and the GEMM.  Scratch: Xs, Xi, then ng ints of umap.
 template <typename R>
 int launch_combine_open(int kind, const double2 *spec, int np, const double2 *ins, int nq, int n_r, int nt,
                         const double2 *snk, int ngs, const double2 *ins_g, int ngi, void *scratch, double2 *out,
@@ -480,25 +495,28 @@ int launch_combine_open(int kind, const double2 *spec, int np, const double2 *in
   const int RS = kind == LHC_MESON ? 4 : 16;
   cplx<R> *Xs = static_cast<cplx<R> *>(scratch);
   cplx<R> *Xi = Xs + (size_t)ngs * np * 3 * RS * n_r;
+  int *umap = reinterpret_cast<int *>(Xi + (size_t)nt * ngi * nq * 12 * n_r);
   int nch;
   size_t smem;
+  gamma_reps<<<blocks(ngi, 128), 128, 0, st>>>(ins_g, ngi, umap);
+  note_launch();
   if (kind == LHC_MESON) {
     LHC_TRY(noise_chunk<R>(ngs, n_r, &nch, &smem));
-    comb_spec_meson<R><<<np, 256, smem, st>>>(spec, np, n_r, nch, snk, ngs, Xs);
+    comb_spec_meson<R><<<np, 256, smem, st>>>(spec, np, n_r, nch, snk, nullptr, ngs, Xs);
   } else {
     LHC_TRY(spec_open_smem<R>(ngs, &smem));
     comb_spec_baryon_open<R><<<np * n_r, 256, smem, st>>>(spec, np, n_r, snk, ngs, Xs);
   }
   note_launch();
   LHC_TRY(noise_chunk<R>(ngi, n_r, &nch, &smem));
-  comb_ins_baryon<R><<<nt * nq, 256, smem, st>>>(ins, nq, n_r, nch, ins_g, ngi, Xi);   // Gamma_ins only
+  comb_ins_gamma<R><<<nt * nq, 256, smem, st>>>(ins, nq, n_r, nch, ins_g, umap, ngi, Xi);   // Gamma_ins only
   note_launch();
   const dim3 grid((4 * nq + TQ - 1) / TQ, (RS * np + TP - 1) / TP, nt * ngs * ngi);
   const float inv_pow2 = (n_r & (n_r - 1)) == 0 ? 1.0f / (float)n_r : 0.0f;   // exact for N = 2^m
   if (kind == LHC_MESON)
-    comb_gemm_open<R, 4><<<grid, 256, 0, st>>>(Xs, Xi, np, nq, n_r, ngs, ngi, 1.0 / n_r, inv_pow2, out);
+    comb_gemm_open<R, 4><<<grid, 256, 0, st>>>(Xs, Xi, umap, np, nq, n_r, ngs, ngi, 1.0 / n_r, inv_pow2, out);
   else
-    comb_gemm_open<R, 16><<<grid, 256, 0, st>>>(Xs, Xi, np, nq, n_r, ngs, ngi, 1.0 / n_r, inv_pow2, out);
+    comb_gemm_open<R, 16><<<grid, 256, 0, st>>>(Xs, Xi, umap, np, nq, n_r, ngs, ngi, 1.0 / n_r, inv_pow2, out);
   note_launch();
   return LHC_OK;
 }
@@ -509,31 +527,24 @@ int launch_combine(int kind, const double2 *spec, int np, const double2 *ins, in
                    double2 *out, cudaStream_t st) {
   cplx<R> *Xs = static_cast<cplx<R> *>(scratch);
   cplx<R> *Xi = Xs + (size_t)ng * np * 12 * n_r;
-  // noises staged per pass: as many as fit 96 KB next to the Gamma matrices (two CTAs
-  // per SM), at least one
-  const size_t g_bytes = (size_t)2 * ng * 16 * sizeof(cplx<R>), row = (size_t)SROW * sizeof(cplx<R>);
-  if (g_bytes + row > 200 * 1024) {
-    set_error("combine: %d Gamma structures do not fit shared memory", ng);
-    return LHC_EINVAL;
-  }
-  const int nch = (int)std::min<size_t>((size_t)n_r, g_bytes + row <= 96 * 1024 ? (96 * 1024 - g_bytes) / row : 1);
-  const size_t smem = g_bytes + (size_t)nch * row;
-  if (smem > 48 * 1024) LHC_TRY(staging_smem_limits<R>());
+  int *umap = reinterpret_cast<int *>(Xi + (size_t)nt * ng * nq * 12 * n_r);
+  int nch;
+  size_t smem;
+  LHC_TRY(noise_chunk<R>(ng, n_r, &nch, &smem));
+  gamma_reps<<<blocks(ng, 128), 128, 0, st>>>(ins_g, ng, umap);
+  note_launch();
   if (kind == LHC_MESON) {
-    comb_spec_meson<R><<<np, 256, smem, st>>>(spec, np, n_r, nch, snk, ng, Xs);
-    note_launch();
-    comb_ins_meson<R><<<nt * nq, 256, smem, st>>>(ins, nq, n_r, nch, ins_g, src, ng, Xi);
-    note_launch();
+    comb_spec_meson<R><<<np, 256, smem, st>>>(spec, np, n_r, nch, snk, src, ng, Xs);
   } else {
     size_t ns = (size_t)ng * np * n_r * 3;
     comb_spec_baryon<R><<<blocks(ns, 128), 128, 0, st>>>(spec, np, n_r, snk, src, ng, Xs);
-    note_launch();
-    comb_ins_baryon<R><<<nt * nq, 256, smem, st>>>(ins, nq, n_r, nch, ins_g, ng, Xi);
-    note_launch();
   }
+  note_launch();
+  comb_ins_gamma<R><<<nt * nq, 256, smem, st>>>(ins, nq, n_r, nch, ins_g, umap, ng, Xi);
+  note_launch();
   dim3 grid((nq + TQ - 1) / TQ, (np + TP - 1) / TP, nt * ng);
   const float inv_pow2 = (n_r & (n_r - 1)) == 0 ? 1.0f / (float)n_r : 0.0f;   // exact for N = 2^m
-  comb_gemm<R><<<grid, 256, 0, st>>>(Xs, Xi, np, nq, n_r, ng, 1.0 / n_r, inv_pow2, out);
+  comb_gemm<R><<<grid, 256, 0, st>>>(Xs, Xi, umap, np, nq, n_r, ng, 1.0 / n_r, inv_pow2, out);
   note_launch();
   return LHC_OK;
 }
@@ -545,7 +556,7 @@ int run_combine(lhc_ctx ctx, int kind, const double2 *spec, int np, const double
                 cudaStream_t st) {
   const size_t es = prec == LHC_MIXED ? sizeof(cplx<float>) : sizeof(cplx<double>);
   const size_t K = (size_t)12 * n_r;
-  LHC_TRY(ensure(ctx, ctx->ws, ((size_t)ng * np * K + (size_t)nt * ng * nq * K) * es));
+  LHC_TRY(ensure(ctx, ctx->ws, ((size_t)ng * np * K + (size_t)nt * ng * nq * K) * es + (size_t)ng * sizeof(int)));
   ProfScope ps(ctx, st, LHC_KERNEL_COMBINE, 8.0 * nt * ng * (double)np * nq * K);
   if (prec == LHC_MIXED)
     LHC_TRY(launch_combine<float>(kind, spec, np, ins, nq, n_r, nt, snk, ins_g, src, ng, ctx->ws.p, out, st));
@@ -556,7 +567,7 @@ int run_combine(lhc_ctx ctx, int kind, const double2 *spec, int np, const double
 }
 
 // The same kernels on caller-provided scratch (room for ng*np*12*n_r + nt*ng*nq*12*n_r
-// complex128 values); no allocation and no context.
+// complex values of the precision, then ng ints); no allocation and no context.
 int run_combine_scratch(int kind, const double2 *spec, int np, const double2 *ins, int nq, int n_r, int nt,
                         const double2 *snk, const double2 *ins_g, const double2 *src, int ng, int prec,
                         double2 *Xs, double2 *Xi, double2 *out, cudaStream_t st) {
@@ -583,7 +594,7 @@ int run_combine_open(lhc_ctx ctx, int kind, const double2 *spec, int np, const d
   }
   const size_t es = prec == LHC_MIXED ? sizeof(cplx<float>) : sizeof(cplx<double>);
   const size_t K = (size_t)3 * n_r;   // (noise, colour)
-  LHC_TRY(ensure(ctx, ctx->ws, ((size_t)ngs * np * RS * K + (size_t)nt * ngi * nq * 4 * K) * es));
+  LHC_TRY(ensure(ctx, ctx->ws, ((size_t)ngs * np * RS * K + (size_t)nt * ngi * nq * 4 * K) * es + (size_t)ngi * sizeof(int)));
   ProfScope ps(ctx, st, LHC_KERNEL_COMBINE, 8.0 * nt * ngs * ngi * (double)RS * np * 4.0 * nq * K);
   if (prec == LHC_MIXED)
     LHC_TRY(launch_combine_open<float>(kind, spec, np, ins, nq, n_r, nt, snk, ngs, ins_g, ngi, ctx->ws.p, out, st));

@@ -1476,13 +1476,18 @@ static int finish_chunk(lhc_ctx ctx, const Prepared &pc, cudaStream_t st) {
   return LHC_OK;
 }
 
-static int kd_default() {
+static int kd_for(Part part) {
   // k-steps accumulated in tensor memory between drains.  The accumulation truncates, so
   // the error grows with the interval: measured on the 24^3 workload (16 noises, 93
   // momenta) intervals 6, 4 and 2 give 4.6e-7, 3.6e-7 and 2.9e-7 per block against the
-  // oracle, for 1% and 11% more time in the fused kernel than interval 6.
-  int kd = 4;
-  if (const char *e = getenv("LHC_KD")) kd = std::max(2, (atoi(e) + 1) / 2 * 2);   // even: k-steps come in pairs
+  // oracle, for 1% and 11% more time in the fused kernel than interval 6.  The combine
+  // adds the errors of both parts; the meson spectator, a small part of the time, drains
+  // every 2 k-steps, the insertion and the baryon spectator every 4.  LHC_KD and
+  // LHC_KD_SPEC (meson spectator) override them; the interval is even, since k-steps
+  // come in pairs.
+  const bool mspec = part == PART_SPEC_MESON;
+  int kd = mspec ? 2 : 4;
+  if (const char *e = getenv(mspec ? "LHC_KD_SPEC" : "LHC_KD")) kd = std::max(2, (atoi(e) + 1) / 2 * 2);
   return kd;
 }
 
@@ -1500,7 +1505,7 @@ static int run_mixed_shape(lhc_ctx ctx, const SliceJob *jobs, int nt, const int 
   const ChunkLayout lay = chunk_layout(j0, std::min(nt, kMaxSlices), nsplit, (size_t)nrc * NH * ncols);
   LHC_TRY(ensure(ctx, ctx->ws, lay.bytes));
   char *ws = static_cast<char *>(ctx->ws.p);
-  const int kd = kd_default();
+  const int kd = kd_for(j0.part);
   for (int jb = 0; jb < nt; jb += kMaxSlices) {
     const int nb = std::min(kMaxSlices, nt - jb);
     Prepared pc;
@@ -1675,12 +1680,11 @@ int run_batch_mixed(lhc_ctx ctx, const std::vector<BatchCall> &calls, cudaStream
   LHC_TRY(ensure(ctx, ctx->ws, off_cursor + sizeof(int) * (size_t)nlaunch));
   char *ws = static_cast<char *>(ctx->ws.p);
   int *cursor = reinterpret_cast<int *>(ws + off_cursor);
-  const int kd = kd_default();
   std::vector<Prepared> pc(n);
   for (int c = 0; c < n; ++c) {
     const BatchCall &bc = calls[c];
     LHC_TRY(prepare_chunk(ctx, bc.jobs.data(), (int)bc.jobs.size(), bc.nq, bc.sign, reps[c], phase[c], rmap[c], NH[c],
-                          nsplit[c], kd, ws + off[c], lay[c], st, &pc[c]));
+                          nsplit[c], kd_for(bc.jobs[0].part), ws + off[c], lay[c], st, &pc[c]));
     const Prepared &q = pc[c];
     for (int j = 0; j < q.nb; ++j)
       if (q.fp.tM[j] != (q.tm0 + j) % q.tmT || q.fp.tV[j] != (q.tv0 + j) % q.tvT) {

@@ -102,13 +102,14 @@ extern "C" int lhc_combine_noalloc(int kind, const void *spec, int np, const voi
                      "memory or read another GPU's)");
       return LHC_EINVAL;
     }
-  // scratch use: Xs (ng*np*12*n_r) once, then Xi (ng*nq*12*n_r) per insertion slice of a chunk
+  // scratch use: Xs (ng*np*12*n_r) once, then Xi (ng*nq*12*n_r) per insertion slice of a
+  // chunk, then the ng ints that map each Gamma_ins to its first equal one
   const size_t K = (size_t)12 * n_r;
   const size_t xs = (size_t)ng * np * K, xi_slice = (size_t)ng * nq * K;
-  const size_t cap = kNoallocScratchBytes / sizeof(double2);
+  const size_t cap = kNoallocScratchBytes / sizeof(double2) - ((size_t)ng * sizeof(int) + 15) / 16;
   if (xs + xi_slice > cap) {
     lhc::set_error("combine too large for the %zu-byte allocation-free scratch: needs %zu bytes for one "
-                   "insertion slice (ng*(np+nq)*12*n_r*16); use lhc_combine",
+                   "insertion slice (ng*(np+nq)*12*n_r*16 + 4*ng); use lhc_combine",
                    kNoallocScratchBytes, (xs + xi_slice) * sizeof(double2));
     return LHC_EINVAL;
   }
