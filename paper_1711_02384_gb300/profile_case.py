@@ -24,6 +24,9 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--dtype", choices=["c128", "c64"], default="c128")
+    ap.add_argument("--gammas", choices=["random", "sweep"], default="random",
+                    help="combine: 16 random structures everywhere, or the Dirac sweep at sink "
+                         "and source with gamma_4 at the insertion (the benchmark's)")
     a = ap.parse_args()
     dev = torch.device("cuda", 0)
     g = torch.Generator(device=dev)
@@ -46,8 +49,13 @@ def main():
         nq = len(k)
         spec = torch.randn((nq, a.nr, 192), dtype=torch.complex128, device=dev, generator=g)
         ins = torch.randn((T, nq, a.nr, 192), dtype=torch.complex128, device=dev, generator=g)
-        G = torch.randn((16, 4, 4), dtype=torch.complex128, device=dev, generator=g)
-        call = lambda: ctx.combine(spec, ins, G, G, G, prec=a.prec)
+        if a.gammas == "sweep":
+            from . import inputs
+            G = torch.from_numpy(inputs.dirac_structures()).to(dev)
+            Gi = torch.from_numpy(inputs.dirac_matrices()[3]).to(dev).expand(16, 4, 4).contiguous()
+        else:
+            G = Gi = torch.randn((16, 4, 4), dtype=torch.complex128, device=dev, generator=g)
+        call = lambda: ctx.combine(spec, ins, G, Gi, G, prec=a.prec)
     call()
     ctx.sync()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
