@@ -295,9 +295,8 @@ static int stage_begin(lhc_ctx ctx, size_t bytes, int *slot, char **base) {
   return LHC_OK;
 }
 
-// Host -> slot copy on the H2D stream, after any output copy still writing that memory.
-static int stage_in(lhc_ctx ctx, int slot, void *dst, const void *src, size_t bytes) {
-  const char *a = static_cast<const char *>(src);
+// The H2D stream waits for any output copy still writing host memory in [a, a + bytes).
+static int wait_pending_out(lhc_ctx ctx, const char *a, size_t bytes) {
   for (auto it = ctx->pending_out.begin(); it != ctx->pending_out.end();) {
     if (cudaEventQuery(it->ev) == cudaSuccess) {   // landed: forget it
       ctx->event_pool.push_back(it->ev);
@@ -308,8 +307,33 @@ static int stage_in(lhc_ctx ctx, int slot, void *dst, const void *src, size_t by
     if (a < it->p + it->n && it->p < a + bytes) LHC_CHECK_CUDA(cudaStreamWaitEvent(ctx->h2d, it->ev, 0));
     ++it;
   }
+  return LHC_OK;
+}
+
+// Host -> slot copy on the H2D stream, after any output copy still writing that memory.
+static int stage_in(lhc_ctx ctx, int slot, void *dst, const void *src, size_t bytes) {
   (void)slot;
+  LHC_TRY(wait_pending_out(ctx, static_cast<const char *>(src), bytes));
   LHC_CHECK_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->h2d));
+  return LHC_OK;
+}
+
+// The same for `rows` equal pieces of `width` bytes, `spitch` apart in host memory and
+// `dpitch` apart in the slot: one strided copy instead of one copy per piece (the noises
+// of a solution tensor), so the link does not idle between many medium copies.
+static int stage_in_rows(lhc_ctx ctx, int slot, void *dst, size_t dpitch, const void *src, size_t spitch,
+                         size_t width, size_t rows) {
+  if (rows == 0) return LHC_OK;
+  int max_pitch = 0;
+  LHC_CHECK_CUDA(cudaDeviceGetAttribute(&max_pitch, cudaDevAttrMaxPitch, ctx->device));
+  if (spitch > (size_t)max_pitch || dpitch > (size_t)max_pitch) {   // beyond a strided copy's pitch: one per piece
+    for (size_t r = 0; r < rows; ++r)
+      LHC_TRY(stage_in(ctx, slot, static_cast<char *>(dst) + r * dpitch, static_cast<const char *>(src) + r * spitch,
+                       width));
+    return LHC_OK;
+  }
+  LHC_TRY(wait_pending_out(ctx, static_cast<const char *>(src), (rows - 1) * spitch + width));
+  LHC_CHECK_CUDA(cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, rows, cudaMemcpyHostToDevice, ctx->h2d));
   return LHC_OK;
 }
 
@@ -679,13 +703,13 @@ int run_part(lhc_ctx ctx, const PartCall &c, cudaStream_t st) {
       char *dst = sp + al(bS) + al(bSB);
       if (!c.vec_has_time) {   // eta: [n_r][V3][12], one block (a spectator call has one slice)
         if (g0 == 0) LHC_TRY(stage_in(ctx, slot, dst, V, (size_t)c.n_r * vec_slice * es));
-      } else {   // psi: per noise, the group's runs of slices
-        for (int i = 0; i < c.n_r; ++i)
-          for (const auto &rn : runs) {
-            const size_t t = (size_t)((c.t0 + rn.first) % T);
-            LHC_TRY(stage_in(ctx, slot, dst + ((size_t)i * nvt + rn.first) * vec_slice * es,
-                             V + ((size_t)i * T + t) * vec_slice * es, (size_t)rn.second * vec_slice * es));
-          }
+      } else {   // psi: the group's runs of slices, every noise in one strided copy per run
+        for (const auto &rn : runs) {
+          const size_t t = (size_t)((c.t0 + rn.first) % T);
+          LHC_TRY(stage_in_rows(ctx, slot, dst + (size_t)rn.first * vec_slice * es, (size_t)nvt * vec_slice * es,
+                                V + t * vec_slice * es, (size_t)T * vec_slice * es,
+                                (size_t)rn.second * vec_slice * es, (size_t)c.n_r));
+        }
       }
     }
     if (any_host) LHC_TRY(stage_ready(ctx, slot, st));
