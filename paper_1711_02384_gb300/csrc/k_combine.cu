@@ -103,9 +103,12 @@ constexpr int kMaxGamma = 512;
 // CTA per (t, q): Xi[t][g][q][i,b,c] = sum_{at,bt} Gins[g][at][bt] I[t][q][i][at,bt,b,c] for
 // the representatives g (umap[g] == g) only: the insertion part with Gamma_ins applied,
 // spins (b, c) left for the spectator side
+// (FP32: at most 64 registers, so that four CTAs share an SM; the kernel spends its time
+// staging the insertion part, and more CTAs keep more of those loads in flight)
 template <typename R>
-__global__ void comb_ins_gamma(const double2 *__restrict__ I, int nq, int n_r, int nch, const double2 *__restrict__ Gins,
-                               const int *__restrict__ umap, int ng, cplx<R> *__restrict__ Xi) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1)
+    comb_ins_gamma(const double2 *__restrict__ I, int nq, int n_r, int nch, const double2 *__restrict__ Gins,
+                   const int *__restrict__ umap, int ng, cplx<R> *__restrict__ Xi) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ int reps[kMaxGamma];
   __shared__ int nrep;

@@ -736,8 +736,11 @@ __global__ void __launch_bounds__(kReduceThreads)
   const int rho = (int)(e / ncols), col = (int)(e % ncols);
   const float4 *pj = part + (size_t)j * nsplit * per_split + e;
   float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
+  // unrolled so that several splits' loads are in flight before the first is added (the
+  // order of the sums is unchanged)
+#pragma unroll 4
   for (int s = 0; s < nsplit; ++s) {
-    const float4 v = pj[(size_t)s * per_split];
+    const float4 v = __ldcs(pj + (size_t)s * per_split);
     two_sum(h[0], l[0], v.x);
     two_sum(h[1], l[1], v.y);
     two_sum(h[2], l[2], v.z);
