@@ -1,11 +1,13 @@
 // Noise-averaged combine (Eqs. 5 and 8).
 //
-// Both cases reduce to  out[t][g][p][q] = (1/N) sum_K Xs[g][p][K] Xi[t][g][q][K]  with
-// K = (noise i, spin j, colour c) (12 N values):
-//   meson   Xs[g][p][i,al,a] = sum_{ap,bp} Gsnk[ap][bp] S[p][i][bp,ap,al,a]
-//           Xi[t][g][q][i,al,a] = sum_b Gsrc[b][al] sum_{at,bt} Gins[at][bt] I[t][q][i][at,bt,b,a]
-//   baryon  Xs[g][p][i,b,c]  = sum Wsnk[a1p][a2p][bp] Wsrc[a1][a2][b] B[p][i][a1p,a1,a2p,a2,bp,c]
-//           Xi[t][g][q][i,b,c] = sum_{at,bt} Gins[at][bt] I[t][q][i][at,bt,b,c]
+// Both cases reduce to  out[t][g][p][q] = (1/N) sum_K Xs[g][p][K] Xi[t][u(g)][q][K]  with
+// K = (noise i, spin b, colour c) (12 N values):
+//   meson   Xs[g][p][i,b,a] = sum_al Gsrc[b][al] sum_{ap,bp} Gsnk[ap][bp] S[p][i][bp,ap,al,a]
+//   baryon  Xs[g][p][i,b,c] = sum Wsnk[a1p][a2p][bp] Wsrc[a1][a2][b] B[p][i][a1p,a1,a2p,a2,bp,c]
+//   both    Xi[t][g][q][i,b,c] = sum_{at,bt} Gins[at][bt] I[t][q][i][at,bt,b,c]
+// The meson's source structure sits on the spectator side (Eq. 8's sum over the source
+// spins regrouped), so the insertion side depends on g only through Gins: it is formed
+// for the first g of each distinct Gins matrix, u(g) (gamma_reps), and shared.
 // Precision: LHC_FP64 does everything in double.  LHC_MIXED does the Gamma contractions and
 // the spin-colour sums of each pair of noises in FP32; the sum over those (the noise
 // average of Eq. 5) is exact: each pair's term is added with Knuth's TwoSum into an
