@@ -197,7 +197,10 @@ __global__ void comb_spec_meson(const double2 *__restrict__ S, int np, int n_r, 
   }
 }
 
-// one thread per (g, p, i, c): Bhat[a1][a2] = sum Wsnk B, then the four b values
+// one thread per (g, p, i, c): Bhat[a1][a2] = sum Wsnk B, then the four b values.  The sums
+// (64 terms, then 16) run in FP64 in both precisions and are rounded once to R: in FP32
+// their rounding would be the largest error of the mixed baryon combine, and the kernel
+// is small beside the GEMM.
 template <typename R>
 __global__ void comb_spec_baryon(const double2 *__restrict__ B, int np, int n_r, const double2 *__restrict__ Wsnk,
                                  const double2 *__restrict__ Wsrc, int ng, cplx<R> *__restrict__ Xs) {
@@ -211,21 +214,31 @@ __global__ void comb_spec_baryon(const double2 *__restrict__ B, int np, int n_r,
   const double2 *s = B + ((size_t)p * n_r + i) * 3072;
   const double2 *Ws = Wsnk + (size_t)g * 64;
   const double2 *Wc = Wsrc + (size_t)g * 64;
-  cplx<R> out[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  cplx<double> out[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+#pragma unroll 1
   for (int a1 = 0; a1 < 4; ++a1)
+#pragma unroll 1
     for (int a2 = 0; a2 < 4; ++a2) {
-      cplx<R> h{0, 0};
+      cplx<double> h{0, 0};
+#pragma unroll 1
       for (int a1p = 0; a1p < 4; ++a1p)
-        for (int a2p = 0; a2p < 4; ++a2p)
-          for (int bp = 0; bp < 4; ++bp)
-            cfma(h, ld<R>(Ws + (a1p * 4 + a2p) * 4 + bp),
-                 ld<R>(s + ((((a1p * 4 + a1) * 4 + a2p) * 4 + a2) * 4 + bp) * 3 + c));
 #pragma unroll
-      for (int b = 0; b < 4; ++b) cfma(out[b], ld<R>(Wc + (a1 * 4 + a2) * 4 + b), h);
+        for (int a2p = 0; a2p < 4; ++a2p)
+#pragma unroll
+          for (int bp = 0; bp < 4; ++bp)
+            cfma(h, ld<double>(Ws + (a1p * 4 + a2p) * 4 + bp),
+                 ld<double>(s + ((((a1p * 4 + a1) * 4 + a2p) * 4 + a2) * 4 + bp) * 3 + c));
+#pragma unroll
+      for (int b = 0; b < 4; ++b) cfma(out[b], ld<double>(Wc + (a1 * 4 + a2) * 4 + b), h);
     }
   cplx<R> *o = Xs + ((size_t)g * np + p) * 12 * n_r + i * 12 + c;
 #pragma unroll
-  for (int b = 0; b < 4; ++b) o[b * 3] = out[b];
+  for (int b = 0; b < 4; ++b) {
+    if constexpr (std::is_same<R, float>::value)
+      o[b * 3] = cplx<R>{f64_to_f32_rne(out[b].x), f64_to_f32_rne(out[b].y)};
+    else
+      o[b * 3] = out[b];
+  }
 }
 
 // CTA per (p, i), the source spins left open:

@@ -1484,13 +1484,16 @@ static int kd_for(Part part) {
   // the error grows with the interval: measured on the 24^3 workload (16 noises, 93
   // momenta) intervals 6, 4 and 2 give 4.6e-7, 3.6e-7 and 2.9e-7 per block against the
   // oracle, for 1% and 11% more time in the fused kernel than interval 6.  The combine
-  // adds the errors of both parts; the meson spectator, a small part of the time, drains
-  // every 2 k-steps, the insertion and the baryon spectator every 4.  LHC_KD and
-  // LHC_KD_SPEC (meson spectator) override them; the interval is even, since k-steps
-  // come in pairs.
-  const bool mspec = part == PART_SPEC_MESON;
-  int kd = mspec ? 2 : 4;
-  if (const char *e = getenv(mspec ? "LHC_KD_SPEC" : "LHC_KD")) kd = std::max(2, (atoi(e) + 1) / 2 * 2);
+  // adds the errors of both parts, so the spectators (meson: a tenth of the fused time;
+  // baryon: the part whose error dominates its combine) drain every 2, the insertion every
+  // 4.  LHC_KD sets every part's interval, LHC_KD_INS,
+  // LHC_KD_SPEC and LHC_KD_BAR one part's; intervals are even, since k-steps come in pairs.
+  static const int defaults[3] = {4, 2, 2};   // insertion, meson spectator, baryon spectator
+  static const char *names[3] = {"LHC_KD_INS", "LHC_KD_SPEC", "LHC_KD_BAR"};
+  int kd = defaults[(int)part];
+  const char *e = getenv(names[(int)part]);
+  if (!e) e = getenv("LHC_KD");
+  if (e) kd = std::max(2, (atoi(e) + 1) / 2 * 2);
   return kd;
 }
 

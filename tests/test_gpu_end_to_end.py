@@ -53,3 +53,41 @@ def test_chain_24c_one_slice_per_correlator(seed):
           f"combine {e_corr:.3e} per correlator")
     assert e_ins < CS.MIXED_TOL and e_spec < CS.MIXED_TOL
     assert e_corr < CS.MIXED_TOL
+
+
+@pytest.mark.parametrize("seed", [3300, 3400])
+def test_baryon_chain_16c_123_momenta_per_correlator(seed):
+    """The baryon chain on 16^3 with the 123 momenta of the baryon configuration (|k|^2 <= 9,
+    |k_j| <= 3: 62 representatives, two chunks), 4 noises, complex64 propagators: the mixed
+    eps-eps spectator and the insertion of one slice on the GPU, combined there for 4
+    random sink/source structures and insertion Gammas, against the oracle's chain
+    (Sec. 2, Eqs. 5, 8, 10), per correlator within 1e-6."""
+    from oracle import contractions as OC
+    from oracle.momenta import momenta
+    from paper_1711_02384_gb300 import inputs, lhc
+    L, n_r, t_ins, t_snk = 16, 4, 3, 9
+    k = momenta(9, 3)
+    GA = inputs.propagator(seed, L, 32, slices=[t_ins, t_snk]).astype(np.complex64)
+    GB = inputs.propagator(seed, L, 32, slices=[t_ins, t_snk], tensor_id=inputs.TID_PROP_B).astype(np.complex64)
+    psi = inputs.solutions(seed + 1, L, 32, n_r, slices=[t_ins, t_snk]).astype(np.complex64)
+    eta = inputs.noise(seed + 2, L, n_r, t_snk).astype(np.complex64)
+    ws = CS.random_gammas(seed + 3, 4, (4, 4, 4))
+    gi = CS.random_gammas(seed + 4, 4, (4, 4))
+    wc = CS.random_gammas(seed + 5, 4, (4, 4, 4))
+    r = np.array([2, 5, 11, 0], dtype=np.int32)
+    with lhc.Context(0) as ctx:
+        dA = dev(GA)
+        ins = ctx.insertion(dA, dev(psi), 0, 0, r, k, prec="mixed")
+        spec = ctx.spectator(dA, dev(eta), 1, r, k, prec="mixed", GB=dev(GB))
+        corr = ctx.combine(spec, ins, dev(ws), dev(gi), dev(wc), prec="mixed")
+        ins, spec, corr = ins.cpu().numpy(), spec.cpu().numpy(), corr.cpu().numpy()
+        ctx.sync()
+    g5 = CS.g5_matrix()
+    ri = OC.insertion(GA[0:1].astype(complex), psi[:, 0:1].astype(complex), g5, r[:3], k, L)
+    rs = OC.spectator_baryon(GA[1].astype(complex), GB[1].astype(complex), eta.astype(complex), g5, r[:3], k, L)
+    rc = OC.combine_baryon(rs, ri[0], ws, gi, wc)
+    e_ins, e_spec, e_corr = block_err(ins[0], ri[0]), block_err(spec, rs), CS.corr_err(corr[0], rc)
+    print(f"[parity] baryon 16^3 chain, 123 momenta, seed {seed}: insertion {e_ins:.3e}, spectator {e_spec:.3e}, "
+          f"combine {e_corr:.3e} per correlator")
+    assert e_ins < CS.MIXED_TOL and e_spec < CS.MIXED_TOL
+    assert e_corr < CS.MIXED_TOL
