@@ -245,19 +245,21 @@ __global__ void comb_spec_baryon(const double2 *__restrict__ B, int np, int n_r,
 //   Xs[g][p][i][(a1*4 + a2)*3 + c] = sum_{a1p,a2p,bp} Wsnk[g][a1p][a2p][bp] B[p][i][a1p,a1,a2p,a2,bp,c]
 // The noise's 3072 values and the ng Wsnk tensors are staged in shared memory; a task is
 // one (g, a1, a2, c).
+// As in the closed form, the 64-term sums run in FP64 in both precisions (the noise's
+// values and the W tensors staged in double) and are rounded once to R.
 template <typename R>
 __global__ void comb_spec_baryon_open(const double2 *__restrict__ B, int np, int n_r, const double2 *__restrict__ Wsnk,
                                       int ng, cplx<R> *__restrict__ Xs) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  cplx<R> *sW = reinterpret_cast<cplx<R> *>(sm_raw), *sB = sW + ng * 64;
+  cplx<double> *sW = reinterpret_cast<cplx<double> *>(sm_raw), *sB = sW + ng * 64;
   const int pi = blockIdx.x, p = pi / n_r, i = pi % n_r;
   stage(sW, Wsnk, ng * 64);
   stage(sB, B + (size_t)pi * 3072, 3072);
   __syncthreads();
   for (int task = threadIdx.x; task < ng * 48; task += blockDim.x) {
     const int c = task % 3, a2 = (task / 3) % 4, a1 = (task / 12) % 4, g = task / 48;
-    const cplx<R> *W = sW + g * 64;
-    cplx<R> h{0, 0};
+    const cplx<double> *W = sW + g * 64;
+    cplx<double> h{0, 0};
 #pragma unroll
     for (int a1p = 0; a1p < 4; ++a1p)
 #pragma unroll
@@ -265,7 +267,11 @@ __global__ void comb_spec_baryon_open(const double2 *__restrict__ B, int np, int
 #pragma unroll
         for (int bp = 0; bp < 4; ++bp)
           cfma(h, W[(a1p * 4 + a2p) * 4 + bp], sB[((((a1p * 4 + a1) * 4 + a2p) * 4 + a2) * 4 + bp) * 3 + c]);
-    Xs[(((size_t)g * np + p) * n_r + i) * 48 + task % 48] = h;
+    cplx<R> *o = Xs + (((size_t)g * np + p) * n_r + i) * 48 + task % 48;
+    if constexpr (std::is_same<R, float>::value)
+      *o = cplx<R>{f64_to_f32_rne(h.x), f64_to_f32_rne(h.y)};
+    else
+      *o = h;
   }
 }
 
@@ -491,7 +497,7 @@ int noise_chunk(int ng, int n_r, int *nch, size_t *smem) {
 // Shared memory of comb_spec_baryon_open: one noise's 3072 values and ng Wsnk tensors.
 template <typename R>
 int spec_open_smem(int ng, size_t *smem) {
-  *smem = ((size_t)ng * 64 + 3072) * sizeof(cplx<R>);
+  *smem = ((size_t)ng * 64 + 3072) * sizeof(cplx<double>);   // staged in double in both precisions
   if (*smem > 200 * 1024) {
     set_error("combine_open: %d sink structures do not fit shared memory", ng);
     return LHC_EINVAL;
