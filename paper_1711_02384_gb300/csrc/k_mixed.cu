@@ -24,7 +24,8 @@
 //               propagator or diquark box and the two noises' vector box) into the input
 //               ring, whose stages the producers free
 //   warp 1      allocates tensor memory and issues the MMAs
-//   warps 2-9   drain the accumulator every KD k-steps into an FP32 running sum
+//   warps 2-9   drain the accumulator every KD k-steps into an FP32 running sum, which
+//               starts again after every group of at most 128 chunks
 //   warps 10-21 producers, four per k-step and three k-steps in flight: contract the
 //               inputs in FP32, split each value into fp16 hi + lo and write the four A
 //               tiles (Ur hi/lo, Ui hi/lo), MN-major
@@ -33,9 +34,11 @@
 //   D[:, 0:2NH]   += Ur_h [cos|sin]_h + Ur_h [cos|sin]_l + Ur_l [cos|sin]_h
 //   D[:, 2NH:4NH] += Ui_h [cos|sin]_h + Ui_h [cos|sin]_l + Ui_l [cos|sin]_h
 // (the lo*lo term dropped), i.e. Re C, Re S, Im C, Im S.  Tensor memory accumulation
-// truncates, so D is double-buffered and drained every KD k-steps; each CTA writes FP32
-// partial sums of (Re C, Re S, Im C, Im S), and reduce_f64 adds the partials of all CTAs
-// exactly, rounds to FP64 and forms out[q] = C + i sigma_q S.
+// truncates, so the products with a lo factor go first within each pair of k-steps, and D
+// is double-buffered and drained every KD k-steps into a two-level FP32 sum (a running
+// sum over groups of at most 128 chunks, whose group sums add up in tensor memory or, for
+// the widest chunks, in the CTA's partial sums in global memory); reduce_f64 adds the
+// partials of all CTAs exactly, rounds to FP64 and forms out[q] = C + i sigma_q S.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -68,6 +71,8 @@ constexpr int NPK = 3;                   // k-steps in flight in the producers (
 constexpr int kWarps = 23;
 constexpr int kThreads = kWarps * 32;
 constexpr int kDrainWarp0 = 2;
+constexpr int kMaxGroup = 64;
+constexpr int kMaxSplits = 16;           // site splits per slice of the heuristic and tuned launch shapes            // drained chunks per running sum before it goes out
 constexpr int kProdWarp0 = 10;
 constexpr int kInWarp = kProdWarp0 + 4 * NPK;
 constexpr uint32_t kTmemCols = 512;
@@ -141,7 +146,11 @@ struct FusedCore {
   CUtensorMap tmM;   // (CUtensorMap carries its own 64-byte alignment)
   CUtensorMap tmV;
   const __half *B;                      // phase table
-  float4 *partial;                      // [nt][nsplit][nrc * NH][ncols]: (Re C, Re S, Im C, Im S)
+  // per CTA (slice j, split, chunk rc, tile ct; in that order, ct fastest) a block of
+  // [half h][column quad m < NH / 2][row < 128] float4s (columns 4m .. 4m + 3): the
+  // thread of (row, h) owns one float4 of every quad, so a warp's accesses are 512-byte
+  // runs
+  float *partial;
   int *err;
   // per slice of the launch: the largest |re| or |im| of the matrix operand and of the
   // vector operand (as float bits), from which the CTA picks its power-of-two scale
@@ -384,16 +393,26 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
             break;
           }
           tc::tc_fence_after();
+          // Per half (Ur: columns [0, NP), Ui: [NP, 2NP)) the products with one lo factor
+          // of both k-steps come first and the hi x hi products last.  Every MMA
+          // truncates the accumulator, by up to one unit in its last place; the small
+          // products then meet a small accumulator at the start of a chunk, so a drain
+          // interval of two k-steps takes two full-size truncations instead of six.
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const uint64_t a = dA0 + (2 * pr + h) * kStageStep, bb = dB0 + (2 * pr + h) * kStageStep;
-            const uint32_t acc = h ? 1u : acc0;
-            tc::mma_f16(d, a, bb, idesc, acc);                            // Ur_h [cos|sin]_h
-            tc::mma_f16(d, a, bb + kBHalf, idesc, 1u);                    // Ur_h [cos|sin]_l
-            tc::mma_f16(d, a + kATile, bb, idesc, 1u);                    // Ur_l [cos|sin]_h
-            tc::mma_f16(d + NP, a + 2 * kATile, bb, idesc, acc);          // Ui_h [cos|sin]_h
-            tc::mma_f16(d + NP, a + 2 * kATile, bb + kBHalf, idesc, 1u);  // Ui_h [cos|sin]_l
-            tc::mma_f16(d + NP, a + 3 * kATile, bb, idesc, 1u);           // Ui_l [cos|sin]_h
+          for (int part = 0; part < 2; ++part) {
+            const uint32_t dd = d + part * NP;
+            const uint64_t ah = dA0 + 2 * part * kATile, al = ah + kATile;   // U hi, U lo of stage 0
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const uint64_t so = (2 * pr + h) * kStageStep;
+              tc::mma_f16(dd, ah + so, dB0 + so + kBHalf, idesc, h ? 1u : acc0);   // U_h [cos|sin]_l
+              tc::mma_f16(dd, al + so, dB0 + so, idesc, 1u);                       // U_l [cos|sin]_h
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const uint64_t so = (2 * pr + h) * kStageStep;
+              tc::mma_f16(dd, ah + so, dB0 + so, idesc, 1u);                       // U_h [cos|sin]_h
+            }
           }
           tc::mma_commit(&empty[pr]);
           if (++pr == NPAIR) {
@@ -414,17 +433,105 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
     const int row = qd * 32 + lane;
     const uint32_t lane_base = tbase + ((uint32_t)(qd * 32) << 16);
     const uint32_t rsum = lane_base + (uint32_t)(4 * NP + h * NT);   // this half's running sum in TMEM
+    // Two-level sum over the CTA's chunks.  The running sum takes up to kMaxGroup chunks
+    // (the chunks split into equal groups) and restarts; the group sums add up in tensor
+    // memory or in the CTA's block of partial sums in global memory.  A long site range
+    // (a 48^3 slice split 8 ways has 432 chunks of 2 k-steps per CTA) would otherwise add
+    // FP32 roundings of a growing sum above the tensor-memory truncation; shorter ranges
+    // (up to 128 chunks) make one group.  The group length is recomputed where needed
+    // (one register fewer across the chunk loop).
+    auto ngrp = [&]() {
+      const int ng = (nchunks + kMaxGroup - 1) / kMaxGroup;
+      return (nchunks + ng - 1) / max(ng, 1);
+    };
+    // Chunks of at most 32 representatives (NP <= 64) leave tensor-memory columns for the
+    // second level as well: the group sums of this half, NT columns after both running
+    // sums.  Wider chunks add each group into global memory.
+    constexpr bool kGroupInTmem = 8 * 2 * NH <= (int)kTmemCols;
+    const uint32_t gsum = rsum + (uint32_t)(2 * NT);
     float acc[kNRMax];   // columns NT .. NP - 1 of the running sum (widest chunk only)
 #pragma unroll
     for (int n = 0; n < kNRMax; ++n) acc[n] = 0.f;
-    for (int c = 0; c < nchunks; ++c) {
+    // tcgen05.ld is warp-collective: every lane executes it and stores its own row
+    auto flush = [&](bool first, bool last) {
+      // this thread's row of the block (computed here so that none of it stays live
+      // across the chunk loop; the empty asm keeps the compiler from hoisting it)
+      int rw = row;
+      asm volatile("" : "+r"(rw));
+      // gamma5 signs of this row: g5(v) for the insertion and the baryon spectator,
+      // g5(v) g5(bt) g5(b) for the meson spectator (s = bt*12 + b*3 + a), row = (s - s0)*8
+      // + noise*4 + v; the projection is linear, so they act on the finished sums
+      const int v = rw & 3, sidx = s0 + (rw >> 3);
+      const int smask = MODE != 1 ? (p.g5mask >> v)
+                                  : ((p.g5mask >> v) ^ (p.g5mask >> (sidx / 12)) ^ (p.g5mask >> ((sidx % 12) / 3)));
+      const float sgn = ldexpf((smask & 1) ? -1.f : 1.f, -sc_e);   // the sign and the inverse split scale
+      // column quad m (columns 4m .. 4m + 3) of this half at out[m * MT]
+      float4 *out = reinterpret_cast<float4 *>(p.partial) +
+                    ((((size_t)j * p.nsplit + split) * p.nrc + rc) * p.nct + ct) * (NH * MT) + (size_t)h * (NH / 2) * MT +
+                    rw;
+      if constexpr (kGroupInTmem) {
+        // the group sums add up in tensor memory; only the last group writes, once
+#pragma unroll 1
+        for (int n0 = 0; n0 < NT; n0 += 8) {
+          float r[8], g[8];
+          tc::tmem_ld8(rsum + n0, r);
+          if (!first) tc::tmem_ld8(gsum + n0, g);
+          tc::tmem_wait_ld();
+          if (!first)
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) add2(r[e], r[e + 1], g[e], g[e + 1]);
+          if (last) {
+#pragma unroll
+            for (int e = 0; e < 8; e += 4)
+              out[(size_t)(n0 + e) / 4 * MT] = make_float4(sgn * r[e], sgn * r[e + 1], sgn * r[e + 2], sgn * r[e + 3]);
+          } else {
+            tc::tmem_st8(gsum + n0, r);
+          }
+        }
+        if (!last) tc::tmem_wait_st();
+      } else {
+        // the first group stores; later groups add with fire-and-forget vector reductions
+        // (one thread per address, so they apply in program order: the sum is
+        // deterministic)
+        auto put = [&](int m, float x0, float x1, float x2, float x3) {
+          const float4 x = make_float4(sgn * x0, sgn * x1, sgn * x2, sgn * x3);
+          if (first)
+            out[(size_t)m * MT] = x;
+          else
+            atomicAdd(out + (size_t)m * MT, x);
+        };
+#pragma unroll 1
+        for (int n0 = 0; n0 < NT; n0 += 16) {
+          float r[16];
+          tc::tmem_ld16(rsum + n0, r);
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 16; e += 4) put((n0 + e) / 4, r[e], r[e + 1], r[e + 2], r[e + 3]);
+        }
+        if (wide) {   // NP - NT == kNRMax
+#pragma unroll
+          for (int e = 0; e < kNRMax; e += 4) {
+            put((NT + e) / 4, acc[e], acc[e + 1], acc[e + 2], acc[e + 3]);
+            acc[e] = acc[e + 1] = acc[e + 2] = acc[e + 3] = 0.f;
+          }
+        }
+      }
+    };
+    bool ok = true;
+    for (int c0 = 0; c0 < nchunks && ok; c0 += ngrp()) {
+     const int c1 = min(nchunks, c0 + ngrp());
+     for (int c = c0; c < c1; ++c) {
       int b = c & 1, ub = c >> 1;
+      const bool restart = c == c0;   // the chunk opens a group: it replaces the running sum
       // one thread waits, the eight drain warps block on named barrier 1 and follow its
       // verdict together (the tensor-memory loads below are warp-collective and must
       // never see a split warp; every drain warp reaches the barrier in every chunk)
       if (warp == kDrainWarp0 && lane == 0) verdict[b] = tc::mbar_wait(&tfull[b], ub & 1, err, 5) ? 1 : 0;
       tc::named_bar_sync(1, 256);
-      if (!verdict[b]) break;
+      if (!verdict[b]) {
+        ok = false;
+        break;
+      }
       tc::tc_fence_after();
       const uint32_t t = lane_base + (uint32_t)(b * 2 * NP + h * NP);
 #pragma unroll
@@ -434,11 +541,11 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
         tc::tmem_ld16(t + n0, v);
         if (n0 < NT) {
           float r[16];
-          if (c > 0) tc::tmem_ld16(rsum + n0, r);
+          if (!restart) tc::tmem_ld16(rsum + n0, r);
           tc::tmem_wait_ld();
 #pragma unroll
           for (int e = 0; e < 16; e += 2) {
-            if (c > 0) {
+            if (!restart) {
               add2(r[e], r[e + 1], v[e], v[e + 1]);
             } else {
               r[e] = v[e];
@@ -457,46 +564,9 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
       tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&tempty[b]);
-    }
-    // row -> (s, noise, spin): m = sl*8 + ii*4 + v
-    const int sl = row >> 3, ii = (row >> 2) & 1, v = row & 3;
-    const int noise = i0 + ii;
-    const int sidx = s0 + sl;
-    // meson: col = (noise, v, s); baryon: col = (noise, alpha = s/3, beta' = v, c = s%3)
-    const int col = MODE == 2 ? noise * 3072 + (sidx / 3) * 12 + v * 3 + sidx % 3 : noise * 192 + v * 48 + sidx;
-    // gamma5 signs of this row: g5(v) for the insertion and the baryon spectator,
-    // g5(v) g5(bt) g5(b) for the meson spectator (s = bt*12 + b*3 + a); the projection is
-    // linear, so they act on the finished sums
-    const int smask = MODE != 1 ? (p.g5mask >> v)
-                                : ((p.g5mask >> v) ^ (p.g5mask >> (sidx / 12)) ^ (p.g5mask >> ((sidx % 12) / 3)));
-    const float sgn = ldexpf((smask & 1) ? -1.f : 1.f, -sc_e);   // the sign and the inverse split scale
-    const int rend = min(p.nrep - rc * NH, NH);
-    // tcgen05.ld is warp-collective: every lane executes it, only the stores are per lane
-    const int failed = __shfl_sync(0xffffffffu, *err, 0);
-    if (!failed && nk > 0) {
-      const bool mine = noise < p.n_r;
-      // column n of this half is (cos, sin) = (n / NH) of representative rc NH + n % NH;
-      // it goes to component 2 h + n / NH of the (Re C, Re S, Im C, Im S) quadruple
-      float *out = reinterpret_cast<float *>(p.partial + ((size_t)j * p.nsplit + split) * p.nrc * NH * p.ncols) +
-                   (size_t)rc * NH * p.ncols * 4 + (size_t)col * 4 + 2 * h;
-#pragma unroll 1
-      for (int n0 = 0; n0 < NT; n0 += 16) {
-        float r[16];
-        tc::tmem_ld16(rsum + n0, r);
-        tc::tmem_wait_ld();
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int n = n0 + e, rho = n % NH;
-          if (mine && rho < rend) out[(size_t)rho * p.ncols * 4 + n / NH] = sgn * r[e];
-        }
-      }
-      if (wide) {   // NP - NT == kNRMax
-#pragma unroll
-        for (int e = 0; e < kNRMax; ++e) {
-          const int n = NT + e, rho = n % NH;
-          if (mine && rho < rend && n < NP) out[(size_t)rho * p.ncols * 4 + n / NH] = sgn * acc[e];
-        }
-      }
+     }
+     // the buffer is free again: the group's sum goes out while the next chunk accumulates
+     if (ok) flush(c0 == 0, c1 == nchunks);
     }
   } else {
     // ---------------------------------------------------- producers
@@ -717,44 +787,83 @@ __device__ __forceinline__ void two_sum(float &hi, float &lo, float v) {
   lo += e;
 }
 
-// One thread per (slice j, representative rho, column): the four sums (Re C, Re S, Im C,
-// Im S) over the site splits are each kept exactly as an unevaluated FP32 pair (TwoSum).
-// Every requested momentum q of rho (rep_q[rep_first[rho] ..], entry 2 q + 1 when
-// k_q = -k_rho) receives out[j][q][col] = C + i sigma_q S with sigma_q = sign * (+1 or
-// -1): Re = Re C - sigma Im S and Im = Im C + sigma Re S are formed as FP32 pairs too
-// (TwoSum of the leading parts, the trailing parts added), and each pair is rounded once
-// to FP64 with one FP64 addition; the FP64 pipe of GB300 does nothing else here.
-__global__ void __launch_bounds__(kReduceThreads)
-    reduce_f64(const float4 *__restrict__ part, int nsplit, size_t per_split,
-                           const int *__restrict__ rep_first, const int *__restrict__ rep_q, int nrep, int sign,
-                           int ncols, double2 *__restrict__ out, int nt, size_t out_stride) {
-  const size_t n_in = (size_t)nrep * ncols;
+// One thread per (slice j, chunk rc, tile ct, quad m of representatives of the chunk,
+// row of the tile), rows fastest, so that the float4 loads of the CTA blocks are 512-byte
+// runs: for each representative rho = rc NH + 4m + i (i < 4) the four sums (Re C, Re S,
+// Im C, Im S) over the site splits are each kept exactly as an unevaluated FP32 pair
+// (TwoSum).  The row is the output column col of noise i0 + ii, spin v and matrix index
+// s0 + sl (row = sl*8 + ii*4 + v; meson col = (noise, v, s), baryon col = (noise,
+// alpha = s/3, beta' = v, c = s%3)); rows of a missing second noise and representatives
+// past the last are skipped.  Every requested momentum q of rho (rep_q[rep_first[rho]
+// ..], entry 2 q + 1 when k_q = -k_rho) receives out[j][q][col] = C + i sigma_q S with
+// sigma_q = sign * (+1 or -1): Re = Re C - sigma Im S and Im = Im C + sigma Re S are
+// formed as FP32 pairs too (TwoSum of the leading parts, the trailing parts added), and
+// each pair is rounded once to FP64 with one FP64 addition; the FP64 pipe of GB300 does
+// nothing else here.
+struct ReduceArgs {
+  const float *part;
+  size_t per_split;   // floats per site split of a slice (nrc * nct blocks of 4 NH * MT)
+  const int *rep_first, *rep_q;
+  double2 *out;
+  size_t out_stride;  // between slices
+  int nsplit, nrep, sign, ncols, nt, nrc, nct, NH, n_r, mode;
+};
+
+__global__ void __launch_bounds__(kReduceThreads) reduce_f64(const ReduceArgs a) {
+  const int nm = a.NH / 4;
+  const size_t n_in = (size_t)a.nrc * a.nct * nm * MT;
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n_in * nt) return;
+  if (idx >= n_in * a.nt) return;
   const int j = (int)(idx / n_in);
-  const size_t e = idx % n_in;
-  const int rho = (int)(e / ncols), col = (int)(e % ncols);
-  const float4 *pj = part + (size_t)j * nsplit * per_split + e;
-  float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
-  // unrolled so that several splits' loads are in flight before the first is added (the
-  // order of the sums is unchanged)
-#pragma unroll 4
-  for (int s = 0; s < nsplit; ++s) {
-    const float4 v = __ldcs(pj + (size_t)s * per_split);
-    two_sum(h[0], l[0], v.x);
-    two_sum(h[1], l[1], v.y);
-    two_sum(h[2], l[2], v.z);
-    two_sum(h[3], l[3], v.w);
+  size_t e = idx % n_in;
+  const int row = (int)(e % MT);
+  e /= MT;
+  const int m = (int)(e % nm);
+  e /= nm;
+  const int ct = (int)(e % a.nct), rc = (int)(e / a.nct);
+  const int rg0 = rc * a.NH + 4 * m;
+  const int npairs = (a.n_r + 1) / 2;
+  const int noise = 2 * (ct % npairs) + ((row >> 2) & 1), sidx = 16 * (ct / npairs) + (row >> 3), v = row & 3;
+  if (rg0 >= a.nrep || noise >= a.n_r) return;
+  const int col = a.mode == 2 ? noise * 3072 + (sidx / 3) * 12 + v * 3 + sidx % 3 : noise * 192 + v * 48 + sidx;
+  // quads of the block: Re C at m, Re S at NH/4 + m (half 0), Im C at NH/2 + m, Im S at
+  // 3NH/4 + m (half 1)
+  const float4 *pj = reinterpret_cast<const float4 *>(a.part + (size_t)j * a.nsplit * a.per_split) +
+                     ((size_t)rc * a.nct + ct) * (a.NH * MT) + (size_t)m * MT + row;
+  const size_t o1 = (size_t)nm * MT, o2 = 2 * o1, o3 = 3 * o1, sp = a.per_split / 4;
+  float h[4][4], l[4][4];   // [component][representative of the quad]
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[c][i] = l[c][i] = 0.f;
+  // the four loads of a split are in flight together (the order of the sums is fixed)
+#pragma unroll 1
+  for (int s = 0; s < a.nsplit; ++s) {
+    const float4 *q = pj + (size_t)s * sp;
+    const float4 x[4] = {__ldcs(q), __ldcs(q + o1), __ldcs(q + o2), __ldcs(q + o3)};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      two_sum(h[c][0], l[c][0], x[c].x);
+      two_sum(h[c][1], l[c][1], x[c].y);
+      two_sum(h[c][2], l[c][2], x[c].z);
+      two_sum(h[c][3], l[c][3], x[c].w);
+    }
   }
-  double2 *oj = out + (size_t)j * out_stride + col;
-  for (int u = __ldg(rep_first + rho), u1 = __ldg(rep_first + rho + 1); u < u1; ++u) {
-    const int qe = __ldg(rep_q + u);
-    const float sg = (qe & 1) ? -(float)sign : (float)sign;
-    // Re = (h0 + l0) - sg (h3 + l3), Im = (h2 + l2) + sg (h1 + l1): sg = +-1 is exact
-    float rh = h[0], rl = l[0] - sg * l[3], ih = h[2], il = l[2] + sg * l[1];
-    two_sum(rh, rl, -sg * h[3]);
-    two_sum(ih, il, sg * h[1]);
-    oj[(size_t)(qe >> 1) * ncols] = make_double2(f32_to_f64(rh) + f32_to_f64(rl), f32_to_f64(ih) + f32_to_f64(il));
+  double2 *oj = a.out + (size_t)j * a.out_stride + col;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int rg = rg0 + i;
+    if (rg >= a.nrep) break;
+    for (int u = __ldg(a.rep_first + rg), u1 = __ldg(a.rep_first + rg + 1); u < u1; ++u) {
+      const int qe = __ldg(a.rep_q + u);
+      const float sg = (qe & 1) ? -(float)a.sign : (float)a.sign;
+      // Re = (h0 + l0) - sg (h3 + l3), Im = (h2 + l2) + sg (h1 + l1): sg = +-1 is exact
+      float rh = h[0][i], rl = l[0][i] - sg * l[3][i], ih = h[2][i], il = l[2][i] + sg * l[1][i];
+      two_sum(rh, rl, -sg * h[3][i]);
+      two_sum(ih, il, sg * h[1][i]);
+      oj[(size_t)(qe >> 1) * a.ncols] =
+          make_double2(f32_to_f64(rh) + f32_to_f64(rl), f32_to_f64(ih) + f32_to_f64(il));
+    }
   }
 }
 
@@ -1084,12 +1193,13 @@ static int get_phase_cs(lhc_ctx ctx, int L, const int *k, int nq, const int r[4]
 // the phase table of its momentum set.  Used for admission control by the job server.
 size_t mixed_call_bytes(Part part, int dtype, int V3, int n_r, int nt, int nq) {
   const bool baryon = part == PART_SPEC_BARYON;
-  const size_t ncols = (size_t)n_r * (baryon ? kBarCols : 192);
+  // partial sums are kept per tile of two noises: an odd count is padded by one
+  const size_t ncols = (size_t)(n_r + 1) / 2 * 2 * (baryon ? kBarCols : 192);
   const size_t ntl = (size_t)std::min(nt, kMaxSlices);
   // at most nq representatives: at most ceil(nq / RCHUNK) chunks of at most RCHUNK
   const size_t nrep_pad = (size_t)(nq + RCHUNK - 1) / RCHUNK * RCHUNK;
   const size_t nkb = (V3 + 2 * KSTEP - 1) / (2 * KSTEP) * 2;
-  size_t b = ntl * 8 * nrep_pad * ncols * sizeof(float4);
+  size_t b = ntl * kMaxSplits * nrep_pad * ncols * sizeof(float4);
   if (dtype == LHC_C128) b += ntl * V3 * 144 * 8 + (baryon ? (size_t)V3 * 144 * 8 : 0) + (size_t)n_r * ntl * V3 * 12 * 8;
   if (baryon) b += (size_t)V3 * 2304 * 8;
   b += nkb * 2 * 2 * nrep_pad * 32 + 4 * (size_t)(2 * nq + 1) + 12 * (size_t)nq + 4096;
@@ -1302,10 +1412,17 @@ struct ChunkLayout {
   size_t off_s, off_sb, off_v, off_d, off_m, bytes;
 };
 
+// floats of the partial sums per site split of one slice: nrc chunks x nct tiles, each
+// a CTA block of 4 NH x MT floats
+static size_t split_floats(const SliceJob &j0, int NH, int nrc) {
+  const int nct = (j0.part == PART_SPEC_BARYON ? 48 : 3) * ((j0.n_r + 1) / 2);
+  return (size_t)nrc * nct * 4 * NH * MT;
+}
+
 static ChunkLayout chunk_layout(const SliceJob &j0, int ntl, int nsplit, size_t per_split) {
   const bool baryon = j0.part == PART_SPEC_BARYON, narrow = j0.dtype == LHC_C128;
   const int V3 = j0.V3, n_r = j0.n_r;
-  const size_t p_bytes = (size_t)ntl * nsplit * per_split * sizeof(float4);
+  const size_t p_bytes = (size_t)ntl * nsplit * per_split * sizeof(float);
   const size_t s_bytes = narrow ? (size_t)ntl * V3 * 144 * sizeof(float2) : 0;
   const size_t sb_bytes = narrow && baryon ? (size_t)V3 * 144 * sizeof(float2) : 0;
   const size_t v_bytes = narrow ? (size_t)n_r * ntl * V3 * 12 * sizeof(float2) : 0;
@@ -1342,7 +1459,7 @@ static int prepare_chunk(lhc_ctx ctx, const SliceJob *jobs, int nb, int nq, int 
   unsigned *maxS = reinterpret_cast<unsigned *>(ws + lay.off_m), *maxV = maxS + kMaxSlices, *maxD = maxV + kMaxSlices;
   FusedParams &fp = pc->fp;
   fp.c.B = phase;
-  fp.c.partial = reinterpret_cast<float4 *>(ws);
+  fp.c.partial = reinterpret_cast<float *>(ws);
   fp.c.err = ctx->dev_err;
   fp.c.n_r = n_r;
   fp.c.V3 = V3;
@@ -1372,7 +1489,7 @@ static int prepare_chunk(lhc_ctx ctx, const SliceJob *jobs, int nb, int nq, int 
   pc->nsplit = nsplit;
   pc->NH = NH;
   pc->mode = (int)j0.part;
-  pc->per_split = (size_t)nrc * NH * ncols;
+  pc->per_split = split_floats(j0, NH, nrc);
   pc->n_out = (size_t)nq * ncols;
   pc->rmap = rmap;
   pc->out = j0.out;
@@ -1471,9 +1588,25 @@ static int prepare_chunk(lhc_ctx ctx, const SliceJob *jobs, int nb, int nq, int 
 static int finish_chunk(lhc_ctx ctx, const Prepared &pc, cudaStream_t st) {
   const size_t n_in = (size_t)pc.nrep * pc.ncols;
   ProfScope ps(ctx, st, LHC_KERNEL_REDUCE, (double)pc.nb * pc.nsplit * n_in * 16 + (double)pc.nb * pc.n_out * 16);
-  reduce_f64<<<(unsigned)((n_in * pc.nb + kReduceThreads - 1) / kReduceThreads), kReduceThreads, 0, st>>>(
-      pc.fp.c.partial, pc.nsplit, pc.per_split, pc.rmap, pc.rmap + pc.nrep + 1, pc.nrep, pc.sign, pc.ncols, pc.out,
-      pc.nb, pc.n_out);
+  ReduceArgs a;
+  a.part = pc.fp.c.partial;
+  a.per_split = pc.per_split;
+  a.rep_first = pc.rmap;
+  a.rep_q = pc.rmap + pc.nrep + 1;
+  a.out = pc.out;
+  a.out_stride = pc.n_out;
+  a.nsplit = pc.nsplit;
+  a.nrep = pc.nrep;
+  a.sign = pc.sign;
+  a.ncols = pc.ncols;
+  a.nt = pc.nb;
+  a.nrc = pc.fp.c.nrc;
+  a.nct = pc.fp.c.nct;
+  a.NH = pc.NH;
+  a.n_r = pc.fp.c.n_r;
+  a.mode = pc.mode;
+  const size_t threads = (size_t)pc.nb * a.nrc * a.nct * (a.NH / 4) * MT;
+  reduce_f64<<<(unsigned)((threads + kReduceThreads - 1) / kReduceThreads), kReduceThreads, 0, st>>>(a);
   note_launch();
   LHC_CHECK_CUDA(cudaGetLastError());
   return LHC_OK;
@@ -1508,7 +1641,7 @@ static int run_mixed_shape(lhc_ctx ctx, const SliceJob *jobs, int nt, const int 
   const int *rmap = nullptr;
   LHC_TRY(get_phase_cs(ctx, j0.L, k, nq, r, reps, NH, nrc, nkb, st, &phase, &rmap));
   const int ncols = j0.n_r * (j0.part == PART_SPEC_BARYON ? kBarCols : 192);
-  const ChunkLayout lay = chunk_layout(j0, std::min(nt, kMaxSlices), nsplit, (size_t)nrc * NH * ncols);
+  const ChunkLayout lay = chunk_layout(j0, std::min(nt, kMaxSlices), nsplit, split_floats(j0, NH, nrc));
   LHC_TRY(ensure(ctx, ctx->ws, lay.bytes));
   char *ws = static_cast<char *>(ctx->ws.p);
   const int kd = kd_for(j0.part);
@@ -1541,7 +1674,7 @@ static void tune_candidates(int nrep, int npairs, std::vector<std::pair<int, int
     if (nh < 16 && nrep > 8 && !widths.empty()) break;
     if (std::find(widths.begin(), widths.end(), nh) == widths.end()) widths.push_back(nh);
   }
-  static const int kSplits[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16};
+  static const int kSplits[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, kMaxSplits};
   for (int nh : widths)
     for (int ns : kSplits)
       if (ns == 1 || ns <= npairs / 2) out->emplace_back(nh, ns);
@@ -1671,8 +1804,7 @@ int run_batch_mixed(lhc_ctx ctx, const std::vector<BatchCall> &calls, cudaStream
     const int nrc = (reps[c].nrep() + NH[c] - 1) / NH[c];
     const int nkb = ((j0.V3 + 2 * KSTEP - 1) / (2 * KSTEP)) * 2;
     LHC_TRY(get_phase_cs(ctx, j0.L, bc.k, bc.nq, bc.r, reps[c], NH[c], nrc, nkb, st, &phase[c], &rmap[c]));
-    const int ncols = j0.n_r * (j0.part == PART_SPEC_BARYON ? kBarCols : 192);
-    lay[c] = chunk_layout(j0, nt, nsplit[c], (size_t)nrc * NH[c] * ncols);
+    lay[c] = chunk_layout(j0, nt, nsplit[c], split_floats(j0, NH[c], nrc));
     off[c + 1] = off[c] + lay[c].bytes;
   }
   // persistent launches: at most one per (part, chunk width) and kMaxBatch calls

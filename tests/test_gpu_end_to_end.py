@@ -55,6 +55,38 @@ def test_chain_24c_one_slice_per_correlator(seed):
     assert e_corr < CS.MIXED_TOL
 
 
+def test_chain_48c_largest_served_lattice_per_correlator():
+    """The meson chain on the largest served lattice (48^3, 110592 sites per slice: the
+    longest site sums), 4 noises, complex64 inputs, 93 momenta, against the oracle on the
+    same complex64-rounded inputs, per correlator."""
+    from oracle import contractions as OC
+    from oracle.momenta import momenta
+    from paper_1711_02384_gb300 import inputs, lhc
+    L, n_r = 48, 4
+    k = momenta(8)
+    S = inputs.propagator(3100, L, 96, slices=[20, 30]).astype(np.complex64)
+    psi = inputs.solutions(3101, L, 96, n_r, slices=[20, 30]).astype(np.complex64)
+    eta = inputs.noise(3102, L, n_r, 30).astype(np.complex64)
+    g16 = inputs.dirac_structures()
+    g4 = np.broadcast_to(inputs.dirac_matrices()[3], (16, 4, 4)).copy()
+    r = np.array([7, 30, 41, 0], dtype=np.int32)
+    with lhc.Context(0) as ctx:
+        dS = dev(S)
+        gi = ctx.insertion(dS, dev(psi), 0, 0, r, k, prec="mixed")
+        gs = ctx.spectator(dS, dev(eta), 1, r, k, prec="mixed")
+        gc = ctx.combine(gs, gi, dev(g16), dev(g4), dev(g16), prec="mixed")
+        gi, gs, gc = gi.cpu().numpy(), gs.cpu().numpy(), gc.cpu().numpy()
+        ctx.sync()
+    g5 = CS.g5_matrix()
+    ri = OC.insertion(S[0:1].astype(complex), psi[:, 0:1].astype(complex), g5, r[:3], k, L)
+    rs = OC.spectator_meson(S[1].astype(complex), eta.astype(complex), g5, r[:3], k, L)
+    rc = OC.combine_meson(rs, ri[0], g16, g4, g16)
+    e_ins, e_spec, e_corr = block_err(gi[0], ri[0]), block_err(gs, rs), CS.corr_err(gc[0], rc)
+    print(f"[parity] 48^3 chain: insertion {e_ins:.3e}, spectator {e_spec:.3e}, combine {e_corr:.3e} per correlator")
+    assert e_ins < CS.MIXED_TOL and e_spec < CS.MIXED_TOL
+    assert e_corr < CS.MIXED_TOL
+
+
 @pytest.mark.parametrize("seed", [3300, 3400])
 def test_baryon_chain_16c_123_momenta_per_correlator(seed):
     """The baryon chain on 16^3 with the 123 momenta of the baryon configuration (|k|^2 <= 9,
