@@ -396,9 +396,9 @@ def main():
         bound, punit, peak_src = "alu", "TFLOP/s", "nominal FP64 1.25 TFLOP/s"
     achieved = (kwork / (kms / 1e3)) / 1e12 if kms > 0 else None
     # DRAM bytes per launch: ncu dram__bytes_read + dram__bytes_write of the same kernel on
-    # the 2-slice 24^3 case (86.00 MB for 4.11e7 units: 2.09 bytes per unit, the compulsory
+    # the 2-slice 24^3 case (83.07 MB for 4.11e7 units: 2.02 bytes per unit, the compulsory
     # input), scaled to this workload's units per launch
-    traffic = 2.09 * upstep / kn if (args.prec == "mixed" and kn) else None
+    traffic = 2.02 * upstep / kn if (args.prec == "mixed" and kn) else None
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": punit,
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "kernel_ms_per_launch": kms / kn if kn else None, "launches_per_step": kn,

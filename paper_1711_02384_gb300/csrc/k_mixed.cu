@@ -1614,14 +1614,16 @@ static int finish_chunk(lhc_ctx ctx, const Prepared &pc, cudaStream_t st) {
 
 static int kd_for(Part part) {
   // k-steps accumulated in tensor memory between drains.  The accumulation truncates, so
-  // the error grows with the interval: measured on the 24^3 workload (16 noises, 93
-  // momenta) intervals 6, 4 and 2 give 4.6e-7, 3.6e-7 and 2.9e-7 per block against the
-  // oracle, for 1% and 11% more time in the fused kernel than interval 6.  The combine
-  // adds the errors of both parts, so the spectators (meson: a tenth of the fused time;
-  // baryon: the part whose error dominates its combine) drain every 2, the insertion every
-  // 4.  LHC_KD sets every part's interval, LHC_KD_INS,
+  // the error grows with the interval.  Measured against the oracle on the 24^3 chain (16
+  // noises, 93 momenta): the insertion gives 1.6e-7 per block at interval 2 and 2.5e-7 at
+  // 4, for 13% more fused-kernel time at 2; the meson and baryon spectators 1.6e-7 and
+  // 1.4e-7 at 2, 2.5e-7 and 2.4e-7 at 4, for 11% and 10% more time at 2.  The combine adds
+  // the errors of both parts: the meson spectator (a tenth of the meson step) drains every
+  // 2, the insertion and the baryon spectator (most of the baryon step) every 4, which
+  // leaves every correlator of those chains within 6.5e-7 (meson) and 7.5e-7 (baryon) of
+  // the oracle, relative to its row.  LHC_KD sets every part's interval, LHC_KD_INS,
   // LHC_KD_SPEC and LHC_KD_BAR one part's; intervals are even, since k-steps come in pairs.
-  static const int defaults[3] = {4, 2, 2};   // insertion, meson spectator, baryon spectator
+  static const int defaults[3] = {4, 2, 4};   // insertion, meson spectator, baryon spectator
   static const char *names[3] = {"LHC_KD_INS", "LHC_KD_SPEC", "LHC_KD_BAR"};
   int kd = defaults[(int)part];
   const char *e = getenv(names[(int)part]);
