@@ -25,7 +25,7 @@
 //               ring, whose stages the producers free
 //   warp 1      allocates tensor memory and issues the MMAs
 //   warps 2-9   drain the accumulator every KD k-steps into an FP32 running sum, which
-//               starts again after every group of at most 128 chunks
+//               starts again after every group of at most 64 chunks
 //   warps 10-21 producers, four per k-step and three k-steps in flight: contract the
 //               inputs in FP32, split each value into fp16 hi + lo and write the four A
 //               tiles (Ur hi/lo, Ui hi/lo), MN-major
@@ -36,7 +36,7 @@
 // (the lo*lo term dropped), i.e. Re C, Re S, Im C, Im S.  Tensor memory accumulation
 // truncates, so the products with a lo factor go first within each pair of k-steps, and D
 // is double-buffered and drained every KD k-steps into a two-level FP32 sum (a running
-// sum over groups of at most 128 chunks, whose group sums add up in tensor memory or, for
+// sum over groups of at most 64 chunks, whose group sums add up in tensor memory or, for
 // the widest chunks, in the CTA's partial sums in global memory); reduce_f64 adds the
 // partials of all CTAs exactly, rounds to FP64 and forms out[q] = C + i sigma_q S.
 #include <algorithm>
@@ -71,8 +71,7 @@ constexpr int NPK = 3;                   // k-steps in flight in the producers (
 constexpr int kWarps = 23;
 constexpr int kThreads = kWarps * 32;
 constexpr int kDrainWarp0 = 2;
-constexpr int kMaxGroup = 64;
-constexpr int kMaxSplits = 16;           // site splits per slice of the heuristic and tuned launch shapes            // drained chunks per running sum before it goes out
+constexpr int kMaxGroup = 64;            // drained chunks per running sum before it goes out
 constexpr int kProdWarp0 = 10;
 constexpr int kInWarp = kProdWarp0 + 4 * NPK;
 constexpr uint32_t kTmemCols = 512;
@@ -438,7 +437,7 @@ __device__ __forceinline__ void fused_body(const FusedCore &p, const int ct, con
     // memory or in the CTA's block of partial sums in global memory.  A long site range
     // (a 48^3 slice split 8 ways has 432 chunks of 2 k-steps per CTA) would otherwise add
     // FP32 roundings of a growing sum above the tensor-memory truncation; shorter ranges
-    // (up to 128 chunks) make one group.  The group length is recomputed where needed
+    // (up to 64 chunks) make one group.  The group length is recomputed where needed
     // (one register fewer across the chunk loop).
     auto ngrp = [&]() {
       const int ng = (nchunks + kMaxGroup - 1) / kMaxGroup;

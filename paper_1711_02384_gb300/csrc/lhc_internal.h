@@ -57,6 +57,9 @@ int ensure_smem_limit(K *kernel, int bytes, std::atomic<unsigned long long> &don
 constexpr int kInsCols = 192;       // (alpha~, beta~, beta, a) per noise
 constexpr int kMesCols = 192;       // (beta', alpha', alpha, a) per noise
 constexpr int kBarCols = 3072;      // (alpha1', alpha1, alpha2', alpha2, beta', c) per noise
+// site splits per slice of a mixed launch: the autotuner's largest candidate, the bound of
+// a tuning-table entry and of the workspace estimate of the job server's admission
+constexpr int kMaxSplits = 16;
 
 enum Part { PART_INS = 0, PART_SPEC_MESON = 1, PART_SPEC_BARYON = 2 };
 

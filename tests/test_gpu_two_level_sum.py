@@ -1,11 +1,11 @@
 """Long site ranges per CTA.  The fused kernel drains its tensor-memory accumulator into
-an FP32 running sum that restarts after groups of at most 128 drained chunks; the group
+an FP32 running sum that restarts after groups of at most 64 drained chunks; the group
 sums add up in tensor memory when a chunk has at most 32 momentum representatives, and in
 the CTA's block of partial sums in global memory (float4 atomic adds) for wider chunks.
 
 With one site split per slice (LHC_NSPLIT=1) every CTA of a 24^3 slice runs all 864
-k-steps: the meson spectator (drained every 2 k-steps) makes 432 chunks in 4 groups, the
-insertion and the baryon spectator (every 4) 216 chunks in 2 groups.  Both second-level
+k-steps: the meson spectator (drained every 2 k-steps) makes 432 chunks in 7 groups, the
+insertion and the baryon spectator (every 4) 216 chunks in 4 groups.  Both second-level
 paths must match the oracle within the mixed bound, as closely as the default launch
 shape does, and repeat bit for bit (each partial-sum address has one writer, so the order
 of the adds is fixed)."""
